@@ -1,0 +1,241 @@
+/*
+ * ld_oracle.c -- plain, slow CPU oracle for the lane-detection hot path of
+ * "Hardware Acceleration of Lane Detection Algorithm: A GPU Versus FPGA
+ * Comparison" (arXiv 2212.09460).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file.  The CUDA library never
+ * links, calls or includes it, and it shares no code, header or table with
+ * the CUDA path.
+ *
+ * Every function is the direct definition of one step, written as plain
+ * loops in the paper's order:
+ *   Step 1  Sobel gradient magnitude |G| = |Sx*Img| + |Sy*Img|   (Sec. 2.1, Eq. 1)
+ *           on the zero-padded image                            (Sec. 3.1, Sec. 4.1)
+ *   Step 2  binarization to 0/255                               (Sec. 2.2, Sec. 3.2, Sec. 4.2)
+ *   Step 3  Hough voting r = x cos(theta) + y sin(theta)        (Sec. 2.3, Eq. 3, Sec. 4.3)
+ *           with the cos/sin symmetry of Eqs. 4-5               (Sec. 3.3)
+ *   Step 4  Hough peaks (done in MATLAB in the paper)           (Sec. 2.3, Sec. 5)
+ *
+ * Readings where the paper is silent (each one is also listed with its pin in
+ * the design notes):
+ *   - Sobel pair: the standard 3x3 pair; |Gx|+|Gy| does not depend on sign,
+ *     transpose, flip or correlation-vs-convolution conventions.
+ *   - magnitude saturated to 255 (8-bit output); threshold T, test M >= T.
+ *   - x = column (0..w-1, rightwards), y = row (0..h-1, downwards).
+ *   - theta_k = k*180/n_theta degrees, k = 0..n_theta-1 (half-open [0,180)).
+ *   - cos/sin in Q16: c_k = llround(cos(k*pi/n_theta)*65536) for
+ *     k <= n_theta/2, and the mirror c_k = -c_{n-k}, s_k = s_{n-k} (Eqs. 4-5).
+ *   - rho = floor((x*c_k + y*s_k + 32768) / 65536), accumulator index rho+D,
+ *     D = ceil(sqrt(w^2+h^2)); a vote whose rho falls outside [-D, D] is not
+ *     counted (it is reported in the return value).
+ *   - peaks: greedy in the order votes desc, theta_idx asc, rho_idx asc,
+ *     each pick suppresses a window of nms_theta x nms_rho cells (no wrap).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LDO_BORDER_ZERO 0
+#define LDO_BORDER_CLEAR 1
+
+/* Smallest integer D with D*D >= w*w + h*h, i.e. ceil(sqrt(w^2+h^2)). */
+int ldo_rho_max(int w, int h)
+{
+    int64_t r2 = (int64_t)w * w + (int64_t)h * h;
+    int64_t d = 0;
+    while (d * d < r2) d++;
+    return (int)d;
+}
+
+/* Padded pixel P(x, y): the image inside, 0 outside (Sec. 3.1, Sec. 4.1). */
+static int pix(const uint8_t *img, int w, int h, int pitch, int x, int y)
+{
+    if (x < 0 || y < 0 || x >= w || y >= h) return 0;
+    return img[(size_t)y * pitch + x];
+}
+
+/*
+ * Step 1 (Eq. 1): mag[y*w+x] = min(|Gx| + |Gy|, 255) with
+ *   Gx = P(x+1,y-1) + 2P(x+1,y) + P(x+1,y+1) - P(x-1,y-1) - 2P(x-1,y) - P(x-1,y+1)
+ *   Gy = P(x-1,y+1) + 2P(x,y+1) + P(x+1,y+1) - P(x-1,y-1) - 2P(x,y-1) - P(x+1,y-1)
+ * written as the two 3x3 kernels applied tap by tap.  With border ==
+ * LDO_BORDER_CLEAR the 1-pixel frame of the output is forced to 0.
+ * variant (0..7) picks one of the eight sign/transpose conventions of the
+ * kernel pair: bit0 negates Sx, bit1 negates Sy, bit2 swaps Sx and Sy.  All
+ * give the same magnitude; the tests use this to pin convention independence.
+ */
+void ldo_sobel_mag(const uint8_t *img, int w, int h, int pitch, int border,
+                   int variant, uint8_t *mag)
+{
+    static const int SX[3][3] = {{-1, 0, 1}, {-2, 0, 2}, {-1, 0, 1}};
+    static const int SY[3][3] = {{-1, -2, -1}, {0, 0, 0}, {1, 2, 1}};
+    int kx[3][3], ky[3][3];
+    int sx = (variant & 1) ? -1 : 1, sy = (variant & 2) ? -1 : 1;
+    for (int j = 0; j < 3; j++)
+        for (int i = 0; i < 3; i++) {
+            int a = sx * SX[j][i], b = sy * SY[j][i];
+            if (variant & 4) { kx[j][i] = b; ky[j][i] = a; }
+            else { kx[j][i] = a; ky[j][i] = b; }
+        }
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            int gx = 0, gy = 0;
+            for (int j = -1; j <= 1; j++)
+                for (int i = -1; i <= 1; i++) {
+                    int p = pix(img, w, h, pitch, x + i, y + j);
+                    gx += kx[j + 1][i + 1] * p;
+                    gy += ky[j + 1][i + 1] * p;
+                }
+            int m = abs(gx) + abs(gy);
+            if (m > 255) m = 255;
+            if (border == LDO_BORDER_CLEAR &&
+                (x == 0 || y == 0 || x == w - 1 || y == h - 1))
+                m = 0;
+            mag[(size_t)y * w + x] = (uint8_t)m;
+        }
+}
+
+/* Step 2 (Sec. 2.2): every pixel becomes 255 if mag >= T, else 0. */
+void ldo_binarize(const uint8_t *mag, int w, int h, int threshold, uint8_t *bin)
+{
+    for (size_t i = 0; i < (size_t)w * h; i++)
+        bin[i] = (mag[i] >= threshold) ? 255 : 0;
+}
+
+/*
+ * Coordinates of the 255 pixels, row-major, packed as (y << 16) | x
+ * (the edge list the GPU voting stage reads, Sec. 4.3).  Writes at most
+ * `capacity` entries; returns the true count.
+ */
+int64_t ldo_edge_list(const uint8_t *bin, int w, int h, uint32_t *edges,
+                      int64_t capacity)
+{
+    int64_t n = 0;
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++)
+            if (bin[(size_t)y * w + x] == 255) {
+                if (n < capacity) edges[n] = ((uint32_t)y << 16) | (uint32_t)x;
+                n++;
+            }
+    return n;
+}
+
+/*
+ * Q16 cos/sin table over theta_k = k*pi/n_theta (Sec. 3.3).  Entries for
+ * k <= n_theta/2 are rounded from fp64 cos/sin; the rest follow from
+ * Eq. 4 (sin t = sin(180-t)) and Eq. 5 (cos t = -cos(180-t)).
+ */
+void ldo_trig_q16(int n_theta, int32_t *c, int32_t *s)
+{
+    for (int k = 0; k <= n_theta / 2; k++) {
+        double t = (double)k * M_PI / (double)n_theta;
+        c[k] = (int32_t)llround(cos(t) * 65536.0);
+        s[k] = (int32_t)llround(sin(t) * 65536.0);
+    }
+    for (int k = n_theta / 2 + 1; k < n_theta; k++) {
+        c[k] = -c[n_theta - k];
+        s[k] = s[n_theta - k];
+    }
+}
+
+static int64_t floor_div(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) q--;
+    return q;
+}
+
+/*
+ * Step 3 (Eq. 3): acc[k*(2D+1) + rho + D] += 1 for every edge (x, y) and
+ * every k, with rho = floor((x*c_k + y*s_k + 32768) / 65536) in int64.
+ * acc holds n_theta*(2D+1) int32 cells and is overwritten.  Returns the
+ * number of votes that fell outside [-D, D] (not counted).
+ */
+int64_t ldo_hough(const uint32_t *edges, int64_t n_edges, int w, int h,
+                  int n_theta, int32_t *acc)
+{
+    int D = ldo_rho_max(w, h);
+    int n_rho = 2 * D + 1;
+    int32_t *c = (int32_t *)malloc(sizeof(int32_t) * n_theta);
+    int32_t *s = (int32_t *)malloc(sizeof(int32_t) * n_theta);
+    ldo_trig_q16(n_theta, c, s);
+    memset(acc, 0, sizeof(int32_t) * (size_t)n_theta * n_rho);
+    int64_t dropped = 0;
+    for (int64_t e = 0; e < n_edges; e++) {
+        int64_t x = edges[e] & 0xFFFF, y = edges[e] >> 16;
+        for (int k = 0; k < n_theta; k++) {
+            int64_t rho = floor_div(x * c[k] + y * s[k] + 32768, 65536);
+            if (rho < -D || rho > D) { dropped++; continue; }
+            acc[(size_t)k * n_rho + (size_t)(rho + D)] += 1;
+        }
+    }
+    free(c);
+    free(s);
+    return dropped;
+}
+
+/* a precedes b in the peak order: votes desc, theta asc, rho asc. */
+static int before(int32_t va, int ta, int ra, int32_t vb, int tb, int rb)
+{
+    if (va != vb) return va > vb;
+    if (ta != tb) return ta < tb;
+    return ra < rb;
+}
+
+/*
+ * Step 4 (Sec. 2.3 "Hough Peak"): greedy non-maximum suppression.  Up to
+ * top_k times: take the first cell in peak order that is not suppressed and
+ * has votes >= min_votes; emit (theta_idx, rho_idx, votes); suppress every
+ * cell with |dtheta| <= nms_theta/2 and |drho| <= nms_rho/2 (clipped, no
+ * wrap).  out holds 3*top_k int32.  Returns the number of peaks emitted.
+ */
+int ldo_peaks(const int32_t *acc, int n_theta, int n_rho, int top_k,
+              int nms_theta, int nms_rho, int min_votes, int32_t *out)
+{
+    uint8_t *sup = (uint8_t *)calloc((size_t)n_theta * n_rho, 1);
+    int ht = nms_theta / 2, hr = nms_rho / 2, n = 0;
+    for (int p = 0; p < top_k; p++) {
+        int bt = -1, br = -1;
+        int32_t bv = 0;
+        for (int t = 0; t < n_theta; t++)
+            for (int r = 0; r < n_rho; r++) {
+                size_t i = (size_t)t * n_rho + r;
+                if (sup[i] || acc[i] < min_votes) continue;
+                if (bt < 0 || before(acc[i], t, r, bv, bt, br)) {
+                    bt = t; br = r; bv = acc[i];
+                }
+            }
+        if (bt < 0) break;
+        out[3 * n + 0] = bt;
+        out[3 * n + 1] = br;
+        out[3 * n + 2] = bv;
+        n++;
+        for (int t = bt - ht; t <= bt + ht; t++)
+            for (int r = br - hr; r <= br + hr; r++)
+                if (t >= 0 && t < n_theta && r >= 0 && r < n_rho)
+                    sup[(size_t)t * n_rho + r] = 1;
+    }
+    free(sup);
+    return n;
+}
+
+/*
+ * The whole path for one frame, Steps 1-4 in order; used by the CPU baseline.
+ * mag/bin are w*h scratch, edges has capacity w*h, acc n_theta*(2D+1).
+ * Returns the peak count (>= 0).
+ */
+int ldo_detect(const uint8_t *img, int w, int h, int pitch, int border,
+               int threshold, int n_theta, int top_k, int nms_theta,
+               int nms_rho, int min_votes, uint8_t *mag, uint8_t *bin,
+               uint32_t *edges, int32_t *acc, int32_t *peaks)
+{
+    ldo_sobel_mag(img, w, h, pitch, border, 0, mag);
+    ldo_binarize(mag, w, h, threshold, bin);
+    int64_t n = ldo_edge_list(bin, w, h, edges, (int64_t)w * h);
+    ldo_hough(edges, n, w, h, n_theta, acc);
+    int D = ldo_rho_max(w, h);
+    return ldo_peaks(acc, n_theta, 2 * D + 1, top_k, nms_theta, nms_rho,
+                     min_votes, peaks);
+}

@@ -1,0 +1,194 @@
+"""Seeded synthetic road frames (uint8 grayscale) -- input generator only.
+
+This module holds no step of the detection method (no Sobel, no
+binarization, no voting, no peak picking); it only draws pixels.  Both the
+CUDA path and the CPU oracle consume its frames, so the two always see the
+same input.
+
+The paper's only workload is a 512x512 gray road image that is not
+available, so these frames stand in for it.  Every pixel is a pure function
+of (seed, x, y): random numbers come from SplitMix64 (Steele, Lea and Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014) used as a
+counter-based generator, and all per-pixel arithmetic is integer, so a
+device-side generator can reproduce a frame bit for bit.
+
+Frame recipe (all quantities per frame, drawn from the frame's seed):
+  * background: vertical gradient 40 (top row) .. 120 (bottom row);
+  * 2 solid stripes (``style='solid'``) or 2-4 dashed stripes
+    (``style='dashed'``, dash and gap lengths U[30, 60] px) of 6 px width and
+    intensity U[200, 255]; stripe directions alternate between U[25, 65] and
+    U[115, 155] degrees from the x-axis, each through a point in the lower half;
+  * additive noise, approximately Gaussian (Irwin-Hall sum of eight 16-bit
+    uniforms) with std ``sigma`` above the horizon (y < h/2) and
+    ``sigma_road`` below it (road texture), rounded, clamped to [0, 255];
+  * salt: each pixel set to 255 with probability ``salt``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+# std of a sum of eight independent uniforms on {0..65535}
+_IH8_STD = math.sqrt(8.0 * (65536.0 ** 2 - 1.0) / 12.0)
+_IH8_MEAN = 8 * 65535 // 2  # 262140
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function applied to a uint64 array."""
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def _stream_base(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        s = np.array([(int(seed) * 8 + int(stream)) & ((1 << 64) - 1)], np.uint64)
+        return _mix64(s + _GAMMA)[0]
+
+
+def _draws(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """The idx-th SplitMix64 outputs of the stream (seed, stream)."""
+    base = _stream_base(seed, stream)
+    with np.errstate(over="ignore"):
+        return _mix64(base + (idx.astype(np.uint64) + np.uint64(1)) * _GAMMA)
+
+
+class _Scalars:
+    """Sequential uniform draws for the per-frame parameters (stream 0)."""
+
+    def __init__(self, seed: int):
+        self.seed = seed
+        self.i = 0
+
+    def u(self) -> float:
+        v = _draws(self.seed, 0, np.array([self.i]))[0]
+        self.i += 1
+        return float(v >> np.uint64(11)) / float(1 << 53)
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Uniform integer in [lo, hi]."""
+        return lo + min(int(self.u() * (hi - lo + 1)), hi - lo)
+
+
+@dataclass(frozen=True)
+class FrameStyle:
+    style: str = "solid"        # 'solid' (two stripes) or 'dashed' (2-4 stripes)
+    sigma: float = 8.0          # noise std above the horizon
+    sigma_road: float = 8.0     # noise std below the horizon (road texture)
+    salt: float = 0.0           # probability of a 255 salt pixel
+
+
+# Workload presets.  ``LATENCY_640x480`` is the single-frame latency frame
+# (solid stripes, sigma 8, no salt).  ``THROUGHPUT_1080P`` is the dashed-lane
+# frame with 0.5% salt; its road texture sigma_road was tuned once so that the
+# binarized edge density of every frame lies in [5%, 10%].
+LATENCY_640x480 = FrameStyle("solid", 8.0, 8.0, 0.0)
+THROUGHPUT_1080P = FrameStyle("dashed", 8.0, 12.0, 0.005)
+
+
+@dataclass(frozen=True)
+class Stripe:
+    nx: int      # Q16 unit normal
+    ny: int
+    c: int       # Q16 offset: inside if |x*nx + y*ny - c| < 3*65536
+    tx: int      # Q16 unit tangent
+    ty: int
+    t0: int      # Q16 phase along the stripe
+    dash: int    # dash length in px (0: solid)
+    gap: int
+    value: int   # stripe intensity
+
+
+def frame_stripes(seed: int, w: int, h: int, style: FrameStyle):
+    """Per-frame stripe descriptors (integer Q16 geometry)."""
+    r = _Scalars(seed)
+    n_lines = 2 if style.style == "solid" else 2 + min(int(r.u() * 3), 2)
+    out = []
+    for j in range(n_lines):
+        lo, hi = (25.0, 65.0) if j % 2 == 0 else (115.0, 155.0)
+        phi = math.radians(lo + (hi - lo) * r.u())
+        px = (0.2 + 0.6 * r.u()) * (w - 1)
+        py = (0.5 + 0.5 * r.u()) * (h - 1)
+        value = r.randint(200, 255)
+        if style.style == "dashed":
+            dash, gap = r.randint(30, 60), r.randint(30, 60)
+            phase = r.randint(0, dash + gap - 1)
+        else:
+            dash, gap, phase = 0, 0, 0
+        dx, dy = math.cos(phi), math.sin(phi)
+        nx, ny = -dy, dx
+        q = 65536.0
+        out.append(Stripe(nx=int(round(nx * q)), ny=int(round(ny * q)),
+                          c=int(round((px * nx + py * ny) * q)),
+                          tx=int(round(dx * q)), ty=int(round(dy * q)),
+                          t0=int(round((px * dx + py * dy) * q)) - phase * 65536,
+                          dash=dash, gap=gap, value=value))
+    return out
+
+
+def road_frame(seed: int, w: int, h: int, style: FrameStyle = LATENCY_640x480) -> np.ndarray:
+    """One uint8 [h][w] frame, a pure function of (seed, w, h, style)."""
+    ys = np.arange(h, dtype=np.int64)[:, None]
+    xs = np.arange(w, dtype=np.int64)[None, :]
+    v = np.broadcast_to(40 + (80 * ys) // max(h - 1, 1), (h, w)).astype(np.int64)
+    for st in frame_stripes(seed, w, h, style):
+        inside = np.abs(xs * st.nx + ys * st.ny - st.c) < 3 * 65536
+        if st.dash:
+            t = np.floor_divide(xs * st.tx + ys * st.ty - st.t0, 65536)
+            inside &= np.mod(t, st.dash + st.gap) < st.dash
+        v = np.where(inside, st.value, v)
+    idx = np.arange(w * h, dtype=np.uint64).reshape(h, w)
+    a = _draws(seed, 1, idx)
+    b = _draws(seed, 2, idx)
+    m16 = np.uint64(0xFFFF)
+    s8 = np.zeros((h, w), np.int64)
+    for z in (a, b):
+        for k in range(4):
+            s8 += ((z >> np.uint64(16 * k)) & m16).astype(np.int64)
+    n = s8 - _IH8_MEAN
+    k_top = int(round(style.sigma / _IH8_STD * 2.0 ** 32))
+    k_road = int(round(style.sigma_road / _IH8_STD * 2.0 ** 32))
+    kk = np.where(ys >= h // 2, k_road, k_top)
+    noise = (n * kk + (1 << 31)) >> 32
+    v = np.clip(v + noise, 0, 255)
+    if style.salt > 0:
+        c = _draws(seed, 3, idx)
+        thr = np.uint64(int(style.salt * 2.0 ** 32))
+        v = np.where((c & np.uint64(0xFFFFFFFF)) < thr, 255, v)
+    return v.astype(np.uint8)
+
+
+def pitched(frame: np.ndarray, pitch: int | None = None, fill: int | None = None,
+            seed: int = 0) -> np.ndarray:
+    """Copy a [h][w] frame into a [h][pitch] buffer (pitch a multiple of 16).
+
+    The columns beyond w are filled with ``fill`` or, when None, with seeded
+    garbage, so that tests can check that nothing reads them.
+    """
+    h, w = frame.shape
+    if pitch is None:
+        pitch = (w + 15) // 16 * 16
+    buf = np.empty((h, pitch), np.uint8)
+    if fill is None:
+        idx = np.arange(h * pitch, dtype=np.uint64).reshape(h, pitch)
+        buf[:] = (_draws(seed, 7, idx) & np.uint64(0xFF)).astype(np.uint8)
+    else:
+        buf[:] = fill
+    buf[:, :w] = frame
+    return buf
+
+
+def random_image(seed: int, w: int, h: int, density: float | None = None) -> np.ndarray:
+    """Uniform random uint8 image; with ``density`` a 0/255 pattern instead."""
+    idx = np.arange(w * h, dtype=np.uint64).reshape(h, w)
+    z = _draws(seed, 5, idx)
+    if density is None:
+        return (z & np.uint64(0xFF)).astype(np.uint8)
+    thr = np.uint64(int(density * 2.0 ** 32))
+    return np.where((z & np.uint64(0xFFFFFFFF)) < thr, 255, 0).astype(np.uint8)
