@@ -1,0 +1,338 @@
+"""Throughput benchmark of the lane-detection hot path on one GB300 per rank.
+
+Workload: a batch of 64 seeded synthetic 1920x1080 uint8 road frames
+(dashed lanes, 0.5% salt, edge density 5-10%), 3x3 Sobel |Gx|+|Gy|,
+threshold 128, Hough voting into 360 theta bins of 0.5 deg with rho step
+1 px, top-4 peaks with 5x5 suppression.  One step = one ld_detect_batch call
+over the whole batch (Steps 1-4 of the paper's pipeline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is frames/s with the frames resident in HBM
+(device time from CUDA events on the launching stream, L2 flushed before
+every step); ``e2e`` is frames/s through the same C-ABI call from pinned host
+memory, with the host->device copy of the frames and the device->host copy
+of the peaks inside the timed region.  ``--impl reference`` times the CPU
+oracle on a bounded sample of the same workload.  Under torchrun every rank
+processes its own 64-frame batch (weak scaling; frames are independent, so
+there is no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H, N_FRAMES, N_THETA, TOP_K = 1920, 1080, 64, 360, 4
+SEED0 = 1000
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "1080p frames/s end-to-end, % of HBM roofline; proposal vs plain at equal peaks"
+
+
+def _gen(seed: int) -> np.ndarray:
+    from paper_2212_09460_gb300 import synth
+    return synth.road_frame(seed, W, H, synth.THROUGHPUT_1080P)
+
+
+def make_frames(seeds) -> np.ndarray:
+    """[n][H][W] uint8 frames, generated in a spawn-context process pool."""
+    n_proc = max(1, min(16, os.cpu_count() or 1, len(seeds)))
+    if n_proc == 1:
+        return np.stack([_gen(s) for s in seeds])
+    with mp.get_context("spawn").Pool(n_proc) as pool:
+        return np.stack(pool.map(_gen, seeds))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(frames: np.ndarray, budget_s: float = 12.0):
+    """The oracle as it stands, single-threaded, on as many frames as fit the budget."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(frames):
+        oracle.detect(frames[done], N_THETA, TOP_K)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {len(frames)} 1920x1080 frames, full Steps 1-4 (oracle.detect), "
+                      f"{dt:.1f} s, one thread"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    frames = make_frames([SEED0 + i for i in range(4)])
+    import oracle
+    oracle.build()
+    per_step = 2                               # frames per reference step (bounded sample)
+    for i in range(args.warmup):
+        oracle.detect(frames[i % len(frames)], N_THETA, TOP_K)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for j in range(per_step):
+            oracle.detect(frames[(k * per_step + j) % len(frames)], N_THETA, TOP_K)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * per_step / total
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{N_FRAMES} x {W}x{H} uint8 frames, {N_THETA} theta, top-{TOP_K}; "
+                                   f"each reference step = {per_step} frames",
+                       "global_batch": N_FRAMES, "parallelism": "host, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} frames per step x {args.steps} steps, one thread"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # frames are generated before any CUDA call (spawn pool)
+    seeds = [SEED0 + rank * N_FRAMES + i for i in range(N_FRAMES)]
+    host_frames = make_frames(seeds)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_09460_gb300 import ld
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    dev = torch.device("cuda", local_rank)
+    frames_d = torch.from_numpy(host_frames).to(dev)                 # [64][1080][1920], pitch 1920
+    frames_h = torch.from_numpy(host_frames).pin_memory()
+    frames_e2e = torch.empty_like(frames_d)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    p = ld.params(n_theta=N_THETA, top_k=TOP_K)
+    ctx = ld.Context(local_rank)
+    ctx.reserve(N_FRAMES * W * H, N_FRAMES, 0, p)
+    out = (torch.zeros((N_FRAMES, TOP_K, 3), dtype=torch.int32, device=dev),
+           torch.zeros(N_FRAMES, dtype=torch.int32, device=dev),
+           torch.zeros(N_FRAMES, dtype=torch.int32, device=dev))
+    views = [frames_d[i] for i in range(N_FRAMES)]
+    views_e2e = [frames_e2e[i] for i in range(N_FRAMES)]
+    stream = torch.cuda.current_stream(dev)
+    ld.ld_ctx_enable_timing(ctx.handle, True)
+
+    def step(vs):
+        ctx.detect_batch(vs, p, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step(views)
+    torch.cuda.synchronize(dev)
+    st = out[2].cpu()
+    if int(st.abs().sum()) != 0:
+        raise RuntimeError(f"device status not OK: {st.tolist()}")
+
+    # ---- device-resident timed region: K steps, L2 flushed before each
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = np.zeros(3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev0[k].record(stream)
+            step(views)
+            ev1[k].record(stream)
+            stage += np.array(ld.ld_ctx_stage_ms(ctx.handle))   # waits for this step
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = float(sum(step_ms))
+    stage_ms = stage / args.steps                                 # mean per step: sobel, hough, peaks
+
+    # ---- end to end through the same call, from pinned host memory
+    peaks_h = torch.empty((N_FRAMES, TOP_K, 3), dtype=torch.int32).pin_memory()
+    npk_h = torch.empty(N_FRAMES, dtype=torch.int32).pin_memory()
+    st_h = torch.empty(N_FRAMES, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+
+    def e2e_step():
+        frames_e2e.copy_(frames_h, non_blocking=True)
+        step(views_e2e)
+        peaks_h.copy_(out[0], non_blocking=True)
+        npk_h.copy_(out[1], non_blocking=True)
+        st_h.copy_(out[2], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    for k in range(e2e_steps):
+        flush.fill_(k & 0xFF)
+        e0[k].record(stream)
+        e2e_step()
+        e1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in zip(e0, e1))) / e2e_steps
+    assert int(st_h.abs().sum()) == 0 and bool((npk_h == TOP_K).all())
+
+    # max over ranks
+    if dist:
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+
+    if rank == 0:
+        import json as _json
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = _json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        value = world * N_FRAMES * args.steps / (total_ms / 1000.0)
+        e2e_val = world * N_FRAMES / (e2e_ms / 1000.0)
+
+        # algorithmic work per step: Hough E*n_theta votes per frame;
+        # Sobel 1 B/px read + 4 B per edge written
+        e_sum = edge_count_total(ctx, views, p, dev)
+        votes = e_sum * N_THETA
+        hough_s = stage_ms[1] / 1000.0
+        sobel_s = stage_ms[0] / 1000.0
+        sobel_bytes = N_FRAMES * W * H * 1 + e_sum * 4
+        atom_peak = n_sms * 32 * sm_max_mhz * 1e6 / 1e9          # Gvote/s: 32 banks/clk/SM
+        roof = {"bound": "alu", "kernel": "hough_kernel (Step 3 voting + per-tile top-M)",
+                "achieved": votes / hough_s / 1e9, "peak": atom_peak, "unit": "Gvote/s",
+                "frac": votes / hough_s / 1e9 / atom_peak, "traffic": None,
+                "peak_basis": f"{n_sms} SMs x 32 shared-memory banks/clk x {sm_max_mhz:.0f} MHz "
+                              f"(one conflict-free 4-byte atomic per bank per clock)",
+                "avg_launch_ms": stage_ms[1]}
+        roof_sobel = {"bound": "hbm", "kernel": "sobel_bin_edges_kernel (Steps 1-2 + compaction)",
+                      "achieved": sobel_bytes / sobel_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": sobel_bytes / sobel_s / 1e9 / hbm_peak, "traffic": None,
+                      "peak_basis": f"{hbm_src} HBM copy bandwidth", "avg_launch_ms": stage_ms[0]}
+        with_cpu = not args.no_cpu_baseline
+        cpu = cpu_baseline(host_frames) if with_cpu else None
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"{N_FRAMES} x {W}x{H} uint8 seeded dashed-lane frames (seeds "
+                                       f"{SEED0}+), 5-10% edge density, 3x3 Sobel, T=128, {N_THETA} theta x "
+                                       f"1 px rho int32 accumulator, top-{TOP_K} 5x5 NMS",
+                           "global_batch": N_FRAMES * world, "frames_per_gpu": N_FRAMES,
+                           "parallelism": f"frames sharded across {world} GPU(s), no collective",
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "edges_per_frame_mean": e_sum / N_FRAMES},
+                "stage_ms": {"sobel_binarize": stage_ms[0], "hough_vote": stage_ms[1], "peaks": stage_ms[2]},
+                "roofline": roof, "roofline_sobel": roof_sobel,
+                "e2e": {"value": e2e_val, "unit": "frames/s",
+                        "h2d_bytes_per_step": int(frames_h.numel()),
+                        "d2h_bytes_per_step": int(peaks_h.numel() * 4 + npk_h.numel() * 4 + st_h.numel() * 4)},
+                "gpu_launches": 3 * args.steps,
+                "clocks": clk.summary(),
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def edge_count_total(ctx, views, p, dev) -> float:
+    """Total edge pixels of the batch (one untimed Sobel pass through the C ABI)."""
+    import torch
+    tot = 0
+    edges = torch.empty(W * H, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    for v in views:
+        ctx.sobel_binarize(v, p, edges=edges, count=cnt)
+        tot += int(cnt.item())
+    return float(tot)
+
+
+if __name__ == "__main__":
+    main()

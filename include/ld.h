@@ -1,0 +1,196 @@
+/*
+ * ld.h -- C ABI of the GB300 lane-detection hot path (libld.so).
+ *
+ * The library computes, on one CUDA GPU, the data-parallel steps of the
+ * lane-detection pipeline of "Hardware Acceleration of Lane Detection
+ * Algorithm: A GPU Versus FPGA Comparison" (arXiv 2212.09460):
+ *
+ *   Step 1  Sobel gradient magnitude |G| = |Sx*Img| + |Sy*Img|  (Sec. 2.1, Eq. 1)
+ *           on the zero-padded image                           (Sec. 3.1, Sec. 4.1)
+ *   Step 2  binarization to 0 / 255                            (Sec. 2.2, Sec. 4.2)
+ *   Step 3  Hough voting r = x cos(theta) + y sin(theta)       (Sec. 2.3, Eq. 3, Sec. 4.3)
+ *           with sin/cos symmetry                              (Sec. 3.3, Eqs. 4-5)
+ *   Step 4  Hough peaks, which the paper leaves to MATLAB      (Sec. 2.3, Sec. 5)
+ *
+ * Conventions shared by every entry point:
+ *   - Images are uint8, row-major, row stride `pitch` bytes.  x is the column
+ *     (0..w-1, rightwards), y the row (0..h-1, downwards).
+ *   - theta_idx k in [0, n_theta) means theta = k * 180 / n_theta degrees.
+ *   - D = ceil(sqrt(w^2 + h^2)); rho lies in [-D, D] and is stored at
+ *     rho_idx = rho + D, so an accumulator has n_rho = 2D + 1 columns.
+ *   - The accumulator is int32, theta-major: acc[theta_idx * n_rho + rho_idx].
+ *   - rho = floor((x * c_k + y * s_k + 32768) / 65536) with the Q16 table
+ *     c_k = round(65536 cos(k pi / n_theta)), s_k = round(65536 sin(k pi / n_theta))
+ *     for k <= n_theta / 2 and c_k = -c_{n-k}, s_k = s_{n-k} above (Eqs. 4-5).
+ *   - An edge pixel is packed as (y << 16) | x in a uint32.
+ *   - Pointers named d_* are device pointers, h_* host pointers.  The caller
+ *     owns every buffer passed in; the library keeps only its context.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; argument errors are
+ *     returned synchronously and enqueue nothing.
+ *   - Every call returns an ld_status; ld_last_error() gives the message of
+ *     the calling thread's last failure.
+ */
+#ifndef LD_H
+#define LD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LD_API __attribute__((visibility("default")))
+#else
+#define LD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LD_OK = 0,
+    LD_ERR_INVALID = 1,   /* bad argument; nothing was enqueued */
+    LD_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    LD_ERR_NOMEM = 3,     /* device allocation of context scratch failed */
+    LD_ERR_CAPACITY = 4,  /* an edge list overflowed its capacity */
+    LD_ERR_TIMEOUT = 5    /* a bounded device wait gave up */
+} ld_status;
+
+typedef enum {
+    LD_BORDER_ZERO = 0,   /* zero padding, output size = input size (Sec. 3.1, 4.1) */
+    LD_BORDER_CLEAR = 1   /* as ZERO, then the 1-pixel output frame is forced to 0 */
+} ld_border;
+
+/* Method parameters.  ld_params_default() fills the values in brackets. */
+typedef struct {
+    int32_t n_theta;       /* theta bins over [0, 180) deg, even, 2..4096   [180] */
+    int32_t threshold;     /* binarization: 255 if |G| >= threshold, 1..255  [128] */
+    int32_t border;        /* ld_border                                      [ZERO] */
+    int32_t top_k;         /* peaks to return, 1..16                         [4]   */
+    int32_t nms_theta;     /* suppression window height (theta), odd >= 1    [5]   */
+    int32_t nms_rho;       /* suppression window width (rho), odd >= 1       [5]   */
+    int32_t min_votes;     /* a peak needs votes >= min_votes                [1]   */
+    int32_t reserved;      /* must be 0                                            */
+    int64_t edge_capacity; /* slots in a caller edge list; 0 = w*h           [0]   */
+} ld_params;
+
+/* One Hough peak: theta = theta_idx*180/n_theta deg, rho = rho_idx - D. */
+typedef struct {
+    int32_t theta_idx;
+    int32_t rho_idx;
+    int32_t votes;
+} ld_peak;
+
+/* One frame of a batch: device image, its size and row pitch in bytes. */
+typedef struct {
+    const uint8_t *img;
+    int32_t w, h, pitch;
+    int32_t reserved;      /* must be 0 */
+} ld_frame;
+
+typedef struct ld_ctx ld_ctx;
+
+/* Fill *p with the defaults listed in ld_params. */
+LD_API ld_status ld_params_default(ld_params *p);
+
+/* Create a context on CUDA device `device`: Q16 tables and scratch for
+ * ld_hough_peaks and ld_detect_batch are allocated lazily and kept until
+ * ld_ctx_destroy.  A context may be used from one host thread at a time. */
+LD_API ld_status ld_ctx_create(ld_ctx **out, int device);
+LD_API ld_status ld_ctx_destroy(ld_ctx *ctx);
+
+/* Pre-size the context scratch so that later ld_detect_batch calls with at
+ * most `max_frames` frames totalling `max_pixels` pixels, and ld_hough_peaks
+ * calls on at most `max_acc_cells` cells, allocate nothing (needed before
+ * capturing those calls in a CUDA graph). */
+LD_API ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames,
+                         int64_t max_acc_cells, const ld_params *p);
+
+/* Sizes for a w x h image: *acc_elems = n_theta * (2D+1) int32 cells,
+ * *edge_elems = w*h (worst-case edge count), *D = ceil(sqrt(w^2+h^2)).
+ * Validates the size: 3 <= w, h and w + h <= 32767 (so the packed edge and
+ * the Q16 rho fit 32 bits), and p (may be NULL for the defaults). */
+LD_API ld_status ld_query_sizes(int32_t w, int32_t h, const ld_params *p,
+                         size_t *acc_elems, size_t *edge_elems, int32_t *D);
+
+/*
+ * Steps 1-2 fused (Eq. 1, Sec. 2.2, Sec. 3.1, Sec. 4.1-4.2) plus the edge list
+ * the voting stage reads (Sec. 4.3).
+ *   d_img        uint8 [h][pitch]; pitch % 16 == 0, pitch >= w, d_img 16-byte
+ *                aligned.  Bytes beyond w in a row are never read into the result.
+ *   d_bin        optional (NULL to skip) uint8 [h][pitch] output, 0 or 255 per
+ *                pixel, 16-byte aligned; the padding bytes w..pitch-1 of each row
+ *                are unspecified on return.
+ *   d_edges      uint32 [p->edge_capacity] (or [w*h] when that is 0) output:
+ *                the (y << 16) | x of every 255 pixel, in unspecified order.
+ *   d_edge_count int32 [1] output: the true number of edge pixels.  If it
+ *                exceeds the capacity, only `capacity` entries were written
+ *                (the caller checks after synchronising; LD_ERR_CAPACITY).
+ */
+LD_API ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w,
+                            int32_t h, int32_t pitch, const ld_params *p,
+                            uint8_t *d_bin, uint32_t *d_edges,
+                            int32_t *d_edge_count, void *stream);
+
+/*
+ * Step 3 (Eq. 3, Eqs. 4-5, Sec. 4.3): for every edge pixel and every theta bin,
+ * acc[k][rho + D] += 1.
+ *   d_edges      uint32 edge list, 16-byte aligned, as written by ld_sobel_binarize:
+ *                distinct pixels.  Entries with x >= w or y >= h are skipped.  (The
+ *                kernel counts in 16 bits per cell, exact for distinct pixels since
+ *                a rho strip of width 1 holds at most 2*max(w, h) <= 65528 of them.)
+ *   d_edge_count int32 [1] device count; min(count, capacity) edges are read,
+ *                capacity = p->edge_capacity or w*h when 0.
+ *   d_acc        int32 [n_theta][2D+1] output, fully overwritten.
+ */
+LD_API ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges,
+                        const int32_t *d_edge_count, int32_t w, int32_t h,
+                        const ld_params *p, int32_t *d_acc, void *stream);
+
+/*
+ * Step 4 (Sec. 2.3 "Hough Peak", Sec. 5): greedy non-maximum suppression.
+ * Up to top_k times: take the cell first in the order (votes desc, theta_idx
+ * asc, rho_idx asc) that is not suppressed and has votes >= min_votes, emit
+ * it, and suppress the nms_theta x nms_rho window around it (clipped at the
+ * grid edges, theta does not wrap).
+ *   d_acc        int32 [n_theta][n_rho] input (any values).
+ *   d_peaks      ld_peak [top_k] output, in emission order.
+ *   d_n_peaks    int32 [1] output, the number of peaks emitted (<= top_k).
+ */
+LD_API ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_theta,
+                         int32_t n_rho, const ld_params *p, ld_peak *d_peaks,
+                         int32_t *d_n_peaks, void *stream);
+
+/*
+ * Steps 1-4 for a batch of frames of possibly different sizes, each as in the
+ * calls above (border, threshold, theta bins and peaks from *p).
+ *   h_frames     host array of n frame descriptors (device images); 1 <= n.
+ *   d_peaks      ld_peak [n][top_k] output.
+ *   d_n_peaks    int32 [n] output.
+ *   d_status     int32 [n] output, per-frame ld_status of the device work
+ *                (LD_OK, or LD_ERR_TIMEOUT if a bounded wait gave up).
+ * Edge lists and candidate buffers live in the context scratch, sized for
+ * the worst case (every pixel an edge), so no capacity error can occur.
+ */
+LD_API ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                          const ld_params *p, ld_peak *d_peaks,
+                          int32_t *d_n_peaks, int32_t *d_status, void *stream);
+
+/* Stage timing.  After ld_ctx_enable_timing(ctx, 1), every ld_detect_batch
+ * call also records CUDA events on its stream around its kernels: before
+ * Steps 1-2, between Steps 1-2 and Step 3, between Step 3 and Step 4, and
+ * after Step 4 (batches of more than 128 frames: the first three events
+ * bracket the first launch group, the last one follows the last group).
+ * ld_ctx_stage_ms waits for the last such call and returns the device time of
+ * its three stages in milliseconds.  enable = 0 switches recording off. */
+LD_API ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable);
+LD_API ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]);
+
+/* Message of the calling thread's last failed call ("" if none). */
+LD_API const char *ld_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LD_H */

@@ -1,0 +1,624 @@
+// ld_api.cu -- host side of the C ABI declared in include/ld.h: argument
+// validation, the context (Q16 cos/sin tables, scratch), launch planning.
+// All computation runs in the kernels of ld_sobel.cu, ld_hough.cu and
+// ld_peaks.cu; nothing here computes a result on the host.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ld_internal.cuh"
+
+using namespace ld;
+
+namespace {
+
+thread_local std::string g_err;
+
+ld_status fail(ld_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+ld_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(LD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    // Grow-only device buffer; false on allocation failure.
+    bool ensure(size_t need) {
+        if (need <= bytes) return true;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bytes = need;
+        return true;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// Keeps the calling thread's current device, switching to the context's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct ld_ctx {
+    int device = 0;
+    int num_sms = 148;
+    std::map<int, int32_t *> trig;        // n_theta -> device Q16 table
+    std::map<int, std::vector<int32_t>> trig_host;
+    DevBuf edges, small, cand;            // detect_batch / hough_peaks scratch
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timing = false;
+    bool timed_once = false;
+    std::mutex mu;
+};
+
+namespace {
+
+int64_t rho_max_of(int64_t w, int64_t h) {
+    const int64_t r2 = w * w + h * h;
+    int64_t d = (int64_t)std::sqrt((double)r2);
+    while (d * d < r2) ++d;
+    while (d > 0 && (d - 1) * (d - 1) >= r2) --d;
+    return d;
+}
+
+// Q16 table over k = 0..n_theta/2 (Eqs. 4-5 supply the rest on the device).
+std::vector<int32_t> make_trig(int n_theta) {
+    std::vector<int32_t> t(2 * (n_theta / 2 + 1));
+    for (int k = 0; k <= n_theta / 2; ++k) {
+        const double a = (double)k * M_PI / (double)n_theta;
+        t[2 * k] = (int32_t)std::llround(std::cos(a) * 65536.0);
+        t[2 * k + 1] = (int32_t)std::llround(std::sin(a) * 65536.0);
+    }
+    return t;
+}
+
+ld_status check_params(const ld_params *p) {
+    if (!p) return LD_OK;
+    if (p->n_theta < 2 || p->n_theta > kMaxTheta || (p->n_theta & 1))
+        return fail(LD_ERR_INVALID, "n_theta must be even in [2, %d], got %d", kMaxTheta, p->n_theta);
+    if (p->threshold < 1 || p->threshold > 255)
+        return fail(LD_ERR_INVALID, "threshold must be in [1, 255], got %d", p->threshold);
+    if (p->border != LD_BORDER_ZERO && p->border != LD_BORDER_CLEAR)
+        return fail(LD_ERR_INVALID, "border must be LD_BORDER_ZERO or LD_BORDER_CLEAR");
+    if (p->top_k < 1 || p->top_k > kMaxTopK)
+        return fail(LD_ERR_INVALID, "top_k must be in [1, %d], got %d", kMaxTopK, p->top_k);
+    if (p->nms_theta < 1 || !(p->nms_theta & 1) || p->nms_rho < 1 || !(p->nms_rho & 1) ||
+        p->nms_theta > 255 || p->nms_rho > 255)
+        return fail(LD_ERR_INVALID, "nms_theta and nms_rho must be odd in [1, 255]");
+    if ((int64_t)p->nms_theta * p->nms_rho * (p->top_k - 1) + 1 > 4096)
+        return fail(LD_ERR_INVALID, "nms_theta*nms_rho*(top_k-1)+1 must be <= 4096");
+    if (p->reserved != 0) return fail(LD_ERR_INVALID, "ld_params.reserved must be 0");
+    if (p->edge_capacity < 0) return fail(LD_ERR_INVALID, "edge_capacity must be >= 0");
+    return LD_OK;
+}
+
+int cand_m(const ld_params &p) { return p.nms_theta * p.nms_rho * (p.top_k - 1) + 1; }
+
+// Image size rules plus the guarantee the voting kernel relies on: every
+// pixel's Q16 rho lies in [-D, D].  rho is linear in (x, y), so checking the
+// four corners for every table entry is exact.
+ld_status check_size(int w, int h, const ld_params &p, const std::vector<int32_t> *trig) {
+    if (w < 3 || h < 3 || (int64_t)w + h > 32767)
+        return fail(LD_ERR_INVALID, "image size %dx%d: need w, h >= 3 and w + h <= 32767", w, h);
+    const int64_t D = rho_max_of(w, h);
+    const int64_t n_rho = 2 * D + 1;
+    if (hough_max_pairs((int)n_rho) < 1)
+        return fail(LD_ERR_INVALID, "image %dx%d: accumulator row of %lld cells does not fit shared memory",
+                    w, h, (long long)n_rho);
+    if (trig) {
+        const int half = p.n_theta / 2;
+        const int64_t xs[2] = {0, w - 1}, ys[2] = {0, h - 1};
+        for (int k = 0; k < p.n_theta; ++k) {
+            const int kk = k <= half ? k : p.n_theta - k;
+            const int64_t c = k <= half ? (*trig)[2 * kk] : -(*trig)[2 * kk];
+            const int64_t s = (*trig)[2 * kk + 1];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    const int64_t v = xs[a] * c + ys[b] * s + 32768;
+                    const int64_t r = v >= 0 ? v / 65536 : -((-v + 65535) / 65536);
+                    if (r < -D || r > D)
+                        return fail(LD_ERR_INVALID, "image %dx%d with %d theta bins: rho leaves [-D, D]", w,
+                                    h, p.n_theta);
+                }
+        }
+    }
+    return LD_OK;
+}
+
+ld_status get_trig(ld_ctx *ctx, int n_theta, const int32_t **dev, const std::vector<int32_t> **host) {
+    auto it = ctx->trig.find(n_theta);
+    if (it == ctx->trig.end()) {
+        std::vector<int32_t> t = make_trig(n_theta);
+        int32_t *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, t.size() * sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(trig)");
+        e = cudaMemcpy(d, t.data(), t.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(e, "cudaMemcpy(trig)");
+        }
+        ctx->trig_host[n_theta] = std::move(t);
+        it = ctx->trig.emplace(n_theta, d).first;
+    }
+    *dev = it->second;
+    if (host) *host = &ctx->trig_host[n_theta];
+    return LD_OK;
+}
+
+ld_params defaults() {
+    ld_params p;
+    p.n_theta = 180;
+    p.threshold = 128;
+    p.border = LD_BORDER_ZERO;
+    p.top_k = 4;
+    p.nms_theta = 5;
+    p.nms_rho = 5;
+    p.min_votes = 1;
+    p.reserved = 0;
+    p.edge_capacity = 0;
+    return p;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Sobel rows per warp: the tallest strip that still gives >= 2 CTAs per SM.
+int pick_rows(int64_t tiles_x, int64_t total_rows_tiles_at_r2, int num_sms) {
+    (void)tiles_x;
+    if (total_rows_tiles_at_r2 / 4 >= 2 * num_sms) return 8;
+    if (total_rows_tiles_at_r2 / 2 >= 2 * num_sms) return 4;
+    return 2;
+}
+
+struct HoughPlan {
+    int n_rho, D, pairs, n_tiles;
+};
+
+HoughPlan plan_hough(int w, int h, int n_theta) {
+    HoughPlan hp;
+    hp.D = (int)rho_max_of(w, h);
+    hp.n_rho = 2 * hp.D + 1;
+    const int n_pairs = n_theta / 2;
+    const int pmax = hough_max_pairs(hp.n_rho);
+    hp.n_tiles = (n_pairs + pmax - 1) / pmax;
+    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
+    hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
+    return hp;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ld_last_error(void) { return g_err.c_str(); }
+
+ld_status ld_params_default(ld_params *p) {
+    if (!p) return fail(LD_ERR_INVALID, "ld_params_default: NULL");
+    *p = defaults();
+    return LD_OK;
+}
+
+ld_status ld_ctx_create(ld_ctx **out, int device) {
+    if (!out) return fail(LD_ERR_INVALID, "ld_ctx_create: NULL out");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(LD_ERR_INVALID, "device %d out of range (%d devices)", device, n);
+    ld_ctx *c = new ld_ctx();
+    c->device = device;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+        c->num_sms = sms;
+    *out = c;
+    return LD_OK;
+}
+
+ld_status ld_ctx_destroy(ld_ctx *ctx) {
+    if (!ctx) return LD_OK;
+    {
+        DeviceGuard g(ctx->device);
+        for (auto &kv : ctx->trig) cudaFree(kv.second);
+        for (auto &e : ctx->ev)
+            if (e) cudaEventDestroy(e);
+        ctx->edges.release();
+        ctx->small.release();
+        ctx->cand.release();
+    }
+    delete ctx;
+    return LD_OK;
+}
+
+ld_status ld_query_sizes(int32_t w, int32_t h, const ld_params *pp, size_t *acc_elems, size_t *edge_elems,
+                         int32_t *D) {
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    std::vector<int32_t> t = make_trig(p.n_theta);
+    st = check_size(w, h, p, &t);
+    if (st != LD_OK) return st;
+    const int64_t d = rho_max_of(w, h);
+    if (acc_elems) *acc_elems = (size_t)p.n_theta * (size_t)(2 * d + 1);
+    if (edge_elems) *edge_elems = (size_t)w * (size_t)h;
+    if (D) *D = (int32_t)d;
+    return LD_OK;
+}
+
+ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames, int64_t max_acc_cells,
+                         const ld_params *pp) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_reserve: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (max_pixels < 0 || max_frames < 0 || max_acc_cells < 0)
+        return fail(LD_ERR_INVALID, "ld_ctx_reserve: negative size");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    st = get_trig(ctx, p.n_theta, &dt, nullptr);
+    if (st != LD_OK) return st;
+    const int64_t groups_frames = max_frames < kMaxLaunchFrames ? max_frames : kMaxLaunchFrames;
+    if (!ctx->edges.ensure((size_t)(max_pixels + 4 * (int64_t)groups_frames) * 4))
+        return fail(LD_ERR_NOMEM, "scratch edges: %lld pixels", (long long)max_pixels);
+    if (!ctx->small.ensure((size_t)2 * kMaxLaunchFrames * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    const int64_t per_frame = (int64_t)(p.n_theta / 2) * cand_m(p);
+    const int64_t acc_chunks = (max_acc_cells + kSelectChunk - 1) / kSelectChunk;
+    int64_t nc = groups_frames * per_frame;
+    if (acc_chunks * cand_m(p) > nc) nc = acc_chunks * cand_m(p);
+    if (!ctx->cand.ensure((size_t)nc * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    return LD_OK;
+}
+
+ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_enable_timing: NULL ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    if (enable) {
+        for (auto &e : ctx->ev) {
+            if (e) continue;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+        }
+    }
+    ctx->timing = enable != 0;
+    return LD_OK;
+}
+
+ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]) {
+    if (!ctx || !ms) return fail(LD_ERR_INVALID, "ld_ctx_stage_ms: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->timed_once) return fail(LD_ERR_INVALID, "no timed ld_detect_batch call yet");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    cudaError_t r = cudaEventSynchronize(ctx->ev[3]);
+    if (r != cudaSuccess) return cuda_fail(r, "cudaEventSynchronize");
+    for (int i = 0; i < 3; ++i) {
+        r = cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaEventElapsedTime");
+    }
+    return LD_OK;
+}
+
+ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
+                            const ld_params *pp, uint8_t *d_bin, uint32_t *d_edges, int32_t *d_edge_count,
+                            void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_sobel_binarize: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, nullptr);
+    if (st != LD_OK) return st;
+    if (!d_img || !d_edges || !d_edge_count) return fail(LD_ERR_INVALID, "ld_sobel_binarize: NULL buffer");
+    if (pitch < w || (pitch & 15) || !aligned16(d_img) || (d_bin && !aligned16(d_bin)))
+        return fail(LD_ERR_INVALID, "pitch must be >= w and a multiple of 16, buffers 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_edge_count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
+    SobelLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.n = 1;
+    L.threshold = p.threshold;
+    L.border = p.border;
+    const int tiles_x = (w + kSobelTileW - 1) / kSobelTileW;
+    const int64_t r2tiles = (int64_t)tiles_x * ((h + 15) / 16);
+    L.rows_per_warp = pick_rows(tiles_x, r2tiles, ctx->num_sms);
+    const int rows_cta = L.rows_per_warp * (kSobelThreads / 32);
+    SobelFrame &F = L.f[0];
+    F.img = d_img;
+    F.bin = d_bin;
+    F.edges = d_edges;
+    F.count = d_edge_count;
+    F.cap = p.edge_capacity > 0 ? p.edge_capacity : (int64_t)w * h;
+    F.w = w;
+    F.h = h;
+    F.pitch = pitch;
+    F.tile_begin = 0;
+    F.tiles_x = tiles_x;
+    const int n_ctas = tiles_x * ((h + rows_cta - 1) / rows_cta);
+    e = launch_sobel(L, n_ctas, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+    return LD_OK;
+}
+
+ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_edge_count, int32_t w,
+                        int32_t h, const ld_params *pp, int32_t *d_acc, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_hough_vote: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (!d_edges || !d_edge_count || !d_acc) return fail(LD_ERR_INVALID, "ld_hough_vote: NULL buffer");
+    if (!aligned16(d_edges)) return fail(LD_ERR_INVALID, "d_edges must be 16-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, ht);
+    if (st != LD_OK) return st;
+    const HoughPlan hp = plan_hough(w, h, p.n_theta);
+    int ns = (ctx->num_sms + hp.n_tiles / 2) / hp.n_tiles;
+    if (ns < 1) ns = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ns > 1) {
+        cudaError_t e = cudaMemsetAsync(d_acc, 0, (size_t)p.n_theta * hp.n_rho * sizeof(int32_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(acc)");
+    }
+    HoughLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.n = 1;
+    L.n_theta = p.n_theta;
+    L.mode = kHoughFullAcc;
+    L.trig = dt;
+    HoughFrame &F = L.f[0];
+    F.edges = d_edges;
+    F.count = d_edge_count;
+    F.cap = p.edge_capacity > 0 ? p.edge_capacity : (int64_t)w * h;
+    F.acc = d_acc;
+    F.w = w;
+    F.h = h;
+    F.D = hp.D;
+    F.n_rho = hp.n_rho;
+    F.unit_begin = 0;
+    F.n_splits = ns;
+    F.pairs_per_tile = hp.pairs;
+    F.n_tiles = hp.n_tiles;
+    cudaError_t e = launch_hough(L, hp.n_tiles * ns, hp.pairs, (int64_t)hp.pairs * hp.n_rho, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+    return LD_OK;
+}
+
+ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_theta, int32_t n_rho,
+                         const ld_params *pp, ld_peak *d_peaks, int32_t *d_n_peaks, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_hough_peaks: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    p.n_theta = (n_theta >= 2 && !(n_theta & 1)) ? n_theta : 2;   // n_theta of the table is unused here
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (n_theta < 1 || n_theta > kMaxTheta || n_rho < 1 || n_rho > 65535)
+        return fail(LD_ERR_INVALID, "accumulator %d x %d: need 1 <= n_theta <= %d, 1 <= n_rho <= 65535",
+                    n_theta, n_rho, kMaxTheta);
+    if (!d_acc || !d_peaks || !d_n_peaks) return fail(LD_ERR_INVALID, "ld_hough_peaks: NULL buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int M = cand_m(p);
+    const int64_t cells = (int64_t)n_theta * n_rho;
+    const int n_chunks = (int)((cells + kSelectChunk - 1) / kSelectChunk);
+    if (!ctx->cand.ensure((size_t)n_chunks * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    uint64_t *cand = (uint64_t *)ctx->cand.p;
+    cudaStream_t s = (cudaStream_t)stream;
+    SelectLaunch SL;
+    std::memset(&SL, 0, sizeof SL);
+    SL.n = 1;
+    SL.cand_m = M;
+    SL.min_votes = p.min_votes;
+    SL.j[0].acc = d_acc;
+    SL.j[0].cand = cand;
+    SL.j[0].cells = cells;
+    SL.j[0].n_rho = n_rho;
+    SL.j[0].n_chunks = n_chunks;
+    SL.j[0].chunk_begin = 0;
+    cudaError_t e = launch_select(SL, n_chunks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "select launch");
+    MergeLaunch ML;
+    std::memset(&ML, 0, sizeof ML);
+    ML.n = 1;
+    ML.top_k = p.top_k;
+    ML.nms_theta = p.nms_theta;
+    ML.nms_rho = p.nms_rho;
+    ML.j[0].cand = cand;
+    ML.j[0].n_cand = (int64_t)n_chunks * M;
+    ML.j[0].peaks = d_peaks;
+    ML.j[0].n_peaks = d_n_peaks;
+    e = launch_merge(ML, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+    return LD_OK;
+}
+
+ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                          ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_batch: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1) return fail(LD_ERR_INVALID, "ld_detect_batch: need n >= 1 frames");
+    if (!d_peaks || !d_n_peaks || !d_status) return fail(LD_ERR_INVALID, "ld_detect_batch: NULL output");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        const ld_frame &f = h_frames[i];
+        st = check_size(f.w, f.h, p, ht);
+        if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
+        if (!f.img || f.pitch < f.w || (f.pitch & 15) || !aligned16(f.img) || f.reserved != 0)
+            return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
+    }
+    const int M = cand_m(p);
+    // scratch for the largest group of frames
+    int64_t max_edges = 0, max_cand = 0;
+    for (int g0 = 0; g0 < n; g0 += kMaxLaunchFrames) {
+        const int g1 = g0 + kMaxLaunchFrames < n ? g0 + kMaxLaunchFrames : n;
+        int64_t ed = 0, ca = 0;
+        for (int i = g0; i < g1; ++i) {
+            ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
+            ca += (int64_t)plan_hough(h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles * M;
+        }
+        if (ed > max_edges) max_edges = ed;
+        if (ca > max_cand) max_cand = ca;
+    }
+    if (!ctx->edges.ensure((size_t)max_edges * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
+    if (!ctx->small.ensure((size_t)2 * kMaxLaunchFrames * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    if (!ctx->cand.ensure((size_t)max_cand * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    uint32_t *edges = (uint32_t *)ctx->edges.p;
+    int32_t *counts = (int32_t *)ctx->small.p;
+    int32_t *flags = counts + kMaxLaunchFrames;
+    uint64_t *cand = (uint64_t *)ctx->cand.p;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    SobelLaunch SLn;
+    HoughLaunch HLn;
+    MergeLaunch MLn;
+
+    for (int g0 = 0; g0 < n; g0 += kMaxLaunchFrames) {
+        const int g1 = g0 + kMaxLaunchFrames < n ? g0 + kMaxLaunchFrames : n;
+        const int gn = g1 - g0;
+        cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)2 * kMaxLaunchFrames * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
+        std::memset(&SLn, 0, sizeof SLn);
+        std::memset(&HLn, 0, sizeof HLn);
+        std::memset(&MLn, 0, sizeof MLn);
+        SLn.n = gn;
+        SLn.threshold = p.threshold;
+        SLn.border = p.border;
+        int64_t tiles_r2 = 0;
+        for (int i = g0; i < g1; ++i) {
+            const int tx = (h_frames[i].w + kSobelTileW - 1) / kSobelTileW;
+            tiles_r2 += (int64_t)tx * ((h_frames[i].h + 15) / 16);
+        }
+        SLn.rows_per_warp = pick_rows(0, tiles_r2, ctx->num_sms);
+        const int rows_cta = SLn.rows_per_warp * (kSobelThreads / 32);
+        HLn.n = gn;
+        HLn.n_theta = p.n_theta;
+        HLn.mode = kHoughCandidates;
+        HLn.cand_m = M;
+        HLn.min_votes = p.min_votes;
+        HLn.trig = dt;
+        MLn.n = gn;
+        MLn.top_k = p.top_k;
+        MLn.nms_theta = p.nms_theta;
+        MLn.nms_rho = p.nms_rho;
+        int sob_ctas = 0, hough_ctas = 0, pmax = 1;
+        int64_t eoff = 0, coff = 0;
+        for (int i = g0; i < g1; ++i) {
+            const ld_frame &fr = h_frames[i];
+            const int k = i - g0;
+            SobelFrame &SF = SLn.f[k];
+            SF.img = fr.img;
+            SF.bin = nullptr;
+            SF.edges = edges + eoff;
+            SF.count = counts + k;
+            SF.cap = (int64_t)fr.w * fr.h;
+            SF.w = fr.w;
+            SF.h = fr.h;
+            SF.pitch = fr.pitch;
+            SF.tile_begin = sob_ctas;
+            SF.tiles_x = (fr.w + kSobelTileW - 1) / kSobelTileW;
+            sob_ctas += SF.tiles_x * ((fr.h + rows_cta - 1) / rows_cta);
+
+            const HoughPlan hp = plan_hough(fr.w, fr.h, p.n_theta);
+            HoughFrame &HF = HLn.f[k];
+            HF.edges = edges + eoff;
+            HF.count = counts + k;
+            HF.cap = SF.cap;
+            HF.acc = nullptr;
+            HF.cand = cand + coff;
+            HF.flags = flags + k;
+            HF.w = fr.w;
+            HF.h = fr.h;
+            HF.D = hp.D;
+            HF.n_rho = hp.n_rho;
+            HF.unit_begin = hough_ctas;
+            HF.n_splits = 1;
+            HF.pairs_per_tile = hp.pairs;
+            HF.n_tiles = hp.n_tiles;
+            hough_ctas += hp.n_tiles;
+            if (hp.pairs > pmax) pmax = hp.pairs;
+
+            MergeJob &MJ = MLn.j[k];
+            MJ.cand = cand + coff;
+            MJ.n_cand = (int64_t)hp.n_tiles * M;
+            MJ.peaks = d_peaks + (size_t)i * p.top_k;
+            MJ.n_peaks = d_n_peaks + i;
+            MJ.status = d_status + i;
+            MJ.flags = flags + k;
+
+            eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
+            coff += (int64_t)hp.n_tiles * M;
+        }
+        // dynamic shared memory = max over frames of pairs * n_rho words
+        int64_t words_max = 0;
+        for (int k = 0; k < gn; ++k) {
+            const int64_t wds = (int64_t)HLn.f[k].pairs_per_tile * HLn.f[k].n_rho;
+            if (wds > words_max) words_max = wds;
+        }
+        const bool first = (g0 == 0), last = (g1 == n);
+        if (ctx->timing && first) cudaEventRecord(ctx->ev[0], s);
+        e = launch_sobel(SLn, sob_ctas, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+        if (ctx->timing && first) cudaEventRecord(ctx->ev[1], s);
+        e = launch_hough(HLn, hough_ctas, pmax, words_max, s);
+        if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+        if (ctx->timing && first) cudaEventRecord(ctx->ev[2], s);
+        e = launch_merge(MLn, s);
+        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        if (ctx->timing && last) {
+            cudaEventRecord(ctx->ev[3], s);
+            ctx->timed_once = true;
+        }
+    }
+    return LD_OK;
+}
+
+}  // extern "C"

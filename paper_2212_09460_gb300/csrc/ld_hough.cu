@@ -1,0 +1,384 @@
+// ld_hough.cu -- Step 3, Hough voting r = x cos(theta) + y sin(theta)
+// (Sec. 2.3 Eq. 3, Sec. 4.3), with the sin/cos symmetry of Sec. 3.3
+// (Eqs. 4-5), and the per-tile candidate emission for Step 4.
+//
+// GB300 design.  As in the paper's GPU kernel (Sec. 4.3) every CTA owns a
+// slice of the theta axis in shared memory and counts the votes of all edge
+// pixels with shared-memory atomics; unlike it, a CTA owns a tile of theta
+// *pairs* {k, n_theta-k} (Eqs. 4-5: sin equal, cos opposite), so one
+// y*s_k product serves both angles, and the two counts of a pair share one
+// 32-bit word (low half theta_k, high half theta_{n-k}).  A count never
+// exceeds 2*max(w, h) <= 65528 for a list of distinct pixels (a rho strip of
+// width 1 holds at most 2 pixels per row or per column), so 16 bits are
+// exact and the tile holds twice as many angles.  rho comes from the integer
+// Q16 table: idx = (y*s + 32768 + D*65536 +/- x*c) >> 16, computed modulo
+// 2^32 (its true value lies in [0, (2D+1)*65536)).
+//
+// The edge list is streamed through shared memory in chunks by the bulk-copy
+// engine (cp.async.bulk, completion on an mbarrier, 3 stages).  Lane l of
+// every warp reads edges l*S + o with S odd, so the 32 lanes hit 32 distinct
+// banks and sit far apart in the row-major list, which keeps lanes of a warp
+// from voting into the same cell at once (that serialises shared atomics).
+// Every mbarrier wait is bounded; a wait that gives up sets the frame's
+// timeout flag and the CTA leaves after draining its own copies.
+#include "ld_internal.cuh"
+#include "ld_select.cuh"
+
+namespace ld {
+namespace {
+
+constexpr int kRingBytes = kStages * kChunkEdges * 4;   // 30336 bytes
+constexpr int kRingBytesPad = (kRingBytes + 127) / 128 * 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true if the phase completed, false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// theta of the low / high half of pair slot p of a tile starting at pair j0.
+__device__ __forceinline__ int theta_lo(int j0, int p) { return j0 + p; }
+__device__ __forceinline__ int theta_hi(int j0, int p, int n_theta) {
+    int j = j0 + p;
+    return j == 0 ? n_theta / 2 : n_theta - j;
+}
+
+// Ordered column q of a tile (theta ascending) -> (slot, half).
+// Low halves carry theta j0..j0+np-1 (< n/2), high halves theta > n/2 except
+// slot 0 of the first tile, whose high half is theta = n/2.
+__device__ __forceinline__ void ordered_col(int q, int np, bool has0, int &slot, int &half) {
+    if (q < np) { slot = q; half = 0; return; }
+    int q2 = q - np;
+    half = 1;
+    if (has0) slot = (q2 == 0) ? 0 : np - q2;
+    else slot = np - 1 - q2;
+}
+
+template <int PMAX>
+__global__ void __launch_bounds__(kHoughThreads, 1)
+hough_kernel(const __grid_constant__ HoughLaunch L) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ uint64_t bars[kStages];
+    __shared__ SelectSmem S;
+    __shared__ int abort_flag;
+
+    // ---- which frame / theta tile / edge split
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (L.f[mid].unit_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const HoughFrame &F = L.f[lo];
+    const int local = blockIdx.x - F.unit_begin;
+    const int ns = F.n_splits;
+    const int tile = local / ns, split = local % ns;
+    const int n_theta = L.n_theta;
+    const int j0 = tile * F.pairs_per_tile;
+    const int np = min(F.pairs_per_tile, n_theta / 2 - j0);
+    const bool has0 = (j0 == 0);
+    const int n_rho = F.n_rho;
+    const uint32_t K0 = 32768u + (uint32_t)F.D * 65536u;
+    const uint32_t W = (uint32_t)F.w, H = (uint32_t)F.h;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem_raw + kRingBytesPad);
+    const int words = np * n_rho;
+
+    // ---- Q16 (c, s) of the tile's pairs in registers
+    uint32_t cq[PMAX], sq[PMAX];
+#pragma unroll
+    for (int p = 0; p < PMAX; ++p) {
+        cq[p] = 0; sq[p] = 0;
+        if (p < np) {
+            cq[p] = (uint32_t)L.trig[2 * (j0 + p)];
+            sq[p] = (uint32_t)L.trig[2 * (j0 + p) + 1];
+        }
+    }
+
+    // ---- zero the accumulator tile, set up the barriers
+    for (int i = tid; i < words; i += kHoughThreads) acc[i] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    // ---- this CTA's edge range (split boundaries are multiples of 4 edges)
+    int64_t E = (int64_t)*F.count;
+    if (E > F.cap) E = F.cap;
+    if (E < 0) E = 0;
+    const int64_t e0 = (E * split / ns) & ~int64_t(3);
+    const int64_t e1 = (split + 1 == ns) ? E : ((E * (split + 1) / ns) & ~int64_t(3));
+    const int64_t n_chunks = (e1 > e0) ? (e1 - e0 + kChunkEdges - 1) / kChunkEdges : 0;
+
+    auto issue = [&](int64_t c, int st) {
+        const int64_t start = e0 + c * kChunkEdges;
+        const int n_c = (int)((e1 - start) < kChunkEdges ? (e1 - start) : kChunkEdges);
+        const int n4 = n_c & ~3;
+        if (n4 > 0) {
+            mbar_arrive_expect_tx(&bars[st], (uint32_t)n4 * 4u);
+            bulk_g2s(ring + st * kChunkEdges, F.edges + start, (uint32_t)n4 * 4u, &bars[st]);
+        } else {
+            mbar_arrive(&bars[st]);
+        }
+    };
+    if (tid == 0) {
+        for (int64_t c = 0; c < n_chunks && c < kStages; ++c) issue(c, (int)c);
+    }
+
+    int64_t c = 0;
+    for (; c < n_chunks; ++c) {
+        const int st = (int)(c % kStages);
+        const uint32_t par = (uint32_t)((c / kStages) & 1);
+        const bool ok = mbar_wait_bounded(&bars[st], par);
+        if (!ok) abort_flag = 1;
+        if (ok) {
+            const uint32_t *buf = ring + st * kChunkEdges;
+            const int64_t start = e0 + c * kChunkEdges;
+            const int n_c = (int)((e1 - start) < kChunkEdges ? (e1 - start) : kChunkEdges);
+            const int n4 = n_c & ~3;
+            for (int o = warp; o < kChunkSeg; o += kHoughWarps) {
+                const int idx = lane * kChunkSeg + o;
+                if (idx < n_c) {
+                    const uint32_t e = (idx < n4) ? buf[idx] : F.edges[start + idx];
+                    const uint32_t x = e & 0xFFFFu, y = e >> 16;
+                    if (x < W && y < H) {
+                        if (has0) {   // theta = 0 (rho = x) and theta = 90 deg (rho = y)
+                            atomicAdd(acc + (x + (uint32_t)F.D), 1u);
+                            atomicAdd(acc + (y + (uint32_t)F.D), 0x10000u);
+                        }
+#pragma unroll
+                        for (int p = 0; p < PMAX; ++p) {
+                            if (p < np && (p > 0 || !has0)) {
+                                const uint32_t A = y * sq[p] + K0;
+                                const uint32_t B = x * cq[p];
+                                uint32_t *col = acc + p * n_rho;
+                                atomicAdd(col + ((A + B) >> 16), 1u);        // theta_k
+                                atomicAdd(col + ((A - B) >> 16), 0x10000u);  // theta_{n-k}
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0 && c + kStages < n_chunks) {
+            fence_proxy_async();
+            issue(c + kStages, st);
+        }
+    }
+
+    if (abort_flag) {
+        // drain this CTA's own copies still in flight (bounded), flag the frame
+        if (tid == 0) {
+            for (int64_t k = c; k < n_chunks && k < c + kStages; ++k)
+                (void)mbar_wait_bounded(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+            if (F.flags) atomicOr(F.flags, kFlagTimeout);
+        }
+        return;
+    }
+    __syncthreads();
+
+    if (L.mode == kHoughFullAcc) {
+        for (int p = 0; p < np; ++p) {
+            const int ta = theta_lo(j0, p), tb = theta_hi(j0, p, n_theta);
+            int32_t *ga = F.acc + (size_t)ta * n_rho;
+            int32_t *gb = F.acc + (size_t)tb * n_rho;
+            for (int r = tid; r < n_rho; r += kHoughThreads) {
+                const uint32_t wv = acc[p * n_rho + r];
+                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+                if (ns == 1) {
+                    ga[r] = a;
+                    gb[r] = b;
+                } else {
+                    if (a) atomicAdd(ga + r, a);
+                    if (b) atomicAdd(gb + r, b);
+                }
+            }
+        }
+        return;
+    }
+
+    // ---- candidate mode: exact local top-M of this tile (see ld_select.cuh)
+    const int M = L.cand_m;
+    const int32_t mv = L.min_votes;
+    uint64_t *out = F.cand + (size_t)tile * M;
+
+    // pass 0: included count and the value range
+    int cnt = 0;
+    uint32_t vmax = 0;
+    for (int i = tid; i < words; i += kHoughThreads) {
+        const uint32_t wv = acc[i];
+        const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+        if (a >= mv) { ++cnt; vmax = max(vmax, (uint32_t)a); }
+        if (b >= mv) { ++cnt; vmax = max(vmax, (uint32_t)b); }
+    }
+    const int total = block_sum(cnt, S);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+    if (lane == 0) S.red[warp] = vmax;
+    __syncthreads();
+    uint32_t gmax = 0;
+    for (int w = 0; w < kHoughWarps; ++w) gmax = max(gmax, S.red[w]);
+    __syncthreads();
+
+    const bool all_in = total <= M;
+    if (tid == 0) {
+        S.prefix = 0x80000000u;
+        S.pmask = 0xFFFF0000u;
+        S.rank = M;
+        S.out_n = 0;
+    }
+    __syncthreads();
+    if (!all_in) {
+        int top_shift = 0;   // highest nibble holding a set bit of the max count
+        for (int s = 12; s > 0; s -= 4)
+            if (gmax >> s) { top_shift = s; break; }
+        for (int shift = top_shift; shift >= 0; shift -= 4) {
+            uint32_t wh[16];
+#pragma unroll
+            for (int d = 0; d < 16; ++d) wh[d] = 0;
+            const uint32_t prefix = S.prefix, pmask = S.pmask;
+            for (int base = 0; base < words; base += kHoughThreads) {
+                const int i = base + tid;
+                const uint32_t wv = (i < words) ? acc[i] : 0u;
+                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+                const uint32_t ua = (uint32_t)a ^ 0x80000000u, ub = (uint32_t)b ^ 0x80000000u;
+                ballot_digits(wh, i < words && a >= mv && (ua & pmask) == prefix, (ua >> shift) & 15u);
+                ballot_digits(wh, i < words && b >= mv && (ub & pmask) == prefix, (ub >> shift) & 15u);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int d = 0; d < 16; ++d) S.hist[warp][d] = wh[d];
+            }
+            select_digit(S, shift);
+        }
+    }
+    const uint32_t ustar = S.prefix;
+    const int need = all_in ? 0 : S.rank;   // cells equal to u* to take, in order
+    __syncthreads();
+
+    // ordered emission over per-thread contiguous ranges of the ordered cells
+    const int64_t ncell = 2 * (int64_t)words;
+    const int64_t r0 = ncell * tid / kHoughThreads, r1 = ncell * (tid + 1) / kHoughThreads;
+    auto cell_at = [&](int64_t li, int &theta, int &rho) -> int32_t {
+        const int q = (int)(li / n_rho);
+        rho = (int)(li - (int64_t)q * n_rho);
+        int slot, half;
+        ordered_col(q, np, has0, slot, half);
+        theta = half ? theta_hi(j0, slot, n_theta) : theta_lo(j0, slot);
+        const uint32_t wv = acc[slot * n_rho + rho];
+        return (int32_t)(half ? (wv >> 16) : (wv & 0xFFFFu));
+    };
+    int ties = 0;
+    if (!all_in) {
+        for (int64_t li = r0; li < r1; ++li) {
+            int th, rh;
+            const int32_t v = cell_at(li, th, rh);
+            ties += (v >= mv && ((uint32_t)v ^ 0x80000000u) == ustar);
+        }
+    }
+    // exclusive block scan of the tie counts
+    int incl = ties;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) S.red[warp] = (uint32_t)incl;
+    __syncthreads();
+    int woff = 0;
+    for (int w = 0; w < warp; ++w) woff += (int)S.red[w];
+    int trank = woff + incl - ties;
+    for (int64_t li = r0; li < r1; ++li) {
+        int th, rh;
+        const int32_t v = cell_at(li, th, rh);
+        if (v < mv) continue;
+        const uint32_t u = (uint32_t)v ^ 0x80000000u;
+        if (all_in || u > ustar) {
+            const int slot = atomicAdd(&S.out_n, 1);
+            if (slot < M) out[slot] = peak_key(v, th, rh);
+        } else if (u == ustar) {
+            if (trank < need) out[(M - need) + trank] = peak_key(v, th, rh);
+            ++trank;
+        }
+    }
+    __syncthreads();
+    // unused slots (fewer included cells than M) are empty keys
+    const int filled = all_in ? min(S.out_n, M) : M;
+    for (int i = filled + tid; i < M; i += kHoughThreads) out[i] = 0ull;
+}
+
+template <int PMAX>
+cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t s) {
+    static bool attr_set = false;   // per-process; set before the first launch
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemLimit - (int)sizeof(SelectSmem) - 256);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    hough_kernel<PMAX><<<n_ctas, kHoughThreads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int hough_max_pairs(int n_rho) {
+    const int avail = kSmemLimit - (int)sizeof(SelectSmem) - 256 - kRingBytesPad;
+    int p = avail / (n_rho * 4);
+    return p < 32 ? p : 32;
+}
+
+cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_t acc_words_max,
+                         cudaStream_t s) {
+    if (n_ctas <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kRingBytesPad + (size_t)acc_words_max * 4;
+    if (pairs_max <= 4) return launch_p<4>(L, n_ctas, smem, s);
+    if (pairs_max <= 8) return launch_p<8>(L, n_ctas, smem, s);
+    if (pairs_max <= 12) return launch_p<12>(L, n_ctas, smem, s);
+    if (pairs_max <= 16) return launch_p<16>(L, n_ctas, smem, s);
+    if (pairs_max <= 24) return launch_p<24>(L, n_ctas, smem, s);
+    return launch_p<32>(L, n_ctas, smem, s);
+}
+
+}  // namespace ld

@@ -1,0 +1,146 @@
+// ld_internal.cuh -- declarations shared by the CUDA translation units of
+// libld.so (kernels, launch descriptors, small device helpers).  Nothing here
+// is part of the public C ABI, which lives in include/ld.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ld.h"
+
+namespace ld {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxLaunchFrames = 128;   // frame descriptors passed by value per launch
+constexpr int kMaxTopK = 16;
+constexpr int kMaxTheta = 4096;
+constexpr int kSmemLimit = 232448;      // 227 KB opt-in dynamic shared memory per CTA
+
+// Device-side error bits (OR-ed into a per-frame flag word).
+constexpr int32_t kFlagTimeout = 1;
+
+// Bounded spin: polls of an mbarrier before a wait gives up.
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// ---------------------------------------------------------------- Sobel
+constexpr int kSobelThreads = 256;      // 8 warps
+constexpr int kSobelTileW = 512;        // 32 lanes x 16 pixels
+
+struct SobelFrame {
+    const uint8_t *img;
+    uint8_t *bin;          // nullable
+    uint32_t *edges;
+    int32_t *count;
+    int64_t cap;
+    int32_t w, h, pitch;
+    int32_t tile_begin;    // first CTA of this frame
+    int32_t tiles_x;
+    int32_t pad_;
+};
+
+struct SobelLaunch {
+    int32_t n;
+    int32_t threshold;
+    int32_t border;
+    int32_t rows_per_warp;
+    SobelFrame f[kMaxLaunchFrames];
+};
+
+// ---------------------------------------------------------------- Hough
+constexpr int kHoughThreads = 512;      // 16 warps
+constexpr int kHoughWarps = kHoughThreads / 32;
+// Edge chunk streamed per stage: 32 lane segments of odd length S, so that the
+// 32 lanes of a warp read 32 distinct shared-memory banks (index l*S + o).
+constexpr int kChunkSeg = 5 * kHoughWarps - 1;   // S = 79
+constexpr int kChunkEdges = 32 * kChunkSeg;      // 2528 edges = 10112 bytes
+constexpr int kStages = 3;
+
+enum HoughMode : int32_t {
+    kHoughFullAcc = 0,      // write the int32 accumulator (store or atomic add)
+    kHoughCandidates = 1,   // emit per-tile top-M candidate keys instead
+};
+
+struct HoughFrame {
+    const uint32_t *edges;
+    const int32_t *count;
+    int64_t cap;
+    int32_t *acc;          // [n_theta][n_rho] (full-acc mode)
+    uint64_t *cand;        // [n_tiles][M] keys (candidate mode)
+    int32_t *flags;        // nullable per-frame error flags
+    int32_t w, h, D, n_rho;
+    int32_t unit_begin;    // first CTA of this frame
+    int32_t n_splits;      // CTAs sharing one theta tile (edge ranges)
+    int32_t pairs_per_tile;
+    int32_t n_tiles;
+};
+
+struct HoughLaunch {
+    int32_t n;
+    int32_t n_theta;
+    int32_t mode;
+    int32_t cand_m;        // M per tile (candidate mode)
+    int32_t min_votes;
+    int32_t pad_;
+    const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
+    HoughFrame f[kMaxLaunchFrames];
+};
+
+// ---------------------------------------------------------------- peaks
+constexpr int kSelectThreads = 512;
+constexpr int kMergeThreads = 512;
+constexpr int kSelectChunk = 16384;     // accumulator cells per candidate CTA
+
+struct SelectJob {          // candidates from a full accumulator
+    const int32_t *acc;
+    uint64_t *cand;         // [n_chunks][M]
+    int64_t cells;
+    int32_t n_rho;
+    int32_t n_chunks;
+    int32_t chunk_begin;    // first CTA of this accumulator
+    int32_t pad_;
+};
+
+struct SelectLaunch {
+    int32_t n;
+    int32_t cand_m;
+    int32_t min_votes;
+    int32_t pad_;
+    SelectJob j[kMaxLaunchFrames];
+};
+
+struct MergeJob {
+    const uint64_t *cand;
+    int64_t n_cand;
+    ld_peak *peaks;
+    int32_t *n_peaks;
+    int32_t *status;        // nullable: per-frame ld_status output
+    const int32_t *flags;   // nullable: per-frame device error flags
+};
+
+struct MergeLaunch {
+    int32_t n;
+    int32_t top_k;
+    int32_t nms_theta;
+    int32_t nms_rho;
+    MergeJob j[kMaxLaunchFrames];
+};
+
+// Candidate key: votes desc, theta asc, rho asc  <=>  key desc.  The theta
+// field is 0xFFFF - theta >= 0xF000 (theta < 4096), so a valid key is never 0.
+__host__ __device__ inline uint64_t peak_key(int32_t votes, int32_t theta, int32_t rho) {
+    return (uint64_t(uint32_t(votes) ^ 0x80000000u) << 32) |
+           (uint64_t(0xFFFFu - uint32_t(theta)) << 16) | uint64_t(0xFFFFu - uint32_t(rho));
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s);
+// acc_words_max: the largest pairs_per_tile * n_rho over the launch's frames.
+cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_t acc_words_max,
+                         cudaStream_t s);
+cudaError_t launch_select(const SelectLaunch &L, int n_ctas, cudaStream_t s);
+cudaError_t launch_merge(const MergeLaunch &L, cudaStream_t s);
+
+// Largest pairs-per-tile whose packed accumulator fits shared memory.
+int hough_max_pairs(int n_rho);
+
+}  // namespace ld

@@ -1,0 +1,81 @@
+// ld_select.cuh -- exact block-wide top-M selection used to cut the Hough
+// peak search (Sec. 2.3 "Hough Peak") down to a few candidates per tile.
+//
+// Why it is exact: the greedy peak picker takes, at pick j, the first cell
+// in the order (votes desc, theta asc, rho asc) that is not suppressed; each
+// earlier pick suppresses at most nms_theta*nms_rho cells, so pick j has rank
+// <= (nms_theta*nms_rho)*(j-1)+1 = M for j <= top_k.  Any partition of the
+// accumulator into tiles whose local top-M (same order) are kept therefore
+// keeps every cell the greedy can pick, and the greedy over that union gives
+// the same peaks as over the whole accumulator.
+//
+// Selection: a most-significant-digit radix select with 4-bit digits on the
+// order-preserving key u = votes ^ 0x80000000 finds u* (the M-th largest u
+// among cells with votes >= min_votes) and how many cells equal to u* must be
+// taken; the cells equal to u* are taken in (theta, rho) order.  Digit
+// histograms are built with warp ballots (no shared atomics, so the many
+// equal small counts of an accumulator cost nothing extra).
+#pragma once
+
+#include "ld_internal.cuh"
+
+namespace ld {
+
+struct SelectSmem {
+    uint32_t hist[32][16];   // per-warp digit counts
+    uint32_t digit_sum[16];
+    uint32_t red[32];
+    uint32_t prefix, pmask;
+    int32_t rank;            // remaining rank inside the current prefix
+    int32_t total;           // included cells
+    int32_t out_n;           // emitted so far (cells > u*)
+    int32_t tie_run;         // ties taken so far (ordered pass)
+};
+
+// Add the ballot counts of one warp-step to this warp's 16 digit counters
+// (kept by every lane in registers).
+__device__ __forceinline__ void ballot_digits(uint32_t (&wh)[16], bool m, uint32_t dig) {
+#pragma unroll
+    for (int d = 0; d < 16; ++d) wh[d] += __popc(__ballot_sync(0xFFFFFFFFu, m && dig == (uint32_t)d));
+}
+
+// Block sum of a per-thread int.
+__device__ __forceinline__ int block_sum(int v, SelectSmem &S) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    __syncthreads();
+    if (lane == 0) S.red[warp] = (uint32_t)v;
+    __syncthreads();
+    int t = 0;
+    for (int w = 0; w < nw; ++w) t += (int)S.red[w];
+    __syncthreads();
+    return t;
+}
+
+// After every warp has stored its 16 counts into S.hist[warp], pick the digit
+// holding rank S.rank (counting from the top), narrow the prefix.
+__device__ __forceinline__ void select_digit(SelectSmem &S, int shift) {
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        uint32_t s = 0;
+        for (int w = 0; w < nw; ++w) s += S.hist[w][threadIdx.x];
+        S.digit_sum[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int rank = S.rank, cum = 0, d = 15;
+        for (; d > 0; --d) {
+            int c = (int)S.digit_sum[d];
+            if (cum + c >= rank) break;
+            cum += c;
+        }
+        S.rank = rank - cum;
+        S.prefix |= (uint32_t)d << shift;
+        S.pmask |= 15u << shift;
+    }
+    __syncthreads();
+}
+
+}  // namespace ld

@@ -1,0 +1,203 @@
+// ld_sobel.cu -- Steps 1-2 fused: Sobel |Gx|+|Gy| on the zero-padded image
+// (Sec. 2.1 Eq. 1, Sec. 3.1, Sec. 4.1), binarization against the threshold
+// (Sec. 2.2, Sec. 4.2), and compaction of the 255 pixels into the packed
+// (y << 16) | x edge list the voting stage reads (Sec. 4.3).
+//
+// GB300 design (differs from the paper's 16x16-thread-block K80 kernel,
+// Eq. 6): one warp covers 512 contiguous pixels of a row with one 16-byte
+// load per lane, so every row is read with fully coalesced 512-byte warp
+// transactions.  The 3x3 window slides down R rows in registers (each image
+// row is loaded once per warp strip, plus two halo rows), the left/right
+// neighbour bytes come from the adjacent lanes through shuffles, and zero
+// padding is virtual (never materialised).  Edge bits are compacted with a
+// block-wide prefix sum and one global atomic per CTA.
+#include "ld_internal.cuh"
+
+namespace ld {
+namespace {
+
+struct Row {
+    uint32_t v[4];   // 16 pixels
+    uint32_t l, r;   // pixel x0-1 and x0+16
+};
+
+__device__ __forceinline__ uint4 ldg_nc_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+// Load the 16 pixels of row y starting at x0, with the two neighbour bytes.
+// Pixels outside the image (x >= w, y outside [0,h)) read as 0.  All 32 lanes
+// of the warp must call this (shuffles).
+__device__ __forceinline__ Row load_row(const SobelFrame &F, int x0, int y, int lane) {
+    Row R;
+    R.v[0] = R.v[1] = R.v[2] = R.v[3] = 0;
+    const bool row_ok = (y >= 0) && (y < F.h);
+    if (row_ok && x0 < F.w) {
+        const uint8_t *p = F.img + (size_t)y * F.pitch + x0;
+        uint4 q = ldg_nc_v4(p);
+        R.v[0] = q.x; R.v[1] = q.y; R.v[2] = q.z; R.v[3] = q.w;
+        int nvalid = F.w - x0;
+        if (nvalid < 16) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int k = nvalid - 4 * i;
+                uint32_t m = k >= 4 ? 0xFFFFFFFFu : (k <= 0 ? 0u : ((1u << (8 * k)) - 1u));
+                R.v[i] &= m;
+            }
+        }
+    }
+    uint32_t left = __shfl_up_sync(0xFFFFFFFFu, R.v[3] >> 24, 1);
+    uint32_t right = __shfl_down_sync(0xFFFFFFFFu, R.v[0] & 0xFFu, 1);
+    if (lane == 0) {
+        left = (row_ok && x0 > 0 && x0 - 1 < F.w) ? F.img[(size_t)y * F.pitch + x0 - 1] : 0u;
+    }
+    if (lane == 31) {
+        right = (row_ok && x0 + 16 < F.w) ? F.img[(size_t)y * F.pitch + x0 + 16] : 0u;
+    }
+    R.l = left;
+    R.r = right;
+    return R;
+}
+
+__device__ __forceinline__ int px(const Row &R, int i) {   // i in [-1, 16]
+    if (i < 0) return (int)R.l;
+    if (i > 15) return (int)R.r;
+    return (int)((R.v[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+}
+
+// Eq. 1 for the 16 pixels of the middle row: bit i set iff |Gx|+|Gy| >= thr.
+// Gx = vs(x+1) - vs(x-1) with vs = top + 2 mid + bottom;
+// Gy = vd(x-1) + 2 vd(x) + vd(x+1) with vd = bottom - top.
+__device__ __forceinline__ uint32_t sobel16(const Row &T, const Row &M, const Row &B, int thr) {
+    int vs[18], vd[18];
+#pragma unroll
+    for (int i = -1; i <= 16; ++i) {
+        int t = px(T, i), m = px(M, i), b = px(B, i);
+        vs[i + 1] = t + 2 * m + b;
+        vd[i + 1] = b - t;
+    }
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        int gx = vs[i + 2] - vs[i];
+        int gy = vd[i] + 2 * vd[i + 1] + vd[i + 2];
+        int mag = abs(gx) + abs(gy);
+        bits |= (mag >= thr ? 1u : 0u) << i;
+    }
+    return bits;
+}
+
+// 4 mask bits -> 4 bytes of 0x00 / 0xFF.
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) {
+    return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kSobelThreads)
+sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
+    // frame of this CTA (binary search over tile_begin)
+    const int t = blockIdx.x;
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (L.f[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const SobelFrame &F = L.f[lo];
+    const int local = t - F.tile_begin;
+    const int tx = local % F.tiles_x, ty = local / F.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = tx * kSobelTileW + lane * 16;
+    const int ya = ty * (R * (kSobelThreads / 32)) + warp * R;
+
+    // valid-column mask of this lane's 16 pixels
+    uint32_t colmask = 0;
+    if (x0 < F.w) colmask = (F.w - x0 >= 16) ? 0xFFFFu : ((1u << (F.w - x0)) - 1u);
+    if (L.border == LD_BORDER_CLEAR) {
+        if (x0 == 0) colmask &= ~1u;
+        int xr = F.w - 1 - x0;
+        if (xr >= 0 && xr < 16) colmask &= ~(1u << xr);
+    }
+
+    uint32_t masks[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) masks[r] = 0;
+
+    if (ya < F.h) {   // warp-uniform
+        Row top = load_row(F, x0, ya - 1, lane);
+        Row mid = load_row(F, x0, ya, lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = ya + r;
+            if (y >= F.h) break;   // warp-uniform
+            Row bot = load_row(F, x0, y + 1, lane);
+            uint32_t bits = sobel16(top, mid, bot, L.threshold) & colmask;
+            if (L.border == LD_BORDER_CLEAR && (y == 0 || y == F.h - 1)) bits = 0;
+            masks[r] = bits;
+            if (F.bin != nullptr && x0 < F.pitch) {
+                uint4 o;
+                o.x = spread4(bits & 0xF);
+                o.y = spread4((bits >> 4) & 0xF);
+                o.z = spread4((bits >> 8) & 0xF);
+                o.w = spread4((bits >> 12) & 0xF);
+                *reinterpret_cast<uint4 *>(F.bin + (size_t)y * F.pitch + x0) = o;
+            }
+            top = mid;
+            mid = bot;
+        }
+    }
+
+    // block-wide exclusive prefix of the edge counts, one atomic per CTA
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt += __popc(masks[r]);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    __shared__ int warp_tot[kSobelThreads / 32];
+    __shared__ int cta_base;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < kSobelThreads / 32; ++w) {
+            int v = warp_tot[w];
+            warp_tot[w] = tot;
+            tot += v;
+        }
+        cta_base = tot ? atomicAdd(F.count, tot) : 0;
+    }
+    __syncthreads();
+    int64_t pos = (int64_t)cta_base + warp_tot[warp] + (incl - cnt);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint32_t bits = masks[r];
+        const uint32_t yy = (uint32_t)(ya + r) << 16;
+        while (bits) {
+            int i = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < F.cap) F.edges[pos] = yy | (uint32_t)(x0 + i);
+            ++pos;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s) {
+    if (n_ctas <= 0) return cudaSuccess;
+    switch (L.rows_per_warp) {
+        case 2: sobel_bin_edges_kernel<2><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
+        case 4: sobel_bin_edges_kernel<4><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
+        case 8: sobel_bin_edges_kernel<8><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ld

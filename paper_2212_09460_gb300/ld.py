@@ -1,0 +1,282 @@
+"""Thin Python binding of libld.so (include/ld.h), argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module only
+converts torch tensors into device pointers and the current CUDA stream, and
+turns non-zero ``ld_status`` codes into exceptions.  The C functions are
+exposed under their own names (``ld_sobel_binarize`` ...), taking raw
+integer pointers; :class:`Context` wraps them for torch tensors.  There is
+no fallback: if libld.so is missing, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+from . import build as _build
+
+LD_OK, LD_ERR_INVALID, LD_ERR_CUDA, LD_ERR_NOMEM, LD_ERR_CAPACITY, LD_ERR_TIMEOUT = range(6)
+LD_BORDER_ZERO, LD_BORDER_CLEAR = 0, 1
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ld.h")
+
+
+class LdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ld status {status}: {msg}")
+        self.status = status
+
+
+class ld_params(ctypes.Structure):
+    _fields_ = [("n_theta", ctypes.c_int32), ("threshold", ctypes.c_int32), ("border", ctypes.c_int32),
+                ("top_k", ctypes.c_int32), ("nms_theta", ctypes.c_int32), ("nms_rho", ctypes.c_int32),
+                ("min_votes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("edge_capacity", ctypes.c_int64)]
+
+
+class ld_peak(ctypes.Structure):
+    _fields_ = [("theta_idx", ctypes.c_int32), ("rho_idx", ctypes.c_int32), ("votes", ctypes.c_int32)]
+
+
+class ld_frame(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("pitch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SIGS = {
+    "ld_params_default": [ctypes.POINTER(ld_params)],
+    "ld_ctx_create": [ctypes.POINTER(_P), ctypes.c_int],
+    "ld_ctx_destroy": [_P],
+    "ld_ctx_reserve": [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ld_params)],
+    "ld_query_sizes": [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
+                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                       ctypes.POINTER(ctypes.c_int32)],
+    "ld_sobel_binarize": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
+                          _P, _P, _P, _P],
+    "ld_hough_vote": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P],
+    "ld_hough_peaks": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
+    "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
+                        _P],
+    "ld_ctx_enable_timing": [_P, ctypes.c_int],
+    "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libld.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libld.so not built ({path}); run paper_2212_09460_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.ld_last_error.argtypes = []
+    lib.ld_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/ld.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(r"^LD_API\s+[\w\s\*]*?\b(ld_\w+)\s*\(", text, flags=re.M)
+
+
+def _check(status: int) -> None:
+    if status != LD_OK:
+        raise LdError(status, load().ld_last_error().decode())
+
+
+def params(n_theta=180, threshold=128, border=LD_BORDER_ZERO, top_k=4, nms_theta=5, nms_rho=5,
+           min_votes=1, edge_capacity=0) -> ld_params:
+    p = ld_params()
+    _check(load().ld_params_default(ctypes.byref(p)))
+    p.n_theta, p.threshold, p.border, p.top_k = n_theta, threshold, border, top_k
+    p.nms_theta, p.nms_rho, p.min_votes, p.edge_capacity = nms_theta, nms_rho, min_votes, edge_capacity
+    return p
+
+
+# ------------------------------------------------------------------ raw C names
+
+def ld_params_default() -> ld_params:
+    p = ld_params()
+    _check(load().ld_params_default(ctypes.byref(p)))
+    return p
+
+
+def ld_ctx_create(device: int = 0) -> int:
+    h = _P()
+    _check(load().ld_ctx_create(ctypes.byref(h), device))
+    return h.value
+
+
+def ld_ctx_destroy(ctx: int) -> None:
+    _check(load().ld_ctx_destroy(ctx))
+
+
+def ld_ctx_reserve(ctx: int, max_pixels: int, max_frames: int, max_acc_cells: int, p: ld_params) -> None:
+    _check(load().ld_ctx_reserve(ctx, max_pixels, max_frames, max_acc_cells, ctypes.byref(p)))
+
+
+def ld_query_sizes(w: int, h: int, p: ld_params | None = None):
+    a, e, d = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int32()
+    _check(load().ld_query_sizes(w, h, ctypes.byref(p) if p is not None else None,
+                                 ctypes.byref(a), ctypes.byref(e), ctypes.byref(d)))
+    return a.value, e.value, d.value
+
+
+def ld_sobel_binarize(ctx, d_img, w, h, pitch, p, d_bin, d_edges, d_edge_count, stream) -> None:
+    _check(load().ld_sobel_binarize(ctx, d_img, w, h, pitch, ctypes.byref(p), d_bin, d_edges, d_edge_count,
+                                    stream))
+
+
+def ld_hough_vote(ctx, d_edges, d_edge_count, w, h, p, d_acc, stream) -> None:
+    _check(load().ld_hough_vote(ctx, d_edges, d_edge_count, w, h, ctypes.byref(p), d_acc, stream))
+
+
+def ld_hough_peaks(ctx, d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) -> None:
+    _check(load().ld_hough_peaks(ctx, d_acc, n_theta, n_rho, ctypes.byref(p), d_peaks, d_n_peaks, stream))
+
+
+def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> None:
+    """frames: sequence of (device_ptr, w, h, pitch)."""
+    arr = (ld_frame * len(frames))()
+    for i, (ptr, w, h, pitch) in enumerate(frames):
+        arr[i].img, arr[i].w, arr[i].h, arr[i].pitch, arr[i].reserved = ptr, w, h, pitch, 0
+    _check(load().ld_detect_batch(ctx, arr, len(frames), ctypes.byref(p), d_peaks, d_n_peaks, d_status,
+                                  stream))
+
+
+def ld_ctx_enable_timing(ctx: int, enable: bool) -> None:
+    _check(load().ld_ctx_enable_timing(ctx, 1 if enable else 0))
+
+
+def ld_ctx_stage_ms(ctx: int) -> tuple[float, float, float]:
+    ms = (ctypes.c_float * 3)()
+    _check(load().ld_ctx_stage_ms(ctx, ctypes.byref(ms)))
+    return ms[0], ms[1], ms[2]
+
+
+def ld_last_error() -> str:
+    return load().ld_last_error().decode()
+
+
+# ------------------------------------------------------------------ torch wrappers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class SobelOut:
+    edges: "object"        # torch.uint32/int32 [capacity]
+    count: "object"        # torch.int32 [1]
+    binary: "object|None"  # torch.uint8 [h][pitch] or None
+
+
+class Context:
+    """An ld_ctx on one CUDA device, with torch-tensor wrappers of the calls."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.handle = ld_ctx_create(device)
+
+    def close(self) -> None:
+        if self.handle:
+            ld_ctx_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _img(img):
+        torch = _torch()
+        if img.dtype != torch.uint8 or img.dim() != 2 or not img.is_cuda or img.stride(1) != 1:
+            raise ValueError("image must be a 2-D uint8 CUDA tensor with unit column stride")
+        return img.data_ptr(), img.shape[1], img.shape[0], img.stride(0)
+
+    def reserve(self, max_pixels: int, max_frames: int, max_acc_cells: int, p: ld_params) -> None:
+        ld_ctx_reserve(self.handle, max_pixels, max_frames, max_acc_cells, p)
+
+    def sobel_binarize(self, img, p: ld_params, want_binary: bool = False, edges=None, count=None,
+                       width: int | None = None, stream=None) -> SobelOut:
+        """Steps 1-2 on a [h][pitch] uint8 tensor (``width`` = w if the tensor is padded)."""
+        torch = _torch()
+        ptr, pw, h, pitch = self._img(img)
+        w = pw if width is None else width
+        cap = p.edge_capacity if p.edge_capacity > 0 else w * h
+        if edges is None:
+            edges = torch.empty(cap, dtype=torch.int32, device=img.device)
+        if count is None:
+            count = torch.empty(1, dtype=torch.int32, device=img.device)
+        binary = torch.empty((h, pitch), dtype=torch.uint8, device=img.device) if want_binary else None
+        ld_sobel_binarize(self.handle, ptr, w, h, pitch, p, binary.data_ptr() if binary is not None else None,
+                          edges.data_ptr(), count.data_ptr(), _stream_handle(stream))
+        return SobelOut(edges, count, binary)
+
+    def hough_vote(self, edges, count, w: int, h: int, p: ld_params, acc=None, stream=None):
+        """Step 3: returns the int32 [n_theta][2D+1] accumulator."""
+        torch = _torch()
+        n_acc, _, D = ld_query_sizes(w, h, p)
+        if acc is None:
+            acc = torch.empty((p.n_theta, 2 * D + 1), dtype=torch.int32, device=edges.device)
+        ld_hough_vote(self.handle, edges.data_ptr(), count.data_ptr(), w, h, p, acc.data_ptr(),
+                      _stream_handle(stream))
+        return acc
+
+    def hough_peaks(self, acc, p: ld_params, stream=None):
+        """Step 4: returns (peaks int32 [top_k][3], n_peaks int32 [1]) on the device."""
+        torch = _torch()
+        n_theta, n_rho = acc.shape
+        peaks = torch.zeros((p.top_k, 3), dtype=torch.int32, device=acc.device)
+        n = torch.zeros(1, dtype=torch.int32, device=acc.device)
+        ld_hough_peaks(self.handle, acc.data_ptr(), n_theta, n_rho, p, peaks.data_ptr(), n.data_ptr(),
+                       _stream_handle(stream))
+        return peaks, n
+
+    def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
+        """Steps 1-4 on a list of uint8 CUDA tensors; returns (peaks [n][top_k][3], n_peaks [n], status [n])."""
+        torch = _torch()
+        descs = []
+        for i, f in enumerate(frames):
+            ptr, pw, h, pitch = self._img(f)
+            descs.append((ptr, pw if widths is None else widths[i], h, pitch))
+        n = len(descs)
+        dev = frames[0].device
+        if out is None:
+            out = (torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev),
+                   torch.zeros(n, dtype=torch.int32, device=dev),
+                   torch.zeros(n, dtype=torch.int32, device=dev))
+        peaks, npk, st = out
+        ld_detect_batch(self.handle, descs, p, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
+                        _stream_handle(stream))
+        return peaks, npk, st

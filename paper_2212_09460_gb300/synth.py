@@ -132,35 +132,53 @@ def frame_stripes(seed: int, w: int, h: int, style: FrameStyle):
     return out
 
 
+def _stripe_mask(st: Stripe, w: int, h: int):
+    """Rows, columns of the pixels inside a stripe (and inside a dash).
+
+    The test is the exact integer predicate |x*nx + y*ny - c| < 3*65536 (and
+    the dash phase); it is only evaluated on a window of columns around the
+    centre line of each row, wide enough to hold every pixel that passes.
+    """
+    ys = np.arange(h, dtype=np.int64)
+    half = 3 * 65536 // max(abs(st.nx), 1) + 3
+    xc = np.floor((st.c - ys * st.ny) / st.nx).astype(np.int64)
+    xs = xc[:, None] + np.arange(-half, half + 1, dtype=np.int64)[None, :]
+    yy = np.broadcast_to(ys[:, None], xs.shape)
+    ok = (xs >= 0) & (xs < w) & (np.abs(xs * st.nx + yy * st.ny - st.c) < 3 * 65536)
+    if st.dash:
+        t = np.floor_divide(xs * st.tx + yy * st.ty - st.t0, 65536)
+        ok &= np.mod(t, st.dash + st.gap) < st.dash
+    return yy[ok], xs[ok]
+
+
+_M16x2 = np.uint64(0x0000FFFF0000FFFF)
+
+
 def road_frame(seed: int, w: int, h: int, style: FrameStyle = LATENCY_640x480) -> np.ndarray:
     """One uint8 [h][w] frame, a pure function of (seed, w, h, style)."""
-    ys = np.arange(h, dtype=np.int64)[:, None]
-    xs = np.arange(w, dtype=np.int64)[None, :]
-    v = np.broadcast_to(40 + (80 * ys) // max(h - 1, 1), (h, w)).astype(np.int64)
+    ys = np.arange(h, dtype=np.int32)[:, None]
+    v = np.empty((h, w), np.int32)
+    v[:] = 40 + (80 * ys) // max(h - 1, 1)
     for st in frame_stripes(seed, w, h, style):
-        inside = np.abs(xs * st.nx + ys * st.ny - st.c) < 3 * 65536
-        if st.dash:
-            t = np.floor_divide(xs * st.tx + ys * st.ty - st.t0, 65536)
-            inside &= np.mod(t, st.dash + st.gap) < st.dash
-        v = np.where(inside, st.value, v)
+        ry, rx = _stripe_mask(st, w, h)
+        v[ry, rx] = st.value
     idx = np.arange(w * h, dtype=np.uint64).reshape(h, w)
     a = _draws(seed, 1, idx)
     b = _draws(seed, 2, idx)
-    m16 = np.uint64(0xFFFF)
-    s8 = np.zeros((h, w), np.int64)
-    for z in (a, b):
-        for k in range(4):
-            s8 += ((z >> np.uint64(16 * k)) & m16).astype(np.int64)
+    # sum of the eight 16-bit fields of a and b (two 32-bit partial sums)
+    t = (a & _M16x2) + ((a >> np.uint64(16)) & _M16x2) + (b & _M16x2) + ((b >> np.uint64(16)) & _M16x2)
+    s8 = ((t & np.uint64(0xFFFFFFFF)) + (t >> np.uint64(32))).astype(np.int64)
     n = s8 - _IH8_MEAN
     k_top = int(round(style.sigma / _IH8_STD * 2.0 ** 32))
     k_road = int(round(style.sigma_road / _IH8_STD * 2.0 ** 32))
-    kk = np.where(ys >= h // 2, k_road, k_top)
-    noise = (n * kk + (1 << 31)) >> 32
-    v = np.clip(v + noise, 0, 255)
+    kk = np.where(ys >= h // 2, k_road, k_top).astype(np.int64)
+    noise = ((n * kk + (1 << 31)) >> 32).astype(np.int32)
+    v += noise
+    np.clip(v, 0, 255, out=v)
     if style.salt > 0:
         c = _draws(seed, 3, idx)
         thr = np.uint64(int(style.salt * 2.0 ** 32))
-        v = np.where((c & np.uint64(0xFFFFFFFF)) < thr, 255, v)
+        v[(c & np.uint64(0xFFFFFFFF)) < thr] = 255
     return v.astype(np.uint8)
 
 

@@ -17,3 +17,23 @@ def ora():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def ldlib():
+    """The C-ABI binding with libld.so built (GPU tests only)."""
+    from paper_2212_09460_gb300 import build as ldbuild
+    ldbuild.build()
+    from paper_2212_09460_gb300 import ld
+    ld.load()
+    return ld
+
+
+@pytest.fixture(scope="session")
+def ctx(ldlib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    c = ldlib.Context(0)
+    yield c
+    c.close()

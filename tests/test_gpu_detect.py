@@ -1,0 +1,74 @@
+"""End-to-end parity of ld_detect_batch (Steps 1-4, fused candidate path)
+with the oracle: single frames, mixed-resolution batches, and sampled frames
+of the 64 x 1920x1080 batch in the launch configuration the benchmark times."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2212_09460_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _detect(ctx, ld, frames, widths, **kw):
+    p = ld.params(**kw)
+    dev = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in frames]
+    pk, n, st = ctx.detect_batch(dev, p, widths=widths)
+    torch.cuda.synchronize()
+    return pk.cpu().numpy(), n.cpu().numpy(), st.cpu().numpy()
+
+
+def _check(ora, frames_raw, pk, n, st, **kw):
+    for i, img in enumerate(frames_raw):
+        ref = ora.detect(img, kw.get("n_theta", 180), kw.get("top_k", 4), threshold=kw.get("threshold", 128),
+                         border=kw.get("border", 0), nms_theta=kw.get("nms_theta", 5),
+                         nms_rho=kw.get("nms_rho", 5), min_votes=kw.get("min_votes", 1))
+        assert st[i] == 0
+        assert n[i] == len(ref), (i, n[i], ref)
+        np.testing.assert_array_equal(pk[i, : n[i]], ref, err_msg=f"frame {i}")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_detect_latency_frame(ctx, ldlib, ora, seed):
+    img = synth.road_frame(seed, 640, 480, synth.LATENCY_640x480)
+    kw = dict(n_theta=180, top_k=2)
+    pk, n, st = _detect(ctx, ldlib, [img], [640], **kw)
+    _check(ora, [img], pk, n, st, **kw)
+
+
+def test_detect_mixed_batch(ctx, ldlib, ora):
+    sizes = [(640, 480), (97, 61), (1280, 720), (3, 3), (513, 300), (200, 900), (1920, 1080), (33, 17)]
+    raw = [synth.road_frame(100 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    frames = [synth.pitched(r, seed=i) for i, r in enumerate(raw)]
+    for kw in (dict(n_theta=360, top_k=4), dict(n_theta=180, top_k=16, border=1, nms_theta=3, nms_rho=9)):
+        pk, n, st = _detect(ctx, ldlib, frames, [w for w, h in sizes], **kw)
+        _check(ora, raw, pk, n, st, **kw)
+
+
+def test_detect_blank_frames(ctx, ldlib, ora):
+    raw = [np.zeros((40, 64), np.uint8), np.full((40, 64), 200, np.uint8)]
+    kw = dict(n_theta=180, top_k=4)
+    pk, n, st = _detect(ctx, ldlib, raw, [64, 64], **kw)
+    _check(ora, raw, pk, n, st, **kw)
+    assert n[0] == 0
+
+
+def test_detect_more_frames_than_one_launch(ctx, ldlib, ora):
+    # 130 frames: more descriptors than one launch carries
+    raw = [synth.road_frame(300 + i, 48 + (i % 5) * 16, 32 + (i % 3), synth.THROUGHPUT_1080P) for i in range(130)]
+    kw = dict(n_theta=90, top_k=3)
+    pk, n, st = _detect(ctx, ldlib, raw, [r.shape[1] for r in raw], **kw)
+    _check(ora, raw, pk, n, st, **kw)
+
+
+def test_detect_full_size_batch_sampled(ctx, ldlib, ora):
+    # the benchmark's workload: 64 seeded 1920x1080 dashed-lane frames, 360 theta,
+    # top-4, in one call; the oracle checks a sample of the frames
+    seeds = list(range(1000, 1064))
+    raw = {s: synth.road_frame(s, 1920, 1080, synth.THROUGHPUT_1080P) for s in seeds}
+    kw = dict(n_theta=360, top_k=4)
+    pk, n, st = _detect(ctx, ldlib, [raw[s] for s in seeds], [1920] * 64, **kw)
+    assert (st == 0).all() and (n == 4).all()
+    for i in (0, 21, 42, 63):
+        ref = ora.detect(raw[seeds[i]], 360, 4)
+        np.testing.assert_array_equal(pk[i], ref, err_msg=f"frame {i}")
