@@ -109,13 +109,15 @@ def test_hough_empty_edge_list(ctx, ldlib, ora):
     assert acc.shape == (180, 2 * ora.rho_max(64, 48) + 1) and (acc == 0).all()
 
 
-def test_hough_full_image_16bit_bound(ctx, ldlib, ora):
-    # every pixel an edge: the fullest cells reach ~2*max(w,h) votes
-    w, h = 700, 300
+@pytest.mark.parametrize("w,h,n_theta", [(700, 300, 360), (24000, 3, 180)])
+def test_hough_full_image_16bit_counts(ctx, ldlib, ora, w, h, n_theta):
+    # every pixel an edge: the fullest cells hold max(w, h) votes or more
+    # (24000 at theta = 90 deg for the 24000 x 3 image), close to the 16-bit
+    # bound the packed counters rely on
     edges = ora.edge_list(np.full((h, w), 255, np.uint8))
-    acc = _gpu_hough(ctx, ldlib, edges, w, h, 360)
-    ref = ora.hough(edges, w, h, 360)
-    assert ref.max() > 1000
+    acc = _gpu_hough(ctx, ldlib, edges, w, h, n_theta)
+    ref = ora.hough(edges, w, h, n_theta)
+    assert ref.max() >= max(w, h)
     np.testing.assert_array_equal(acc, ref)
 
 
