@@ -176,6 +176,31 @@ LD_API ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t 
                           const ld_params *p, ld_peak *d_peaks,
                           int32_t *d_n_peaks, int32_t *d_status, void *stream);
 
+/*
+ * Step 4 as ld_hough_peaks, for callers that may not allocate device memory.
+ * The paper has no counterpart; this is a property of the library.
+ *
+ * ld_hough_peaks grows its candidate buffer inside the context with cudaMalloc.
+ * A camera loop with a per-frame deadline or a host thread that must never
+ * block cannot call cudaMalloc while running (it may synchronise the device and
+ * its latency is unbounded), and a process whose device memory is fixed at
+ * start-up may not grow it.  This entry point takes no context and allocates
+ * nothing: the candidates live in a 1 MiB array of the library's own device
+ * memory (131072 keys), present on every GPU that loads the library until the
+ * process exits.  Arguments, results and errors are those of ld_hough_peaks,
+ * on the calling thread's current device, plus one limit: ceil(n_theta*n_rho /
+ * 16384) * (nms_theta*nms_rho*(top_k-1)+1) <= 131072 (a 360 x 4407
+ * accumulator with 5x5 windows and top_k 4 needs 7372), else LD_ERR_INVALID.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array (each call rewrites every slot it reads, nothing needs clearing), so
+ * calls whose work overlaps on the GPU race: serialise them.
+ */
+LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
+                                       int32_t n_rho, const ld_params *p,
+                                       ld_peak *d_peaks, int32_t *d_n_peaks,
+                                       void *stream);
+
 /* Stage timing.  After ld_ctx_enable_timing(ctx, 1), every ld_detect_batch
  * call also records CUDA events on its stream around its kernels: before
  * Steps 1-2, between Steps 1-2 and Step 3, between Step 3 and Step 4, and

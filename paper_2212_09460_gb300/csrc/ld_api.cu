@@ -72,6 +72,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void ld::set_last_error(const char *msg) { g_err = msg; }
+
 struct ld_ctx {
     int device = 0;
     int num_sms = 148;

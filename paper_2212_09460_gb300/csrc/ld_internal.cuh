@@ -143,4 +143,7 @@ cudaError_t launch_merge(const MergeLaunch &L, cudaStream_t s);
 // Largest pairs-per-tile whose packed accumulator fits shared memory.
 int hough_max_pairs(int n_rho);
 
+// Set the calling thread's ld_last_error() message.
+void set_last_error(const char *msg);
+
 }  // namespace ld

@@ -59,6 +59,7 @@ _SIGS = {
     "ld_hough_peaks": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
                         _P],
+    "ld_hough_peaks_static": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_ctx_enable_timing": [_P, ctypes.c_int],
     "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
 }
@@ -157,6 +158,11 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
         arr[i].img, arr[i].w, arr[i].h, arr[i].pitch, arr[i].reserved = ptr, w, h, pitch, 0
     _check(load().ld_detect_batch(ctx, arr, len(frames), ctypes.byref(p), d_peaks, d_n_peaks, d_status,
                                   stream))
+
+
+def ld_hough_peaks_static(d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) -> None:
+    """ld_hough_peaks without a context and without any device allocation."""
+    _check(load().ld_hough_peaks_static(d_acc, n_theta, n_rho, ctypes.byref(p), d_peaks, d_n_peaks, stream))
 
 
 def ld_ctx_enable_timing(ctx: int, enable: bool) -> None:
