@@ -161,9 +161,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=N_FRAMES,
+                    help="frames per GPU (the workload is 64; smaller values are for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    nf = args.frames
     if args.impl == "reference":
         run_reference(args)
         return
@@ -173,7 +176,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     # frames are generated before any CUDA call (spawn pool)
-    seeds = [SEED0 + rank * N_FRAMES + i for i in range(N_FRAMES)]
+    seeds = [SEED0 + rank * nf + i for i in range(nf)]
     host_frames = make_frames(seeds)
 
     import torch
@@ -194,12 +197,12 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     p = ld.params(n_theta=N_THETA, top_k=TOP_K)
     ctx = ld.Context(local_rank)
-    ctx.reserve(N_FRAMES * W * H, N_FRAMES, 0, p)
-    out = (torch.zeros((N_FRAMES, TOP_K, 3), dtype=torch.int32, device=dev),
-           torch.zeros(N_FRAMES, dtype=torch.int32, device=dev),
-           torch.zeros(N_FRAMES, dtype=torch.int32, device=dev))
-    views = [frames_d[i] for i in range(N_FRAMES)]
-    views_e2e = [frames_e2e[i] for i in range(N_FRAMES)]
+    ctx.reserve(nf * W * H, nf, 0, p)
+    out = (torch.zeros((nf, TOP_K, 3), dtype=torch.int32, device=dev),
+           torch.zeros(nf, dtype=torch.int32, device=dev),
+           torch.zeros(nf, dtype=torch.int32, device=dev))
+    views = [frames_d[i] for i in range(nf)]
+    views_e2e = [frames_e2e[i] for i in range(nf)]
     stream = torch.cuda.current_stream(dev)
     ld.ld_ctx_enable_timing(ctx.handle, True)
 
@@ -235,9 +238,9 @@ def main():
     stage_ms = stage / args.steps                                 # mean per step: sobel, hough, peaks
 
     # ---- end to end through the same call, from pinned host memory
-    peaks_h = torch.empty((N_FRAMES, TOP_K, 3), dtype=torch.int32).pin_memory()
-    npk_h = torch.empty(N_FRAMES, dtype=torch.int32).pin_memory()
-    st_h = torch.empty(N_FRAMES, dtype=torch.int32).pin_memory()
+    peaks_h = torch.empty((nf, TOP_K, 3), dtype=torch.int32).pin_memory()
+    npk_h = torch.empty(nf, dtype=torch.int32).pin_memory()
+    st_h = torch.empty(nf, dtype=torch.int32).pin_memory()
     e2e_steps = max(3, args.steps // 2)
 
     def e2e_step():
@@ -275,8 +278,8 @@ def main():
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
         sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        value = world * N_FRAMES * args.steps / (total_ms / 1000.0)
-        e2e_val = world * N_FRAMES / (e2e_ms / 1000.0)
+        value = world * nf * args.steps / (total_ms / 1000.0)
+        e2e_val = world * nf / (e2e_ms / 1000.0)
 
         # algorithmic work per step: Hough E*n_theta votes per frame;
         # Sobel 1 B/px read + 4 B per edge written
@@ -284,7 +287,7 @@ def main():
         votes = e_sum * N_THETA
         hough_s = stage_ms[1] / 1000.0
         sobel_s = stage_ms[0] / 1000.0
-        sobel_bytes = N_FRAMES * W * H * 1 + e_sum * 4
+        sobel_bytes = nf * W * H * 1 + e_sum * 4
         atom_peak = n_sms * 32 * sm_max_mhz * 1e6 / 1e9          # Gvote/s: 32 banks/clk/SM
         roof = {"bound": "alu", "kernel": "hough_kernel (Step 3 voting + per-tile top-M)",
                 "achieved": votes / hough_s / 1e9, "peak": atom_peak, "unit": "Gvote/s",
@@ -301,13 +304,13 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": f"{N_FRAMES} x {W}x{H} uint8 seeded dashed-lane frames (seeds "
+                "config": {"workload": f"{nf} x {W}x{H} uint8 seeded dashed-lane frames (seeds "
                                        f"{SEED0}+), 5-10% edge density, 3x3 Sobel, T=128, {N_THETA} theta x "
                                        f"1 px rho int32 accumulator, top-{TOP_K} 5x5 NMS",
-                           "global_batch": N_FRAMES * world, "frames_per_gpu": N_FRAMES,
+                           "global_batch": nf * world, "frames_per_gpu": nf,
                            "parallelism": f"frames sharded across {world} GPU(s), no collective",
                            "l2": "flushed (256 MiB write) before every timed step",
-                           "edges_per_frame_mean": e_sum / N_FRAMES},
+                           "edges_per_frame_mean": e_sum / nf},
                 "stage_ms": {"sobel_binarize": stage_ms[0], "hough_vote": stage_ms[1], "peaks": stage_ms[2]},
                 "roofline": roof, "roofline_sobel": roof_sobel,
                 "e2e": {"value": e2e_val, "unit": "frames/s",

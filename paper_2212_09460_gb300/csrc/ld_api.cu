@@ -196,10 +196,10 @@ ld_params defaults() {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Sobel rows per warp: the tallest strip that still gives >= 2 CTAs per SM.
+// Sobel rows per warp: 4 (60 registers, 4 CTAs per SM) when that still gives
+// >= 2 CTAs per SM, else 2 (shorter strips, more CTAs for small images).
 int pick_rows(int64_t tiles_x, int64_t total_rows_tiles_at_r2, int num_sms) {
     (void)tiles_x;
-    if (total_rows_tiles_at_r2 / 4 >= 2 * num_sms) return 8;
     if (total_rows_tiles_at_r2 / 2 >= 2 * num_sms) return 4;
     return 2;
 }

@@ -243,16 +243,17 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     const int32_t mv = L.min_votes;
     uint64_t *out = F.cand + (size_t)tile * M;
 
-    // pass 0: included count and the value range
+    // pass 0: included count, per-thread maximum, overall maximum
     int cnt = 0;
-    uint32_t vmax = 0;
+    int tmax = -1;
     for (int i = tid; i < words; i += kHoughThreads) {
         const uint32_t wv = acc[i];
         const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-        if (a >= mv) { ++cnt; vmax = max(vmax, (uint32_t)a); }
-        if (b >= mv) { ++cnt; vmax = max(vmax, (uint32_t)b); }
+        if (a >= mv) { ++cnt; tmax = max(tmax, a); }
+        if (b >= mv) { ++cnt; tmax = max(tmax, b); }
     }
     const int total = block_sum(cnt, S);
+    uint32_t vmax = tmax < 0 ? 0u : (uint32_t)tmax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
     if (lane == 0) S.red[warp] = vmax;
@@ -260,6 +261,52 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     uint32_t gmax = 0;
     for (int w = 0; w < kHoughWarps; ++w) gmax = max(gmax, S.red[w]);
     __syncthreads();
+
+    // Fast path.  L = the M-th largest of the per-thread maxima: M distinct
+    // cells have votes >= L, so every top-M cell does too.  The cells with
+    // votes >= L ("survivors", usually a few hundred) are compacted as keys,
+    // which are unique and ordered like the peaks, and the first M keys of
+    // their descending sort are exactly the tile's top-M.  The edge ring is
+    // free now and holds the scratch.  Too many survivors: the general path.
+    constexpr int kMaxSurv = 2048;
+    if (total > M && M <= kHoughThreads) {
+        int *tm = reinterpret_cast<int *>(ring);
+        uint64_t *keys = reinterpret_cast<uint64_t *>(ring + kHoughThreads);
+        tm[tid] = tmax;
+        if (tid == 0) S.surv = 0;
+        __syncthreads();
+        block_sort_desc(tm, kHoughThreads);
+        const int Lth = tm[M - 1];
+        if (Lth >= 0) {   // block-uniform
+            for (int i = tid; i < words; i += kHoughThreads) {
+                const uint32_t wv = acc[i];
+                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+                if (a >= Lth || b >= Lth) {
+                    const int p = i / n_rho, r = i - p * n_rho;
+                    if (a >= Lth) {
+                        const int slot = atomicAdd(&S.surv, 1);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(a, theta_lo(j0, p), r);
+                    }
+                    if (b >= Lth) {
+                        const int slot = atomicAdd(&S.surv, 1);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(b, theta_hi(j0, p, n_theta), r);
+                    }
+                }
+            }
+            __syncthreads();
+            const int ns_ = S.surv;
+            if (ns_ <= kMaxSurv) {   // block-uniform
+                int n2 = 1;
+                while (n2 < ns_) n2 <<= 1;
+                for (int i = ns_ + tid; i < n2; i += kHoughThreads) keys[i] = 0ull;
+                __syncthreads();
+                block_sort_desc(keys, n2);
+                for (int i = tid; i < M; i += kHoughThreads) out[i] = keys[i];
+                return;
+            }
+        }
+        __syncthreads();
+    }
 
     const bool all_in = total <= M;
     if (tid == 0) {

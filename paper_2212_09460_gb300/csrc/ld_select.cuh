@@ -30,7 +30,30 @@ struct SelectSmem {
     int32_t total;           // included cells
     int32_t out_n;           // emitted so far (cells > u*)
     int32_t tie_run;         // ties taken so far (ordered pass)
+    int32_t surv;            // survivors compacted by the fast path
 };
+
+// Block-wide bitonic sort of buf[0..n) in shared memory, descending; n a
+// power of two.  Every thread of the block must call it.
+template <class T>
+__device__ __forceinline__ void block_sort_desc(T *buf, int n) {
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const T a = buf[i], b = buf[ixj];
+                    const bool desc = (i & k) == 0;
+                    if (desc ? (a < b) : (a > b)) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
 
 // Add the ballot counts of one warp-step to this warp's 16 digit counters
 // (kept by every lane in registers).

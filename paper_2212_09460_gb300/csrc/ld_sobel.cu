@@ -6,10 +6,11 @@
 // GB300 design (differs from the paper's 16x16-thread-block K80 kernel,
 // Eq. 6): one warp covers 512 contiguous pixels of a row with one 16-byte
 // load per lane, so every row is read with fully coalesced 512-byte warp
-// transactions.  The 3x3 window slides down R rows in registers (each image
-// row is loaded once per warp strip, plus two halo rows), the left/right
-// neighbour bytes come from the adjacent lanes through shuffles, and zero
-// padding is virtual (never materialised).  Edge bits are compacted with a
+// transactions.  A warp issues the loads of all R + 2 rows of its strip
+// (R output rows plus two halo rows) before computing, so that many bytes
+// are in flight per SM, then slides the 3x3 window down in registers; the
+// left/right neighbour bytes come from the adjacent lanes through shuffles,
+// and zero padding is virtual (never materialised).  Edge bits are compacted with a
 // block-wide prefix sum and one global atomic per CTA.
 #include "ld_internal.cuh"
 
@@ -28,37 +29,40 @@ __device__ __forceinline__ uint4 ldg_nc_v4(const void *p) {
     return v;
 }
 
-// Load the 16 pixels of row y starting at x0, with the two neighbour bytes.
-// Pixels outside the image (x >= w, y outside [0,h)) read as 0.  All 32 lanes
-// of the warp must call this (shuffles).
-__device__ __forceinline__ Row load_row(const SobelFrame &F, int x0, int y, int lane) {
-    Row R;
-    R.v[0] = R.v[1] = R.v[2] = R.v[3] = 0;
-    const bool row_ok = (y >= 0) && (y < F.h);
-    if (row_ok && x0 < F.w) {
-        const uint8_t *p = F.img + (size_t)y * F.pitch + x0;
-        uint4 q = ldg_nc_v4(p);
-        R.v[0] = q.x; R.v[1] = q.y; R.v[2] = q.z; R.v[3] = q.w;
-        int nvalid = F.w - x0;
+// The 16 pixels of row y starting at x0 as one 16-byte vector; pixels
+// outside the image (x >= w, y outside [0, h)) read as 0.
+__device__ __forceinline__ uint4 load_vec(const SobelFrame &F, int x0, int y) {
+    uint4 q = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < F.h && x0 < F.w) {
+        q = ldg_nc_v4(F.img + (size_t)y * F.pitch + x0);
+        const int nvalid = F.w - x0;
         if (nvalid < 16) {
+            uint32_t *v = reinterpret_cast<uint32_t *>(&q);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                int k = nvalid - 4 * i;
-                uint32_t m = k >= 4 ? 0xFFFFFFFFu : (k <= 0 ? 0u : ((1u << (8 * k)) - 1u));
-                R.v[i] &= m;
+                const int k = nvalid - 4 * i;
+                v[i] &= k >= 4 ? 0xFFFFFFFFu : (k <= 0 ? 0u : ((1u << (8 * k)) - 1u));
             }
         }
     }
-    uint32_t left = __shfl_up_sync(0xFFFFFFFFu, R.v[3] >> 24, 1);
-    uint32_t right = __shfl_down_sync(0xFFFFFFFFu, R.v[0] & 0xFFu, 1);
-    if (lane == 0) {
-        left = (row_ok && x0 > 0 && x0 - 1 < F.w) ? F.img[(size_t)y * F.pitch + x0 - 1] : 0u;
-    }
-    if (lane == 31) {
-        right = (row_ok && x0 + 16 < F.w) ? F.img[(size_t)y * F.pitch + x0 + 16] : 0u;
-    }
-    R.l = left;
-    R.r = right;
+    return q;
+}
+
+// Pixel x0-1 (lane 0) or x0+16 (lane 31) of row y, 0 outside the image.
+__device__ __forceinline__ uint32_t load_edge_byte(const SobelFrame &F, int x, int y) {
+    return (y >= 0 && y < F.h && x >= 0 && x < F.w) ? (uint32_t)F.img[(size_t)y * F.pitch + x] : 0u;
+}
+
+// Assemble a row from its vector and the neighbour bytes, which come from
+// the adjacent lanes (lanes 0 and 31 use the bytes they loaded themselves).
+// All 32 lanes of the warp must call this (shuffles).
+__device__ __forceinline__ Row make_row(uint4 q, uint32_t own_l, uint32_t own_r, int lane) {
+    Row R;
+    R.v[0] = q.x; R.v[1] = q.y; R.v[2] = q.z; R.v[3] = q.w;
+    uint32_t left = __shfl_up_sync(0xFFFFFFFFu, q.w >> 24, 1);
+    uint32_t right = __shfl_down_sync(0xFFFFFFFFu, q.x & 0xFFu, 1);
+    R.l = (lane == 0) ? own_l : left;
+    R.r = (lane == 31) ? own_r : right;
     return R;
 }
 
@@ -126,17 +130,25 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
     for (int r = 0; r < R; ++r) masks[r] = 0;
 
     if (ya < F.h) {   // warp-uniform
-        Row top = load_row(F, x0, ya - 1, lane);
-        Row mid = load_row(F, x0, ya, lane);
+        // issue every load of the strip first (R + 2 rows), then compute
+        uint4 raw[R + 2];
+        uint32_t eb[R + 2];
+#pragma unroll
+        for (int j = 0; j < R + 2; ++j) raw[j] = load_vec(F, x0, ya - 1 + j);
+#pragma unroll
+        for (int j = 0; j < R + 2; ++j)
+            eb[j] = (lane == 0) ? load_edge_byte(F, x0 - 1, ya - 1 + j)
+                                : ((lane == 31) ? load_edge_byte(F, x0 + 16, ya - 1 + j) : 0u);
+        Row top = make_row(raw[0], eb[0], eb[0], lane);
+        Row mid = make_row(raw[1], eb[1], eb[1], lane);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = ya + r;
-            if (y >= F.h) break;   // warp-uniform
-            Row bot = load_row(F, x0, y + 1, lane);
-            uint32_t bits = sobel16(top, mid, bot, L.threshold) & colmask;
+            Row bot = make_row(raw[r + 2], eb[r + 2], eb[r + 2], lane);
+            uint32_t bits = (y < F.h) ? (sobel16(top, mid, bot, L.threshold) & colmask) : 0u;
             if (L.border == LD_BORDER_CLEAR && (y == 0 || y == F.h - 1)) bits = 0;
             masks[r] = bits;
-            if (F.bin != nullptr && x0 < F.pitch) {
+            if (F.bin != nullptr && x0 < F.pitch && y < F.h) {
                 uint4 o;
                 o.x = spread4(bits & 0xF);
                 o.y = spread4((bits >> 4) & 0xF);
