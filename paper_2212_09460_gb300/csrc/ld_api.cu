@@ -214,6 +214,17 @@ HoughPlan plan_hough(int w, int h, int n_theta) {
     hp.n_rho = 2 * hp.D + 1;
     const int n_pairs = n_theta / 2;
     const int pmax = hough_max_pairs(hp.n_rho);
+    // Prefer a compiled tile size that divides the pairs exactly (every tile
+    // runs the predicate-free loop) unless it is much smaller than what fits.
+    int best_div = 0;
+#define LD_DIV(P) if (P <= pmax && n_pairs % P == 0 && P > best_div) best_div = P;
+    LD_HOUGH_PAIR_SIZES(LD_DIV)
+#undef LD_DIV
+    if (best_div > 0 && 10 * best_div >= 7 * (pmax < n_pairs ? pmax : n_pairs)) {
+        hp.pairs = best_div;
+        hp.n_tiles = n_pairs / best_div;
+        return hp;
+    }
     hp.n_tiles = (n_pairs + pmax - 1) / pmax;
     hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
     hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;

@@ -56,6 +56,10 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// Shared-memory reduction without a returned value.
+__device__ __forceinline__ void red_add_shared(uint32_t *addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(addr)), "r"(v) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -90,6 +94,50 @@ __device__ __forceinline__ void ordered_col(int q, int np, bool has0, int &slot,
     else slot = np - 1 - q2;
 }
 
+// Votes of one edge pixel (x, y) into the tile's packed accumulator.  For
+// slot p (theta pair {j, n-j}), kq[p] = 32768 + (D + p*n_rho)*65536 folds the
+// Q16 rounding constant, the rho offset D and the slot's word offset, so
+//   v1 = x*c + y*s + kq  and  v2 = 2*(y*s + kq) - v1 = -x*c + y*s + kq
+// give, after >> 16, the accumulator word of the vote for theta_j (low half)
+// and theta_{n-j} (high half) (Eqs. 3-5).  HAS0: slot 0 is the pair
+// {0, n/2}, whose rho is x and y.  RAGGED: only the first np slots are used.
+template <int P, bool HAS0, bool RAGGED>
+__device__ __forceinline__ void vote_edge(uint32_t x, uint32_t y, const uint32_t (&cq)[P],
+                                          const uint32_t (&sq)[P], const uint32_t (&kq)[P], uint32_t *acc,
+                                          uint32_t D, int np) {
+    if (HAS0) {   // theta = 0 (rho = x) and theta = 90 deg (rho = y)
+        red_add_shared(acc + (x + D), 1u);
+        red_add_shared(acc + (y + D), 0x10000u);
+    }
+#pragma unroll
+    for (int p = HAS0 ? 1 : 0; p < P; ++p) {
+        if (RAGGED && p >= np) break;
+        const uint32_t A = y * sq[p] + kq[p];
+        const uint32_t v1 = x * cq[p] + A;
+        const uint32_t v2 = 2u * A - v1;
+        red_add_shared(acc + (v1 >> 16), 1u);         // theta_j
+        red_add_shared(acc + (v2 >> 16), 0x10000u);   // theta_{n-j}
+    }
+}
+
+// One streamed chunk of n_c edges: lane l of warp w takes edges l*S + o for
+// o = w, w + 16, ... (S odd: 32 distinct banks, lanes far apart in the list).
+template <int P, bool HAS0, bool RAGGED>
+__device__ __forceinline__ void vote_chunk(const uint32_t *buf, const uint32_t *gedges, int n_c, int lane,
+                                           int warp, const uint32_t (&cq)[P], const uint32_t (&sq)[P],
+                                           const uint32_t (&kq)[P], uint32_t *acc, uint32_t W, uint32_t H,
+                                           uint32_t D, int np) {
+    const int n4 = n_c & ~3;
+    for (int o = warp; o < kChunkSeg; o += kHoughWarps) {
+        const int idx = lane * kChunkSeg + o;
+        if (idx < n_c) {
+            const uint32_t e = (idx < n4) ? buf[idx] : gedges[idx];
+            const uint32_t x = e & 0xFFFFu, y = e >> 16;
+            if (x < W && y < H) vote_edge<P, HAS0, RAGGED>(x, y, cq, sq, kq, acc, D, np);
+        }
+    }
+}
+
 template <int PMAX>
 __global__ void __launch_bounds__(kHoughThreads, 1)
 hough_kernel(const __grid_constant__ HoughLaunch L) {
@@ -113,7 +161,6 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     const int np = min(F.pairs_per_tile, n_theta / 2 - j0);
     const bool has0 = (j0 == 0);
     const int n_rho = F.n_rho;
-    const uint32_t K0 = 32768u + (uint32_t)F.D * 65536u;
     const uint32_t W = (uint32_t)F.w, H = (uint32_t)F.h;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -121,14 +168,15 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem_raw + kRingBytesPad);
     const int words = np * n_rho;
 
-    // ---- Q16 (c, s) of the tile's pairs in registers
-    uint32_t cq[PMAX], sq[PMAX];
+    // ---- Q16 (c, s) of the tile's pairs and their folded constants in registers
+    uint32_t cq[PMAX], sq[PMAX], kq[PMAX];
 #pragma unroll
     for (int p = 0; p < PMAX; ++p) {
-        cq[p] = 0; sq[p] = 0;
+        cq[p] = 0; sq[p] = 0; kq[p] = 0;
         if (p < np) {
             cq[p] = (uint32_t)L.trig[2 * (j0 + p)];
             sq[p] = (uint32_t)L.trig[2 * (j0 + p) + 1];
+            kq[p] = 32768u + ((uint32_t)F.D + (uint32_t)(p * n_rho)) * 65536u;
         }
     }
 
@@ -174,29 +222,14 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
             const uint32_t *buf = ring + st * kChunkEdges;
             const int64_t start = e0 + c * kChunkEdges;
             const int n_c = (int)((e1 - start) < kChunkEdges ? (e1 - start) : kChunkEdges);
-            const int n4 = n_c & ~3;
-            for (int o = warp; o < kChunkSeg; o += kHoughWarps) {
-                const int idx = lane * kChunkSeg + o;
-                if (idx < n_c) {
-                    const uint32_t e = (idx < n4) ? buf[idx] : F.edges[start + idx];
-                    const uint32_t x = e & 0xFFFFu, y = e >> 16;
-                    if (x < W && y < H) {
-                        if (has0) {   // theta = 0 (rho = x) and theta = 90 deg (rho = y)
-                            atomicAdd(acc + (x + (uint32_t)F.D), 1u);
-                            atomicAdd(acc + (y + (uint32_t)F.D), 0x10000u);
-                        }
-#pragma unroll
-                        for (int p = 0; p < PMAX; ++p) {
-                            if (p < np && (p > 0 || !has0)) {
-                                const uint32_t A = y * sq[p] + K0;
-                                const uint32_t B = x * cq[p];
-                                uint32_t *col = acc + p * n_rho;
-                                atomicAdd(col + ((A + B) >> 16), 1u);        // theta_k
-                                atomicAdd(col + ((A - B) >> 16), 0x10000u);  // theta_{n-k}
-                            }
-                        }
-                    }
-                }
+            const uint32_t *ge = F.edges + start;
+            const uint32_t D = (uint32_t)F.D;
+            if (np == PMAX) {
+                if (has0) vote_chunk<PMAX, true, false>(buf, ge, n_c, lane, warp, cq, sq, kq, acc, W, H, D, np);
+                else vote_chunk<PMAX, false, false>(buf, ge, n_c, lane, warp, cq, sq, kq, acc, W, H, D, np);
+            } else {
+                if (has0) vote_chunk<PMAX, true, true>(buf, ge, n_c, lane, warp, cq, sq, kq, acc, W, H, D, np);
+                else vote_chunk<PMAX, false, true>(buf, ge, n_c, lane, warp, cq, sq, kq, acc, W, H, D, np);
             }
         }
         __syncthreads();
@@ -413,19 +446,27 @@ cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t
 int hough_max_pairs(int n_rho) {
     const int avail = kSmemLimit - (int)sizeof(SelectSmem) - 256 - kRingBytesPad;
     int p = avail / (n_rho * 4);
-    return p < 32 ? p : 32;
+    return p < 30 ? p : 30;   // registers: 3 per pair, 128 per thread
 }
 
 cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_t acc_words_max,
                          cudaStream_t s) {
     if (n_ctas <= 0) return cudaSuccess;
     const size_t smem = (size_t)kRingBytesPad + (size_t)acc_words_max * 4;
-    if (pairs_max <= 4) return launch_p<4>(L, n_ctas, smem, s);
-    if (pairs_max <= 8) return launch_p<8>(L, n_ctas, smem, s);
-    if (pairs_max <= 12) return launch_p<12>(L, n_ctas, smem, s);
-    if (pairs_max <= 16) return launch_p<16>(L, n_ctas, smem, s);
-    if (pairs_max <= 24) return launch_p<24>(L, n_ctas, smem, s);
-    return launch_p<32>(L, n_ctas, smem, s);
+    switch (hough_template_pairs(pairs_max)) {
+#define LD_CASE(P) case P: return launch_p<P>(L, n_ctas, smem, s);
+        LD_HOUGH_PAIR_SIZES(LD_CASE)
+#undef LD_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int hough_template_pairs(int pairs) {
+    int best = 0;
+#define LD_PICK(P) if (P >= pairs && (best == 0 || P < best)) best = P;
+    LD_HOUGH_PAIR_SIZES(LD_PICK)
+#undef LD_PICK
+    return best;
 }
 
 }  // namespace ld

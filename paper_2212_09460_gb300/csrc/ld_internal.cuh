@@ -47,7 +47,7 @@ struct SobelLaunch {
 };
 
 // ---------------------------------------------------------------- Hough
-constexpr int kHoughThreads = 512;      // 16 warps
+constexpr int kHoughThreads = 512;      // 16 warps (up to 128 registers per thread)
 constexpr int kHoughWarps = kHoughThreads / 32;
 // Edge chunk streamed per stage: 32 lane segments of odd length S, so that the
 // 32 lanes of a warp read 32 distinct shared-memory banks (index l*S + o).
@@ -142,6 +142,12 @@ cudaError_t launch_merge(const MergeLaunch &L, cudaStream_t s);
 
 // Largest pairs-per-tile whose packed accumulator fits shared memory.
 int hough_max_pairs(int n_rho);
+
+// Compiled tile sizes (theta pairs per CTA) of the voting kernel; a tile of
+// exactly one of these sizes runs without per-pair predicates.
+#define LD_HOUGH_PAIR_SIZES(X) X(2) X(3) X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(30)
+// Smallest compiled tile size >= pairs (0 if none).
+int hough_template_pairs(int pairs);
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);

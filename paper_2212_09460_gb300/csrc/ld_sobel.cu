@@ -66,30 +66,76 @@ __device__ __forceinline__ Row make_row(uint4 q, uint32_t own_l, uint32_t own_r,
     return R;
 }
 
-__device__ __forceinline__ int px(const Row &R, int i) {   // i in [-1, 16]
-    if (i < 0) return (int)R.l;
-    if (i > 15) return (int)R.r;
-    return (int)((R.v[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+// A row in 16-bit lanes: E[k] = pixels (4k, 4k+2), O[k] = pixels (4k+1, 4k+3)
+// of the lane's 16, plus the neighbour pixels x0-1 (l) and x0+16 (r).
+struct URow {
+    uint32_t E[4], O[4];
+    uint32_t l, r;
+};
+
+__device__ __forceinline__ URow unpack(const Row &R) {
+    URow U;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        U.E[k] = __byte_perm(R.v[k], 0u, 0x4240);   // bytes 0, 2 -> lanes 0, 1
+        U.O[k] = __byte_perm(R.v[k], 0u, 0x4341);   // bytes 1, 3
+    }
+    U.l = R.l;
+    U.r = R.r;
+    return U;
 }
 
-// Eq. 1 for the 16 pixels of the middle row: bit i set iff |Gx|+|Gy| >= thr.
-// Gx = vs(x+1) - vs(x-1) with vs = top + 2 mid + bottom;
-// Gy = vd(x-1) + 2 vd(x) + vd(x+1) with vd = bottom - top.
-__device__ __forceinline__ uint32_t sobel16(const Row &T, const Row &M, const Row &B, int thr) {
-    int vs[18], vd[18];
+// Eq. 1 and the threshold for the 16 pixels of the middle row, two pixels per
+// 32-bit operation (16-bit lanes, every lane kept non-negative by a bias so
+// no borrow crosses lanes):
+//   S = T + 2M + B (vertical smoothing), D = B - T + 255,
+//   gx(x) = S(x+1) - S(x-1),  gy(x) = D(x-1) + 2D(x) + D(x+1) - 1020,
+//   |gx| + |gy| = max(|gx + gy|, |gx - gy|), tested against thr with four
+//   compares whose result lands in bit 15 of each lane.
+// Returns bit i set iff |Gx| + |Gy| >= thr at pixel x0 + i.
+__device__ __forceinline__ uint32_t sobel16(const URow &T, const URow &M, const URow &B, uint32_t thr) {
+    uint32_t SE[5], SO[5], DE[5], DO[5];
 #pragma unroll
-    for (int i = -1; i <= 16; ++i) {
-        int t = px(T, i), m = px(M, i), b = px(B, i);
-        vs[i + 1] = t + 2 * m + b;
-        vd[i + 1] = b - t;
+    for (int k = 0; k < 4; ++k) {
+        SE[k] = T.E[k] + B.E[k] + 2u * M.E[k];
+        SO[k] = T.O[k] + B.O[k] + 2u * M.O[k];
+        DE[k] = B.E[k] + 0x00FF00FFu - T.E[k];
+        DO[k] = B.O[k] + 0x00FF00FFu - T.O[k];
     }
+    // neighbours: S(-1), D(-1) in the high lane of index "-1" (stored at [4] of
+    // the odd arrays), S(16), D(16) in the low lane of index 4 of the even arrays
+    const uint32_t sl = T.l + B.l + 2u * M.l, dl = B.l + 255u - T.l;
+    const uint32_t sr = T.r + B.r + 2u * M.r, dr = B.r + 255u - T.r;
+    SE[4] = sr;
+    DE[4] = dr;
+    SO[4] = sl << 16;
+    DO[4] = dl << 16;
+    const uint32_t K1 = (0x8000u - 2040u - thr) * 0x10001u;
+    const uint32_t K2 = (0x8000u + 2040u - thr) * 0x10001u;
     uint32_t bits = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        int gx = vs[i + 2] - vs[i];
-        int gy = vd[i] + 2 * vd[i + 1] + vd[i + 2];
-        int mag = abs(gx) + abs(gy);
-        bits |= (mag >= thr ? 1u : 0u) << i;
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t sOm = __funnelshift_l(SO[k == 0 ? 4 : k - 1], SO[k], 16);   // S(4k-1), S(4k+1)
+        const uint32_t dOm = __funnelshift_l(DO[k == 0 ? 4 : k - 1], DO[k], 16);
+        const uint32_t sEp = __funnelshift_r(SE[k], SE[k + 1], 16);               // S(4k+2), S(4k+4)
+        const uint32_t dEp = __funnelshift_r(DE[k], DE[k + 1], 16);
+        // biased by 1020 per lane, in [0, 2040]
+        const uint32_t gxE = SO[k] + 0x03FC03FCu - sOm;   // pixels 4k, 4k+2
+        const uint32_t gxO = sEp + 0x03FC03FCu - SE[k];   // pixels 4k+1, 4k+3
+        const uint32_t gyE = dOm + 2u * DE[k] + DO[k];
+        const uint32_t gyO = DE[k] + 2u * DO[k] + dEp;
+        uint32_t t[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t G = h ? gxO : gxE, Hh = h ? gyO : gyE;
+            const uint32_t s1 = G + Hh;                     // gx + gy + 2040
+            const uint32_t s2 = G + 0x07F807F8u - Hh;       // gx - gy + 2040
+            t[h] = ((s1 + K1) | (K2 - s1) | (s2 + K1) | (K2 - s2)) & 0x80008000u;
+        }
+        // bit 14: pixel 4k, 15: 4k+1, 30: 4k+2, 31: 4k+3
+        const uint32_t w = (t[0] >> 1) | t[1];
+        bits |= ((w >> 14) & 3u) << (4 * k);
+        bits |= ((w >> 28) & 12u) << (4 * k);
     }
     return bits;
 }
@@ -139,13 +185,13 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
         for (int j = 0; j < R + 2; ++j)
             eb[j] = (lane == 0) ? load_edge_byte(F, x0 - 1, ya - 1 + j)
                                 : ((lane == 31) ? load_edge_byte(F, x0 + 16, ya - 1 + j) : 0u);
-        Row top = make_row(raw[0], eb[0], eb[0], lane);
-        Row mid = make_row(raw[1], eb[1], eb[1], lane);
+        URow top = unpack(make_row(raw[0], eb[0], eb[0], lane));
+        URow mid = unpack(make_row(raw[1], eb[1], eb[1], lane));
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = ya + r;
-            Row bot = make_row(raw[r + 2], eb[r + 2], eb[r + 2], lane);
-            uint32_t bits = (y < F.h) ? (sobel16(top, mid, bot, L.threshold) & colmask) : 0u;
+            URow bot = unpack(make_row(raw[r + 2], eb[r + 2], eb[r + 2], lane));
+            uint32_t bits = (y < F.h) ? (sobel16(top, mid, bot, (uint32_t)L.threshold) & colmask) : 0u;
             if (L.border == LD_BORDER_CLEAR && (y == 0 || y == F.h - 1)) bits = 0;
             masks[r] = bits;
             if (F.bin != nullptr && x0 < F.pitch && y < F.h) {
