@@ -332,12 +332,12 @@ def main():
                            "parallelism": f"frames sharded across {world} GPU(s), no collective",
                            "l2": "flushed (256 MiB write) before every timed step",
                            "edges_per_frame_mean": e_sum / nf},
-                "stage_ms": {"sobel_binarize": stage_ms[0], "hough_vote": stage_ms[1], "peaks": stage_ms[2]},
+                "stage_ms": {"sobel_binarize": stage_ms[0], "hough_vote_and_peaks": stage_ms[1]},
                 "roofline": roof, "roofline_sobel": roof_sobel,
                 "e2e": {"value": e2e_val, "unit": "frames/s",
                         "h2d_bytes_per_step": int(frames_h.numel()),
                         "d2h_bytes_per_step": int(peaks_h.numel() * 4 + npk_h.numel() * 4 + st_h.numel() * 4)},
-                "gpu_launches": 3 * args.steps,
+                "gpu_launches": 2 * args.steps,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -2,6 +2,7 @@
 // validation, the context (Q16 cos/sin tables, scratch), launch planning.
 // All computation runs in the kernels of ld_sobel.cu, ld_hough.cu and
 // ld_peaks.cu; nothing here computes a result on the host.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -204,6 +205,17 @@ int pick_rows(int64_t tiles_x, int64_t total_rows_tiles_at_r2, int num_sms) {
     return 2;
 }
 
+// Small per-context scratch: per-frame edge counts, error flags and finished
+// tile counts of one launch group, and the work-queue head.
+constexpr size_t kSmallInts = 3 * kMaxLaunchFrames + 32;
+struct Small {
+    int32_t *counts, *flags, *done, *queue;
+};
+Small small_of(void *p) {
+    int32_t *b = (int32_t *)p;
+    return {b, b + kMaxLaunchFrames, b + 2 * kMaxLaunchFrames, b + 3 * kMaxLaunchFrames};
+}
+
 struct HoughPlan {
     int n_rho, D, pairs, n_tiles;
 };
@@ -306,7 +318,7 @@ ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames, in
     const int64_t groups_frames = max_frames < kMaxLaunchFrames ? max_frames : kMaxLaunchFrames;
     if (!ctx->edges.ensure((size_t)(max_pixels + 4 * (int64_t)groups_frames) * 4))
         return fail(LD_ERR_NOMEM, "scratch edges: %lld pixels", (long long)max_pixels);
-    if (!ctx->small.ensure((size_t)2 * kMaxLaunchFrames * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
     const int64_t per_frame = (int64_t)(p.n_theta / 2) * cand_m(p);
     const int64_t acc_chunks = (max_acc_cells + kSelectChunk - 1) / kSelectChunk;
     int64_t nc = groups_frames * per_frame;
@@ -409,17 +421,23 @@ ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_e
     const HoughPlan hp = plan_hough(w, h, p.n_theta);
     int ns = (ctx->num_sms + hp.n_tiles / 2) / hp.n_tiles;
     if (ns < 1) ns = 1;
+    if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    const Small sm = small_of(ctx->small.p);
     cudaStream_t s = (cudaStream_t)stream;
     if (ns > 1) {
         cudaError_t e = cudaMemsetAsync(d_acc, 0, (size_t)p.n_theta * hp.n_rho * sizeof(int32_t), s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(acc)");
     }
+    cudaError_t e = cudaMemsetAsync(sm.queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(queue)");
     HoughLaunch L;
     std::memset(&L, 0, sizeof L);
     L.n = 1;
     L.n_theta = p.n_theta;
     L.mode = kHoughFullAcc;
     L.trig = dt;
+    L.queue = sm.queue;
+    L.total_units = hp.n_tiles * ns;
     HoughFrame &F = L.f[0];
     F.edges = d_edges;
     F.count = d_edge_count;
@@ -433,7 +451,8 @@ ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_e
     F.n_splits = ns;
     F.pairs_per_tile = hp.pairs;
     F.n_tiles = hp.n_tiles;
-    cudaError_t e = launch_hough(L, hp.n_tiles * ns, hp.pairs, (int64_t)hp.pairs * hp.n_rho, s);
+    const int n_ctas = L.total_units < ctx->num_sms ? L.total_units : ctx->num_sms;
+    e = launch_hough(L, n_ctas, hp.pairs, (int64_t)hp.pairs * hp.n_rho, s);
     if (e != cudaSuccess) return cuda_fail(e, "hough launch");
     return LD_OK;
 }
@@ -522,26 +541,26 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         if (ca > max_cand) max_cand = ca;
     }
     if (!ctx->edges.ensure((size_t)max_edges * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
-    if (!ctx->small.ensure((size_t)2 * kMaxLaunchFrames * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
     if (!ctx->cand.ensure((size_t)max_cand * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
     uint32_t *edges = (uint32_t *)ctx->edges.p;
-    int32_t *counts = (int32_t *)ctx->small.p;
-    int32_t *flags = counts + kMaxLaunchFrames;
+    const Small sm = small_of(ctx->small.p);
     uint64_t *cand = (uint64_t *)ctx->cand.p;
     cudaStream_t s = (cudaStream_t)stream;
 
     SobelLaunch SLn;
     HoughLaunch HLn;
-    MergeLaunch MLn;
+    std::vector<int> order;
+    std::vector<int64_t> eoffs, coffs;
+    std::vector<HoughPlan> plans;
 
     for (int g0 = 0; g0 < n; g0 += kMaxLaunchFrames) {
         const int g1 = g0 + kMaxLaunchFrames < n ? g0 + kMaxLaunchFrames : n;
         const int gn = g1 - g0;
-        cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)2 * kMaxLaunchFrames * 4, s);
+        cudaError_t e = cudaMemsetAsync(sm.counts, 0, kSmallInts * 4, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
         std::memset(&SLn, 0, sizeof SLn);
         std::memset(&HLn, 0, sizeof HLn);
-        std::memset(&MLn, 0, sizeof MLn);
         SLn.n = gn;
         SLn.threshold = p.threshold;
         SLn.border = p.border;
@@ -552,26 +571,29 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         }
         SLn.rows_per_warp = pick_rows(0, tiles_r2, ctx->num_sms);
         const int rows_cta = SLn.rows_per_warp * (kSobelThreads / 32);
-        HLn.n = gn;
-        HLn.n_theta = p.n_theta;
-        HLn.mode = kHoughCandidates;
-        HLn.cand_m = M;
-        HLn.min_votes = p.min_votes;
-        HLn.trig = dt;
-        MLn.n = gn;
-        MLn.top_k = p.top_k;
-        MLn.nms_theta = p.nms_theta;
-        MLn.nms_rho = p.nms_rho;
-        int sob_ctas = 0, hough_ctas = 0, pmax = 1;
+        // per-frame scratch offsets and plans (frame order)
+        eoffs.assign(gn, 0);
+        coffs.assign(gn, 0);
+        plans.resize(gn);
         int64_t eoff = 0, coff = 0;
-        for (int i = g0; i < g1; ++i) {
-            const ld_frame &fr = h_frames[i];
-            const int k = i - g0;
+        for (int k = 0; k < gn; ++k) {
+            const ld_frame &fr = h_frames[g0 + k];
+            plans[k] = plan_hough(fr.w, fr.h, p.n_theta);
+            eoffs[k] = eoff;
+            coffs[k] = coff;
+            eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
+            coff += (int64_t)plans[k].n_tiles * M;
+        }
+        int sob_ctas = 0;
+        for (int k = 0; k < gn; ++k) {
+            const ld_frame &fr = h_frames[g0 + k];
             SobelFrame &SF = SLn.f[k];
             SF.img = fr.img;
             SF.bin = nullptr;
-            SF.edges = edges + eoff;
-            SF.count = counts + k;
+            SF.edges = edges + eoffs[k];
+            SF.count = sm.counts + k;
+            SF.status_init = d_status + g0 + k;
+            SF.npeaks_init = d_n_peaks + g0 + k;
             SF.cap = (int64_t)fr.w * fr.h;
             SF.w = fr.w;
             SF.h = fr.h;
@@ -579,43 +601,58 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
             SF.tile_begin = sob_ctas;
             SF.tiles_x = (fr.w + kSobelTileW - 1) / kSobelTileW;
             sob_ctas += SF.tiles_x * ((fr.h + rows_cta - 1) / rows_cta);
-
-            const HoughPlan hp = plan_hough(fr.w, fr.h, p.n_theta);
-            HoughFrame &HF = HLn.f[k];
-            HF.edges = edges + eoff;
-            HF.count = counts + k;
-            HF.cap = SF.cap;
+        }
+        // voting work units: frames with the most work (pixels x tile size)
+        // first, so that the persistent CTAs end together (longest first)
+        order.resize(gn);
+        for (int k = 0; k < gn; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const int64_t ca = (int64_t)h_frames[g0 + a].w * h_frames[g0 + a].h * plans[a].pairs;
+            const int64_t cb = (int64_t)h_frames[g0 + b].w * h_frames[g0 + b].h * plans[b].pairs;
+            return ca > cb;
+        });
+        HLn.n = gn;
+        HLn.n_theta = p.n_theta;
+        HLn.mode = kHoughCandidates;
+        HLn.cand_m = M;
+        HLn.min_votes = p.min_votes;
+        HLn.top_k = p.top_k;
+        HLn.nms_theta = p.nms_theta;
+        HLn.nms_rho = p.nms_rho;
+        HLn.trig = dt;
+        HLn.queue = sm.queue;
+        int units = 0, pmax = 1;
+        int64_t words_max = 0;
+        for (int q = 0; q < gn; ++q) {
+            const int k = order[q];
+            const ld_frame &fr = h_frames[g0 + k];
+            const HoughPlan &hp = plans[k];
+            HoughFrame &HF = HLn.f[q];
+            HF.edges = edges + eoffs[k];
+            HF.count = sm.counts + k;
+            HF.cap = (int64_t)fr.w * fr.h;
             HF.acc = nullptr;
-            HF.cand = cand + coff;
-            HF.flags = flags + k;
+            HF.cand = cand + coffs[k];
+            HF.flags = sm.flags + k;
+            HF.done = sm.done + k;
+            HF.peaks = d_peaks + (size_t)(g0 + k) * p.top_k;
+            HF.n_peaks = d_n_peaks + g0 + k;
+            HF.status = d_status + g0 + k;
             HF.w = fr.w;
             HF.h = fr.h;
             HF.D = hp.D;
             HF.n_rho = hp.n_rho;
-            HF.unit_begin = hough_ctas;
+            HF.unit_begin = units;
             HF.n_splits = 1;
             HF.pairs_per_tile = hp.pairs;
             HF.n_tiles = hp.n_tiles;
-            hough_ctas += hp.n_tiles;
+            units += hp.n_tiles;
             if (hp.pairs > pmax) pmax = hp.pairs;
-
-            MergeJob &MJ = MLn.j[k];
-            MJ.cand = cand + coff;
-            MJ.n_cand = (int64_t)hp.n_tiles * M;
-            MJ.peaks = d_peaks + (size_t)i * p.top_k;
-            MJ.n_peaks = d_n_peaks + i;
-            MJ.status = d_status + i;
-            MJ.flags = flags + k;
-
-            eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
-            coff += (int64_t)hp.n_tiles * M;
-        }
-        // dynamic shared memory = max over frames of pairs * n_rho words
-        int64_t words_max = 0;
-        for (int k = 0; k < gn; ++k) {
-            const int64_t wds = (int64_t)HLn.f[k].pairs_per_tile * HLn.f[k].n_rho;
+            const int64_t wds = (int64_t)hp.pairs * hp.n_rho;
             if (wds > words_max) words_max = wds;
         }
+        HLn.total_units = units;
+        const int hough_ctas = units < ctx->num_sms ? units : ctx->num_sms;
         const bool first = (g0 == 0), last = (g1 == n);
         if (ctx->timing && first) cudaEventRecord(ctx->ev[0], s);
         e = launch_sobel(SLn, sob_ctas, s);
@@ -624,8 +661,6 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         e = launch_hough(HLn, hough_ctas, pmax, words_max, s);
         if (e != cudaSuccess) return cuda_fail(e, "hough launch");
         if (ctx->timing && first) cudaEventRecord(ctx->ev[2], s);
-        e = launch_merge(MLn, s);
-        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
         if (ctx->timing && last) {
             cudaEventRecord(ctx->ev[3], s);
             ctx->timed_once = true;

@@ -22,6 +22,7 @@
 // Every mbarrier wait is bounded; a wait that gives up sets the frame's
 // timeout flag and the CTA leaves after draining its own copies.
 #include "ld_internal.cuh"
+#include "ld_merge.cuh"
 #include "ld_select.cuh"
 
 namespace ld {
@@ -29,6 +30,8 @@ namespace {
 
 constexpr int kRingBytes = kStages * kChunkEdges * 4;   // 30336 bytes
 constexpr int kRingBytesPad = (kRingBytes + 127) / 128 * 128;
+// static shared memory of the kernel (barriers, select and merge scratch)
+constexpr int kStaticSmemReserve = (int)(sizeof(SelectSmem) + sizeof(MergeSmem)) + 512;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -138,22 +141,13 @@ __device__ __forceinline__ void vote_chunk(const uint32_t *buf, const uint32_t *
     }
 }
 
+// One work unit: theta tile `local / n_splits` of frame F over edge range
+// `local % n_splits`.  seq counts the chunks this CTA streamed before (it
+// fixes the stage and phase of every mbarrier).  Returns false if a bounded
+// wait gave up (the frame is flagged; the CTA must stop).
 template <int PMAX>
-__global__ void __launch_bounds__(kHoughThreads, 1)
-hough_kernel(const __grid_constant__ HoughLaunch L) {
-    extern __shared__ __align__(128) uint8_t smem_raw[];
-    __shared__ uint64_t bars[kStages];
-    __shared__ SelectSmem S;
-    __shared__ int abort_flag;
-
-    // ---- which frame / theta tile / edge split
-    int lo = 0, hi = L.n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (L.f[mid].unit_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    const HoughFrame &F = L.f[lo];
-    const int local = blockIdx.x - F.unit_begin;
+__device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFrame &F, int local, uint32_t &seq,
+                                           uint8_t *smem_raw, uint64_t *bars, SelectSmem &S, int &abort_flag) {
     const int ns = F.n_splits;
     const int tile = local / ns, split = local % ns;
     const int n_theta = L.n_theta;
@@ -180,13 +174,8 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
         }
     }
 
-    // ---- zero the accumulator tile, set up the barriers
+    // ---- zero the accumulator tile
     for (int i = tid; i < words; i += kHoughThreads) acc[i] = 0u;
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-        abort_flag = 0;
-    }
     __syncthreads();
 
     // ---- this CTA's edge range (split boundaries are multiples of 4 edges)
@@ -197,7 +186,8 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     const int64_t e1 = (split + 1 == ns) ? E : ((E * (split + 1) / ns) & ~int64_t(3));
     const int64_t n_chunks = (e1 > e0) ? (e1 - e0 + kChunkEdges - 1) / kChunkEdges : 0;
 
-    auto issue = [&](int64_t c, int st) {
+    auto issue = [&](int64_t c) {
+        const int st = (int)((seq + (uint32_t)c) % kStages);
         const int64_t start = e0 + c * kChunkEdges;
         const int n_c = (int)((e1 - start) < kChunkEdges ? (e1 - start) : kChunkEdges);
         const int n4 = n_c & ~3;
@@ -209,13 +199,15 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
         }
     };
     if (tid == 0) {
-        for (int64_t c = 0; c < n_chunks && c < kStages; ++c) issue(c, (int)c);
+        fence_proxy_async();   // the ring was last written by generic stores
+        for (int64_t c = 0; c < n_chunks && c < kStages; ++c) issue(c);
     }
 
     int64_t c = 0;
     for (; c < n_chunks; ++c) {
-        const int st = (int)(c % kStages);
-        const uint32_t par = (uint32_t)((c / kStages) & 1);
+        const uint32_t g = seq + (uint32_t)c;
+        const int st = (int)(g % kStages);
+        const uint32_t par = (g / kStages) & 1u;
         const bool ok = mbar_wait_bounded(&bars[st], par);
         if (!ok) abort_flag = 1;
         if (ok) {
@@ -236,19 +228,22 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
         if (abort_flag) break;
         if (tid == 0 && c + kStages < n_chunks) {
             fence_proxy_async();
-            issue(c + kStages, st);
+            issue(c + kStages);
         }
     }
 
     if (abort_flag) {
         // drain this CTA's own copies still in flight (bounded), flag the frame
         if (tid == 0) {
-            for (int64_t k = c; k < n_chunks && k < c + kStages; ++k)
-                (void)mbar_wait_bounded(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+            for (int64_t k = c; k < n_chunks && k < c + kStages; ++k) {
+                const uint32_t g = seq + (uint32_t)k;
+                (void)mbar_wait_bounded(&bars[g % kStages], (g / kStages) & 1u);
+            }
             if (F.flags) atomicOr(F.flags, kFlagTimeout);
         }
-        return;
+        return false;
     }
+    seq += (uint32_t)n_chunks;
     __syncthreads();
 
     if (L.mode == kHoughFullAcc) {
@@ -268,7 +263,7 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
                 }
             }
         }
-        return;
+        return true;
     }
 
     // ---- candidate mode: exact local top-M of this tile (see ld_select.cuh)
@@ -335,7 +330,7 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
                 __syncthreads();
                 block_sort_desc(keys, n2);
                 for (int i = tid; i < M; i += kHoughThreads) out[i] = keys[i];
-                return;
+                return true;
             }
         }
         __syncthreads();
@@ -426,6 +421,57 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     // unused slots (fewer included cells than M) are empty keys
     const int filled = all_in ? min(S.out_n, M) : M;
     for (int i = filled + tid; i < M; i += kHoughThreads) out[i] = 0ull;
+    return true;
+}
+
+// Persistent voting kernel: each CTA (one per SM) takes work units from the
+// launch's queue until it is empty.  In candidate mode the CTA that finishes
+// the last theta tile of a frame also runs that frame's greedy peak merge
+// (ld_merge.cuh), so Steps 3-4 take one launch.
+template <int PMAX>
+__global__ void __launch_bounds__(kHoughThreads, 1)
+hough_kernel(const __grid_constant__ HoughLaunch L) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ uint64_t bars[kStages];
+    __shared__ SelectSmem S;
+    __shared__ MergeSmem MS;
+    __shared__ int abort_flag, unit_s, last_s;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    uint32_t seq = 0;
+    for (;;) {
+        if (tid == 0) unit_s = atomicAdd(L.queue, 1);
+        __syncthreads();
+        const int u = unit_s;
+        if (u >= L.total_units) break;   // block-uniform
+        int lo = 0, hi = L.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.f[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const HoughFrame &F = L.f[lo];
+        if (!hough_unit<PMAX>(L, F, u - F.unit_begin, seq, smem_raw, bars, S, abort_flag)) break;
+        if (L.mode == kHoughCandidates) {
+            __syncthreads();   // this tile's candidates are written
+            if (tid == 0) {
+                __threadfence();
+                last_s = (atomicAdd(F.done, 1) == F.n_tiles - 1) ? 1 : 0;
+            }
+            __syncthreads();
+            if (last_s) {   // block-uniform
+                __threadfence();
+                const int32_t fl = F.flags ? __ldcg(F.flags) : 0;
+                block_merge(F.cand, (int64_t)F.n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
+                            F.n_peaks, F.status, fl, MS);
+            }
+        }
+        __syncthreads();   // before unit_s is overwritten
+    }
 }
 
 template <int PMAX>
@@ -433,7 +479,7 @@ cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t
     static bool attr_set = false;   // per-process; set before the first launch
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemLimit - (int)sizeof(SelectSmem) - 256);
+                                             kSmemLimit - kStaticSmemReserve);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -444,7 +490,7 @@ cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t
 }  // namespace
 
 int hough_max_pairs(int n_rho) {
-    const int avail = kSmemLimit - (int)sizeof(SelectSmem) - 256 - kRingBytesPad;
+    const int avail = kSmemLimit - kStaticSmemReserve - kRingBytesPad;
     int p = avail / (n_rho * 4);
     return p < 30 ? p : 30;   // registers: 3 per pair, 128 per thread
 }

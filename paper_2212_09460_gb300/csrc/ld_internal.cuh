@@ -31,6 +31,8 @@ struct SobelFrame {
     uint8_t *bin;          // nullable
     uint32_t *edges;
     int32_t *count;
+    int32_t *status_init;  // nullable: set to LD_ERR_TIMEOUT until the frame's peaks are merged
+    int32_t *npeaks_init;  // nullable: set to 0 likewise
     int64_t cap;
     int32_t w, h, pitch;
     int32_t tile_begin;    // first CTA of this frame
@@ -67,9 +69,13 @@ struct HoughFrame {
     int32_t *acc;          // [n_theta][n_rho] (full-acc mode)
     uint64_t *cand;        // [n_tiles][M] keys (candidate mode)
     int32_t *flags;        // nullable per-frame error flags
+    int32_t *done;         // candidate mode: tiles finished (zeroed before the launch)
+    ld_peak *peaks;        // candidate mode: merged peaks [top_k]
+    int32_t *n_peaks;
+    int32_t *status;       // nullable
     int32_t w, h, D, n_rho;
-    int32_t unit_begin;    // first CTA of this frame
-    int32_t n_splits;      // CTAs sharing one theta tile (edge ranges)
+    int32_t unit_begin;    // first work unit of this frame
+    int32_t n_splits;      // units sharing one theta tile (edge ranges)
     int32_t pairs_per_tile;
     int32_t n_tiles;
 };
@@ -80,7 +86,10 @@ struct HoughLaunch {
     int32_t mode;
     int32_t cand_m;        // M per tile (candidate mode)
     int32_t min_votes;
+    int32_t total_units;   // work units over all frames
+    int32_t top_k, nms_theta, nms_rho;   // candidate mode: the merge
     int32_t pad_;
+    int32_t *queue;        // work-queue head (zeroed before the launch)
     const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
     HoughFrame f[kMaxLaunchFrames];
 };
@@ -134,7 +143,9 @@ __host__ __device__ inline uint64_t peak_key(int32_t votes, int32_t theta, int32
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s);
-// acc_words_max: the largest pairs_per_tile * n_rho over the launch's frames.
+// Persistent launch: n_ctas CTAs (at most one per SM) pull L.total_units
+// work units from L.queue.  acc_words_max: the largest pairs_per_tile * n_rho
+// over the launch's frames.
 cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_t acc_words_max,
                          cudaStream_t s);
 cudaError_t launch_select(const SelectLaunch &L, int n_ctas, cudaStream_t s);

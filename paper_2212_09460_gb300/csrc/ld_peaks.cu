@@ -7,9 +7,9 @@
 // contiguous (theta, rho) cells and keeps each chunk's exact top-M (the
 // argument for exactness is in ld_select.cuh); the voting kernel emits the
 // same per-tile candidates directly from shared memory in ld_detect_batch.
-// merge_kernel then runs the greedy over one frame's candidates: top_k rounds
-// of a block-wide arg-max over the candidates no pick has suppressed.
+// merge_kernel then runs the greedy over one frame's candidates (ld_merge.cuh).
 #include "ld_internal.cuh"
+#include "ld_merge.cuh"
 #include "ld_select.cuh"
 
 namespace ld {
@@ -144,58 +144,10 @@ select_kernel(const __grid_constant__ SelectLaunch L) {
 
 __global__ void __launch_bounds__(kMergeThreads)
 merge_kernel(const __grid_constant__ MergeLaunch L) {
-    __shared__ uint64_t picks[kMaxTopK];
-    __shared__ uint64_t red[kMergeThreads / 32];
+    __shared__ MergeSmem S;
     const MergeJob &J = L.j[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ht = L.nms_theta / 2, hr = L.nms_rho / 2;
-    int n_picked = 0;
-    for (int round = 0; round < L.top_k; ++round) {
-        uint64_t best = 0;
-        for (int64_t i = tid; i < J.n_cand; i += kMergeThreads) {
-            const uint64_t key = J.cand[i];
-            if (key <= best) continue;   // also skips empty (0) slots
-            const int th = 0xFFFF - (int)((key >> 16) & 0xFFFFu);
-            const int rh = 0xFFFF - (int)(key & 0xFFFFu);
-            bool sup = false;
-            for (int p = 0; p < n_picked; ++p) {
-                const int pt = 0xFFFF - (int)((picks[p] >> 16) & 0xFFFFu);
-                const int pr = 0xFFFF - (int)(picks[p] & 0xFFFFu);
-                if (abs(th - pt) <= ht && abs(rh - pr) <= hr) { sup = true; break; }
-            }
-            if (!sup) best = key;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t v = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-            best = v > best ? v : best;
-        }
-        if (lane == 0) red[warp] = best;
-        __syncthreads();
-        if (tid == 0) {
-            uint64_t b = 0;
-            for (int w = 0; w < kMergeThreads / 32; ++w) b = red[w] > b ? red[w] : b;
-            picks[round] = b;
-        }
-        __syncthreads();
-        if (picks[round] == 0ull) break;
-        ++n_picked;
-    }
-    if (tid < n_picked) {
-        const uint64_t key = picks[tid];
-        ld_peak pk;
-        pk.theta_idx = 0xFFFF - (int)((key >> 16) & 0xFFFFu);
-        pk.rho_idx = 0xFFFF - (int)(key & 0xFFFFu);
-        pk.votes = (int32_t)((uint32_t)(key >> 32) ^ 0x80000000u);
-        J.peaks[tid] = pk;
-    }
-    if (tid == 0) {
-        *J.n_peaks = n_picked;
-        if (J.status) {
-            const int32_t fl = J.flags ? *J.flags : 0;
-            *J.status = (fl & kFlagTimeout) ? LD_ERR_TIMEOUT : LD_OK;
-        }
-    }
+    const int32_t fl = J.flags ? *J.flags : 0;
+    block_merge(J.cand, J.n_cand, L.top_k, L.nms_theta, L.nms_rho, J.peaks, J.n_peaks, J.status, fl, S);
 }
 
 }  // namespace

@@ -157,6 +157,10 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
     }
     const SobelFrame &F = L.f[lo];
     const int local = t - F.tile_begin;
+    if (local == 0 && threadIdx.x == 0) {   // until the merge writes the frame's peaks
+        if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
+        if (F.npeaks_init) *F.npeaks_init = 0;
+    }
     const int tx = local % F.tiles_x, ty = local / F.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = tx * kSobelTileW + lane * 16;
