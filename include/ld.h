@@ -95,7 +95,9 @@ LD_API ld_status ld_params_default(ld_params *p);
 
 /* Create a context on CUDA device `device`: Q16 tables and scratch for
  * ld_hough_peaks and ld_detect_batch are allocated lazily and kept until
- * ld_ctx_destroy.  A context may be used from one host thread at a time. */
+ * ld_ctx_destroy.  A context may be used from one host thread at a time, and
+ * the device work of two calls on one context must not overlap (they share
+ * its scratch): use one stream per context, or one context per stream. */
 LD_API ld_status ld_ctx_create(ld_ctx **out, int device);
 LD_API ld_status ld_ctx_destroy(ld_ctx *ctx);
 
@@ -201,13 +203,34 @@ LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
                                        ld_peak *d_peaks, int32_t *d_n_peaks,
                                        void *stream);
 
+/*
+ * Autotuner for ld_detect_batch.  For every distinct frame size among
+ * h_frames (device images, as in ld_detect_batch), it times ld_detect_batch
+ * on the frames of that size for each candidate voting tile size (theta
+ * pairs per CTA: the compiled sizes from 1/8 of the largest that fits shared
+ * memory up to it) and each
+ * Sobel strip height (2, 4 or 8 rows per warp), `iters` times each, and keeps
+ * the fastest pair in the context; later ld_detect_batch calls on frames of
+ * that size and n_theta use it.  Results do not depend on the choice.  Runs
+ * and synchronises `stream`; allocates scratch like ld_detect_batch; must not
+ * be captured.  iters >= 1.
+ */
+LD_API ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                             const ld_params *p, int32_t iters, void *stream);
+
+/* The voting tile size (theta pairs per CTA) and Sobel rows per warp that
+ * ld_detect_batch uses for w x h frames with p->n_theta (tuned or default). */
+LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *p,
+                             int32_t *pairs_per_tile, int32_t *sobel_rows);
+
 /* Stage timing.  After ld_ctx_enable_timing(ctx, 1), every ld_detect_batch
- * call also records CUDA events on its stream around its kernels: before
- * Steps 1-2, between Steps 1-2 and Step 3, between Step 3 and Step 4, and
- * after Step 4 (batches of more than 128 frames: the first three events
- * bracket the first launch group, the last one follows the last group).
- * ld_ctx_stage_ms waits for the last such call and returns the device time of
- * its three stages in milliseconds.  enable = 0 switches recording off. */
+ * call also records CUDA events on its stream around its launches: before
+ * Steps 1-2, between Steps 1-2 and Steps 3-4 (the voting launch also merges
+ * the peaks), and after Steps 3-4 (batches of more than 128 frames: the
+ * first launch group).  ld_ctx_stage_ms waits for every call timed since its
+ * previous use (at most 1024) and returns, summed over them, the device time
+ * of Steps 1-2 (ms[0]) and Steps 3-4 (ms[1]) in milliseconds and the number
+ * of calls in ms[2].  enable = 0 switches recording off. */
 LD_API ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable);
 LD_API ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]);
 

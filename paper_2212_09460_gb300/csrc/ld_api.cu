@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -81,9 +82,12 @@ struct ld_ctx {
     std::map<int, int32_t *> trig;        // n_theta -> device Q16 table
     std::map<int, std::vector<int32_t>> trig_host;
     DevBuf edges, small, cand;            // detect_batch / hough_peaks scratch
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev;   // 3 events per timed call, reused in order
+    int timed_calls = 0;           // timed calls since the last ld_ctx_stage_ms
     bool timing = false;
-    bool timed_once = false;
+    // autotuned plans: (w, h, n_theta) -> (theta pairs per tile, Sobel rows per warp)
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+    int force_pairs = 0, force_rows = 0;   // set while the autotuner times candidates
     std::mutex mu;
 };
 
@@ -220,6 +224,18 @@ struct HoughPlan {
     int n_rho, D, pairs, n_tiles;
 };
 
+HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
+    HoughPlan hp;
+    hp.D = (int)rho_max_of(w, h);
+    hp.n_rho = 2 * hp.D + 1;
+    const int n_pairs = n_theta / 2;
+    const int pmax = hough_max_pairs(hp.n_rho);
+    hp.pairs = pairs < 1 ? 1 : (pairs > pmax ? pmax : pairs);
+    if (hp.pairs > n_pairs) hp.pairs = n_pairs;
+    hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
+    return hp;
+}
+
 HoughPlan plan_hough(int w, int h, int n_theta) {
     HoughPlan hp;
     hp.D = (int)rho_max_of(w, h);
@@ -242,6 +258,33 @@ HoughPlan plan_hough(int w, int h, int n_theta) {
     hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
     return hp;
 }
+
+HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta) {
+    if (ctx->force_pairs > 0) return plan_with_pairs(w, h, n_theta, ctx->force_pairs);
+    auto it = ctx->tuned.find(std::make_tuple(w, h, n_theta));
+    if (it != ctx->tuned.end()) return plan_with_pairs(w, h, n_theta, it->second.first);
+    return plan_hough(w, h, n_theta);
+}
+
+// Sobel rows per warp for a launch group: forced, else the tuned value of the
+// group's largest frame size, else the default heuristic.
+int rows_for(const ld_ctx *ctx, const ld_frame *fr, int g0, int g1, int n_theta, int64_t tiles_r2) {
+    if (ctx->force_rows > 0) return ctx->force_rows;
+    int64_t best_px = -1;
+    int rows = 0;
+    for (int i = g0; i < g1; ++i) {
+        auto it = ctx->tuned.find(std::make_tuple(fr[i].w, fr[i].h, n_theta));
+        const int64_t px = (int64_t)fr[i].w * fr[i].h;
+        if (it != ctx->tuned.end() && px > best_px) {
+            best_px = px;
+            rows = it->second.second;
+        }
+    }
+    return rows > 0 ? rows : pick_rows(0, tiles_r2, ctx->num_sms);
+}
+
+ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s);
 
 }  // namespace
 
@@ -276,8 +319,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         for (auto &kv : ctx->trig) cudaFree(kv.second);
-        for (auto &e : ctx->ev)
-            if (e) cudaEventDestroy(e);
+        for (auto &e : ctx->ev) cudaEventDestroy(e);
         ctx->edges.release();
         ctx->small.release();
         ctx->cand.release();
@@ -327,18 +369,11 @@ ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames, in
     return LD_OK;
 }
 
+constexpr int kMaxTimedCalls = 1024;
+
 ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable) {
     if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_enable_timing: NULL ctx");
     std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
-    if (enable) {
-        for (auto &e : ctx->ev) {
-            if (e) continue;
-            cudaError_t r = cudaEventCreate(&e);
-            if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
-        }
-    }
     ctx->timing = enable != 0;
     return LD_OK;
 }
@@ -346,15 +381,22 @@ ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable) {
 ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]) {
     if (!ctx || !ms) return fail(LD_ERR_INVALID, "ld_ctx_stage_ms: NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (!ctx->timed_once) return fail(LD_ERR_INVALID, "no timed ld_detect_batch call yet");
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
-    cudaError_t r = cudaEventSynchronize(ctx->ev[3]);
-    if (r != cudaSuccess) return cuda_fail(r, "cudaEventSynchronize");
-    for (int i = 0; i < 3; ++i) {
-        r = cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]);
-        if (r != cudaSuccess) return cuda_fail(r, "cudaEventElapsedTime");
+    ms[0] = ms[1] = 0.f;
+    ms[2] = (float)ctx->timed_calls;
+    for (int c = 0; c < ctx->timed_calls; ++c) {
+        cudaEvent_t *e = &ctx->ev[3 * c];
+        cudaError_t r = cudaEventSynchronize(e[2]);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaEventSynchronize");
+        for (int i = 0; i < 2; ++i) {
+            float t = 0.f;
+            r = cudaEventElapsedTime(&t, e[i], e[i + 1]);
+            if (r != cudaSuccess) return cuda_fail(r, "cudaEventElapsedTime");
+            ms[i] += t;
+        }
     }
+    ctx->timed_calls = 0;
     return LD_OK;
 }
 
@@ -516,6 +558,16 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    return detect_impl(ctx, h_frames, n, p, d_peaks, d_n_peaks, d_status, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s) {
+    ld_status st;
     const int32_t *dt;
     const std::vector<int32_t> *ht;
     st = get_trig(ctx, p.n_theta, &dt, &ht);
@@ -535,7 +587,7 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         int64_t ed = 0, ca = 0;
         for (int i = g0; i < g1; ++i) {
             ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
-            ca += (int64_t)plan_hough(h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles * M;
+            ca += (int64_t)plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles * M;
         }
         if (ed > max_edges) max_edges = ed;
         if (ca > max_cand) max_cand = ca;
@@ -546,7 +598,6 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
     uint32_t *edges = (uint32_t *)ctx->edges.p;
     const Small sm = small_of(ctx->small.p);
     uint64_t *cand = (uint64_t *)ctx->cand.p;
-    cudaStream_t s = (cudaStream_t)stream;
 
     SobelLaunch SLn;
     HoughLaunch HLn;
@@ -569,7 +620,7 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
             const int tx = (h_frames[i].w + kSobelTileW - 1) / kSobelTileW;
             tiles_r2 += (int64_t)tx * ((h_frames[i].h + 15) / 16);
         }
-        SLn.rows_per_warp = pick_rows(0, tiles_r2, ctx->num_sms);
+        SLn.rows_per_warp = rows_for(ctx, h_frames, g0, g1, p.n_theta, tiles_r2);
         const int rows_cta = SLn.rows_per_warp * (kSobelThreads / 32);
         // per-frame scratch offsets and plans (frame order)
         eoffs.assign(gn, 0);
@@ -578,7 +629,7 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         int64_t eoff = 0, coff = 0;
         for (int k = 0; k < gn; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
-            plans[k] = plan_hough(fr.w, fr.h, p.n_theta);
+            plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta);
             eoffs[k] = eoff;
             coffs[k] = coff;
             eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
@@ -653,20 +704,123 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
         }
         HLn.total_units = units;
         const int hough_ctas = units < ctx->num_sms ? units : ctx->num_sms;
-        const bool first = (g0 == 0), last = (g1 == n);
-        if (ctx->timing && first) cudaEventRecord(ctx->ev[0], s);
+        // stage events of this call (first launch group), 3 per timed call
+        cudaEvent_t *tev = nullptr;
+        if (ctx->timing && g0 == 0 && ctx->timed_calls < kMaxTimedCalls) {
+            const size_t need = 3 * (size_t)(ctx->timed_calls + 1);
+            while (ctx->ev.size() < need) {
+                cudaEvent_t ne;
+                cudaError_t r = cudaEventCreate(&ne);
+                if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+                ctx->ev.push_back(ne);
+            }
+            tev = &ctx->ev[3 * ctx->timed_calls];
+            ++ctx->timed_calls;
+        }
+        if (tev) cudaEventRecord(tev[0], s);
         e = launch_sobel(SLn, sob_ctas, s);
         if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
-        if (ctx->timing && first) cudaEventRecord(ctx->ev[1], s);
+        if (tev) cudaEventRecord(tev[1], s);
         e = launch_hough(HLn, hough_ctas, pmax, words_max, s);
         if (e != cudaSuccess) return cuda_fail(e, "hough launch");
-        if (ctx->timing && first) cudaEventRecord(ctx->ev[2], s);
-        if (ctx->timing && last) {
-            cudaEventRecord(ctx->ev[3], s);
-            ctx->timed_once = true;
-        }
+        if (tev) cudaEventRecord(tev[2], s);
     }
     return LD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *pp, int32_t *pairs_per_tile,
+                      int32_t *sobel_rows) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_plan: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, nullptr);
+    if (st != LD_OK) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta);
+    if (pairs_per_tile) *pairs_per_tile = hp.pairs;
+    if (sobel_rows) {
+        const ld_frame f = {nullptr, w, h, w, 0};
+        const int tx = (w + kSobelTileW - 1) / kSobelTileW;
+        *sobel_rows = rows_for(ctx, &f, 0, 1, p.n_theta, (int64_t)tx * ((h + 15) / 16));
+    }
+    return LD_OK;
+}
+
+ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp, int32_t iters,
+                      void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_autotune: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1 || iters < 1) return fail(LD_ERR_INVALID, "ld_autotune: need n >= 1 frames, iters >= 1");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // frames grouped by size
+    std::map<std::pair<int, int>, std::vector<ld_frame>> groups;
+    for (int i = 0; i < n; ++i) groups[{h_frames[i].w, h_frames[i].h}].push_back(h_frames[i]);
+    size_t max_n = 0;
+    for (auto &kv : groups) max_n = std::max(max_n, kv.second.size());
+    void *outs = nullptr;
+    cudaError_t e = cudaMalloc(&outs, max_n * (sizeof(ld_peak) * p.top_k + 2 * sizeof(int32_t)));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(autotune outputs)");
+    ld_peak *d_peaks = (ld_peak *)outs;
+    int32_t *d_np = (int32_t *)(d_peaks + max_n * p.top_k);
+    int32_t *d_st = d_np + max_n;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    st = LD_OK;
+    for (auto &kv : groups) {
+        const int w = kv.first.first, h = kv.first.second;
+        const std::vector<ld_frame> &fr = kv.second;
+        const int n_rho = 2 * (int)rho_max_of(w, h) + 1;
+        const int pmax = std::min(hough_max_pairs(n_rho), p.n_theta / 2);
+        std::vector<int> pair_cands;
+        // all compiled tile sizes down to 1/8 of what fits: small frames want
+        // many small tiles (more CTAs), large batches few large ones
+#define LD_CAND(P) if (P <= pmax && 8 * P >= pmax) pair_cands.push_back(P);
+        LD_HOUGH_PAIR_SIZES(LD_CAND)
+#undef LD_CAND
+        if (pair_cands.empty()) pair_cands.push_back(std::max(1, pmax));
+        float best_ms = 1e30f;
+        int best_p = 0, best_r = 0;
+        for (int P : pair_cands) {
+            for (int R : {2, 4, 8}) {
+                ctx->force_pairs = P;
+                ctx->force_rows = R;
+                st = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);   // warm-up
+                if (st != LD_OK) break;
+                cudaEventRecord(e0, s);
+                for (int it = 0; it < iters && st == LD_OK; ++it)
+                    st = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);
+                cudaEventRecord(e1, s);
+                if (st != LD_OK) break;
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) { best_ms = ms; best_p = P; best_r = R; }
+            }
+            if (st != LD_OK) break;
+        }
+        ctx->force_pairs = 0;
+        ctx->force_rows = 0;
+        if (st != LD_OK) break;
+        ctx->tuned[std::make_tuple(w, h, p.n_theta)] = {best_p, best_r};
+    }
+    ctx->force_pairs = 0;
+    ctx->force_rows = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(outs);
+    return st;
 }
 
 }  // extern "C"

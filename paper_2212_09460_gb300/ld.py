@@ -60,6 +60,9 @@ _SIGS = {
     "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
                         _P],
     "ld_hough_peaks_static": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
+    "ld_autotune": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.c_int32, _P],
+    "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
+                    ctypes.POINTER(ctypes.c_int32)],
     "ld_ctx_enable_timing": [_P, ctypes.c_int],
     "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
 }
@@ -152,12 +155,9 @@ def ld_hough_peaks(ctx, d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) ->
 
 
 def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> None:
-    """frames: sequence of (device_ptr, w, h, pitch)."""
-    arr = (ld_frame * len(frames))()
-    for i, (ptr, w, h, pitch) in enumerate(frames):
-        arr[i].img, arr[i].w, arr[i].h, arr[i].pitch, arr[i].reserved = ptr, w, h, pitch, 0
-    _check(load().ld_detect_batch(ctx, arr, len(frames), ctypes.byref(p), d_peaks, d_n_peaks, d_status,
-                                  stream))
+    """frames: sequence of (device_ptr, w, h, pitch), or a ctypes ld_frame array."""
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
 
 
 def ld_hough_peaks_static(d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) -> None:
@@ -165,14 +165,33 @@ def ld_hough_peaks_static(d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) 
     _check(load().ld_hough_peaks_static(d_acc, n_theta, n_rho, ctypes.byref(p), d_peaks, d_n_peaks, stream))
 
 
+def _frames_array(frames):
+    arr = (ld_frame * len(frames))()
+    for i, (ptr, w, h, pitch) in enumerate(frames):
+        arr[i].img, arr[i].w, arr[i].h, arr[i].pitch, arr[i].reserved = ptr, w, h, pitch, 0
+    return arr
+
+
+def ld_autotune(ctx, frames, p, iters, stream) -> None:
+    """frames: sequence of (device_ptr, w, h, pitch)."""
+    _check(load().ld_autotune(ctx, _frames_array(frames), len(frames), ctypes.byref(p), iters, stream))
+
+
+def ld_ctx_plan(ctx, w, h, p) -> tuple[int, int]:
+    pairs, rows = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ld_ctx_plan(ctx, w, h, ctypes.byref(p), ctypes.byref(pairs), ctypes.byref(rows)))
+    return pairs.value, rows.value
+
+
 def ld_ctx_enable_timing(ctx: int, enable: bool) -> None:
     _check(load().ld_ctx_enable_timing(ctx, 1 if enable else 0))
 
 
-def ld_ctx_stage_ms(ctx: int) -> tuple[float, float, float]:
+def ld_ctx_stage_ms(ctx: int) -> tuple[float, float, int]:
+    """(Steps 1-2 ms, Steps 3-4 ms, calls): summed over the calls timed since the last read."""
     ms = (ctypes.c_float * 3)()
     _check(load().ld_ctx_stage_ms(ctx, ctypes.byref(ms)))
-    return ms[0], ms[1], ms[2]
+    return ms[0], ms[1], int(ms[2])
 
 
 def ld_last_error() -> str:
@@ -190,6 +209,12 @@ def _stream_handle(stream=None) -> int:
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+@dataclass
+class PreparedBatch:
+    array: "ctypes.Array"   # ld_frame descriptors
+    device: "object"
 
 
 @dataclass
@@ -269,15 +294,34 @@ class Context:
                        _stream_handle(stream))
         return peaks, n
 
-    def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
-        """Steps 1-4 on a list of uint8 CUDA tensors; returns (peaks [n][top_k][3], n_peaks [n], status [n])."""
-        torch = _torch()
+    def _descs(self, frames, widths=None):
         descs = []
         for i, f in enumerate(frames):
             ptr, pw, h, pitch = self._img(f)
             descs.append((ptr, pw if widths is None else widths[i], h, pitch))
+        return descs
+
+    def autotune(self, frames, p: ld_params, iters: int = 3, widths=None, stream=None) -> None:
+        """Tune tile sizes on representative frames (synchronises the stream)."""
+        ld_autotune(self.handle, self._descs(frames, widths), p, iters, _stream_handle(stream))
+
+    def plan(self, w: int, h: int, p: ld_params) -> tuple[int, int]:
+        """(theta pairs per voting tile, Sobel rows per warp) used for w x h frames."""
+        return ld_ctx_plan(self.handle, w, h, p)
+
+    def prepare(self, frames, widths=None) -> "PreparedBatch":
+        """Build the frame descriptors once, for repeated detect_batch calls on the same tensors."""
+        return PreparedBatch(_frames_array(self._descs(frames, widths)), frames[0].device)
+
+    def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
+        """Steps 1-4 on a list of uint8 CUDA tensors (or a PreparedBatch);
+        returns (peaks [n][top_k][3], n_peaks [n], status [n])."""
+        torch = _torch()
+        if isinstance(frames, PreparedBatch):
+            descs, dev = frames.array, frames.device
+        else:
+            descs, dev = self._descs(frames, widths), frames[0].device
         n = len(descs)
-        dev = frames[0].device
         if out is None:
             out = (torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev),
                    torch.zeros(n, dtype=torch.int32, device=dev),

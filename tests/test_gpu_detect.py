@@ -72,3 +72,44 @@ def test_detect_full_size_batch_sampled(ctx, ldlib, ora):
     for i in (0, 21, 42, 63):
         ref = ora.detect(raw[seeds[i]], 360, 4)
         np.testing.assert_array_equal(pk[i], ref, err_msg=f"frame {i}")
+
+
+MIXED_SIZES = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+
+
+def test_detect_mixed_resolution_batch_sampled(ctx, ldlib, ora):
+    # the batching workload's four resolutions, two frames each, in one call
+    # (one persistent voting launch over all of them), 360 theta, top-4
+    sizes = [s for s in MIXED_SIZES for _ in range(2)]
+    raw = [synth.road_frame(2000 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    kw = dict(n_theta=360, top_k=4)
+    pk, n, st = _detect(ctx, ldlib, raw, [w for w, h in sizes], **kw)
+    for i in (0, 3, 4, 7):
+        ref = ora.detect(raw[i], 360, 4)
+        assert st[i] == 0 and n[i] == len(ref)
+        np.testing.assert_array_equal(pk[i, : n[i]], ref, err_msg=f"frame {i} {sizes[i]}")
+
+
+def test_autotune_keeps_results_and_sets_plans(ldlib, ora):
+    # a fresh context: tuning changes tile sizes, never results
+    c = ldlib.Context(0)
+    try:
+        sizes = [(640, 480), (640, 480), (1280, 720)]
+        raw = [synth.road_frame(3000 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+        p = ldlib.params(n_theta=360, top_k=4)
+        dev = [torch.from_numpy(r).cuda() for r in raw]
+        before = [c.plan(w, h, p) for w, h in sizes]
+        c.autotune(dev, p, iters=2)
+        after = [c.plan(w, h, p) for w, h in sizes]
+        for pairs, rows in after:
+            assert 1 <= pairs <= 30 and rows in (2, 4, 8)
+        pk, n, st = c.detect_batch(dev, p)
+        torch.cuda.synchronize()
+        pk, n, st = pk.cpu().numpy(), n.cpu().numpy(), st.cpu().numpy()
+        for i, r in enumerate(raw):
+            ref = ora.detect(r, 360, 4)
+            assert st[i] == 0 and n[i] == len(ref)
+            np.testing.assert_array_equal(pk[i, : n[i]], ref)
+        assert len(before) == len(after)
+    finally:
+        c.close()
