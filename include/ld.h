@@ -234,6 +234,90 @@ LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params 
 LD_API ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable);
 LD_API ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]);
 
+/*
+ * Input of the proposal network: for each frame, Steps 1-2 as in
+ * ld_detect_batch, then the 8x8 box-downsampled binary map: d_pool[f] is a
+ * uint8 [ceil(h/8)][ceil(w/8)] map (frames packed back to back, in order)
+ * holding the number of edge pixels (0..64) in each 8x8 block (clipped at
+ * the frame edge).
+ */
+LD_API ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                                    const ld_params *p, uint8_t *d_pool, void *stream);
+
+/*
+ * Learned theta-band proposal network: its layers as separate calls (the
+ * caller's training loop or inference orders them).  The paper has no learned
+ * stage; this network predicts, from the 8x8 edge-count map (read as
+ * count / 64 by the first layer), which
+ * 5-degree theta bands hold the top Hough peaks (36 logits) and which of 8
+ * row bands their lines cross (8 logits), so that voting can skip bands.
+ * Layout: activations NHWC, bf16 (uint8 counts 0..64 for the first layer's
+ * input, scaled by 1/64);
+ * conv weights bf16 [Cout][3][3][Cin]; biases, head, losses and gradients
+ * fp32; "dy" is the gradient with respect to a layer's ReLU output.
+ * Supported convs: 1->16 (stride 1), 16->32 and 32->32 (stride 1 or 2), all
+ * 3x3 with zero padding 1; output size (h + 2 - 3) / stride + 1.
+ */
+/* y = relu(conv(x, w) + b). */
+LD_API ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w,
+                                    int32_t cin, int32_t cout, int32_t stride,
+                                    const void *d_w, const float *d_b, void *d_y, void *stream);
+/* From dy (bf16, w.r.t. the ReLU output y): dw += dL/dw, db += dL/db (fp32,
+ * accumulated: zero them first) and, if d_dx != NULL, dx = dL/dx (bf16).  The
+ * 1-channel layer takes d_dx = NULL. */
+LD_API ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w,
+                                     int32_t cin, int32_t cout, int32_t stride,
+                                     const void *d_w, const void *d_y, const void *d_dy,
+                                     void *d_dx, float *d_dw, float *d_db, void *stream);
+/* Adaptive average pool of conv4's output y4 [n][h4][w4][32] to 4x8 ->
+ * feat [n][1024] ((bin row, bin col, channel) order), logits [n][44] =
+ * feat . wh^T + bh, wh [44][1024]. */
+LD_API ld_status ld_pool_head_forward(const void *d_y4, int32_t n, int32_t h4, int32_t w4,
+                                      const float *d_wh, const float *d_bh, float *d_feat,
+                                      float *d_logits, void *stream);
+/* dwh += dlogits^T feat, dbh += sum dlogits (accumulated), dy4 = dL/dy4 (bf16). */
+LD_API ld_status ld_pool_head_backward(const float *d_feat, const float *d_dlogits,
+                                       const float *d_wh, int32_t n, int32_t h4, int32_t w4,
+                                       float *d_dwh, float *d_dbh, void *d_dy4, void *stream);
+/* Mean binary cross-entropy with logits over n*k outputs -> *d_loss, and
+ * d_dlogits = dloss/dlogits. */
+LD_API ld_status ld_bce_loss(const float *d_logits, const float *d_target, int32_t n, int32_t k,
+                             float *d_loss, float *d_dlogits, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on fp32 params; if d_param_bf16
+ * is not NULL it receives the bf16 copy used by the forward pass. */
+LD_API ld_status ld_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v,
+                              int64_t count, float lr, float beta1, float beta2, float eps,
+                              int32_t step, void *d_param_bf16, void *stream);
+
+/*
+ * Synthetic input frames, generated on the device (for training the proposal
+ * network and feeding the serving loop).  Not a step of the method: the
+ * paper's test image is not available, so seeded synthetic road frames stand
+ * in for it.  A frame is the integer function of its descriptor described in
+ * synth.py (background gradient, Q16 stripes with dashes, Irwin-Hall noise
+ * from SplitMix64 streams, salt); both generators give the same bytes.
+ */
+typedef struct {
+    int64_t nx, ny, c;      /* inside if |x*nx + y*ny - c| < 3*65536 (Q16 unit normal) */
+    int64_t tx, ty, t0;     /* dash phase t = floor((x*tx + y*ty - t0) / 65536) */
+    int32_t dash, gap;      /* dash if t mod (dash+gap) < dash; dash = 0: solid */
+    int32_t value;          /* stripe intensity */
+    int32_t reserved;
+} ld_synth_stripe;
+
+typedef struct {
+    uint8_t *img;           /* device output [h][pitch] */
+    int32_t w, h, pitch;
+    int32_t n_stripes;      /* 0..4 */
+    uint64_t base[3];       /* SplitMix64 stream bases: noise a, noise b, salt */
+    int64_t k_top, k_road;  /* Q32 noise scale above / below the horizon y = h/2 */
+    uint64_t salt_thr;      /* salt where the draw's low 32 bits < salt_thr (0: none) */
+    ld_synth_stripe stripes[4];
+} ld_synth_frame;
+
+/* Generate n frames; d_frames is a DEVICE array of n descriptors. */
+LD_API ld_status ld_synth_frames(const ld_synth_frame *d_frames, int32_t n, void *stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 LD_API const char *ld_last_error(void);
 

@@ -732,6 +732,73 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
 
 extern "C" {
 
+ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                             uint8_t *d_pool, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_edge_pool_batch: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1 || !d_pool) return fail(LD_ERR_INVALID, "ld_edge_pool_batch: bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    int64_t pool_bytes = 0, max_edges = 0;
+    for (int i = 0; i < n; ++i) {
+        const ld_frame &f = h_frames[i];
+        st = check_size(f.w, f.h, p, nullptr);
+        if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
+        if (!f.img || f.pitch < f.w || (f.pitch & 15) || !aligned16(f.img) || f.reserved != 0)
+            return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
+        pool_bytes += (int64_t)((f.h + 7) / 8) * ((f.w + 7) / 8);
+        max_edges += ((int64_t)f.w * f.h + 3) / 4 * 4;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_pool, 0, (size_t)pool_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(pool)");
+    if (!ctx->edges.ensure((size_t)std::min<int64_t>(max_edges, kMaxLaunchFrames * (int64_t)32767 * 32767 / 4) * 4))
+        return fail(LD_ERR_NOMEM, "scratch edges");
+    if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    const Small sm = small_of(ctx->small.p);
+    SobelLaunch SL;
+    int64_t poff = 0;
+    for (int g0 = 0; g0 < n; g0 += kMaxLaunchFrames) {
+        const int g1 = std::min(n, g0 + kMaxLaunchFrames);
+        std::memset(&SL, 0, sizeof SL);
+        e = cudaMemsetAsync(sm.counts, 0, kMaxLaunchFrames * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
+        SL.n = g1 - g0;
+        SL.threshold = p.threshold;
+        SL.border = p.border;
+        int64_t tiles_r2 = 0;
+        for (int i = g0; i < g1; ++i)
+            tiles_r2 += (int64_t)((h_frames[i].w + kSobelTileW - 1) / kSobelTileW) * ((h_frames[i].h + 15) / 16);
+        SL.rows_per_warp = rows_for(ctx, h_frames, g0, g1, p.n_theta, tiles_r2);
+        const int rows_cta = SL.rows_per_warp * (kSobelThreads / 32);
+        int ctas = 0;
+        int64_t eoff = 0;
+        for (int i = g0; i < g1; ++i) {
+            const ld_frame &fr = h_frames[i];
+            SobelFrame &F = SL.f[i - g0];
+            F.img = fr.img;
+            F.edges = (uint32_t *)ctx->edges.p + eoff;
+            F.count = sm.counts + (i - g0);
+            F.pool = d_pool + poff;
+            F.cap = (int64_t)fr.w * fr.h;
+            F.w = fr.w;
+            F.h = fr.h;
+            F.pitch = fr.pitch;
+            F.tile_begin = ctas;
+            F.tiles_x = (fr.w + kSobelTileW - 1) / kSobelTileW;
+            ctas += F.tiles_x * ((fr.h + rows_cta - 1) / rows_cta);
+            eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
+            poff += (int64_t)((fr.h + 7) / 8) * ((fr.w + 7) / 8);
+        }
+        e = launch_sobel(SL, ctas, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+    }
+    return LD_OK;
+}
+
 ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *pp, int32_t *pairs_per_tile,
                       int32_t *sobel_rows) {
     if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_plan: NULL ctx");

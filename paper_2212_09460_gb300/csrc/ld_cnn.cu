@@ -1,0 +1,612 @@
+// ld_cnn.cu -- kernels of the learned theta-band proposal network (the paper
+// has no learned stage; this one predicts which 5-degree theta bands hold the
+// top Hough peaks so that voting can skip the others).
+//
+// Network (NHWC activations, bf16 storage, fp32 accumulation):
+//   conv1 3x3 s1 1->16 | conv2 3x3 s2 16->32 | conv3 3x3 s2 32->32 |
+//   conv4 3x3 s2 32->32, each + bias + ReLU | adaptive average pool to 4x8 |
+//   linear 1024 -> 44 logits (36 theta bands + 8 row bands) | BCE loss.
+//
+// conv2..4 (forward, input gradient, weight gradient) are implicit GEMMs on
+// the bf16 tensor cores with fp32 accumulation (mma.sync m16n8k16): forward
+// M = output pixels, N = Cout, K = 9*Cin; input gradient M = input pixels,
+// N = Cin, K = 9*Cout (transposed stride-2 taps); weight gradient M = Cout,
+// N = 9*Cin, K = pixels (split over CTAs, fp32 atomics).  conv1 has a single
+// input channel (K = 9) and runs on the CUDA cores.  Every output of the
+// forward pass depends only on its own sample, in a fixed summation order,
+// so a frame's logits are the same alone and in any batch.
+#include <cmath>
+#include <cstdio>
+
+#include <cuda_bf16.h>
+
+#include "ld_internal.cuh"
+
+namespace ld {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+__device__ __forceinline__ uint32_t bits16(const bf16 *p) {
+    return (uint32_t) * reinterpret_cast<const unsigned short *>(p);
+}
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+__device__ __forceinline__ uint32_t to_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+// dy masked by the ReLU: keep the gradient where the stored output is > 0
+// (ReLU outputs are +0 or positive, so "bits != 0" is "> 0").
+__device__ __forceinline__ uint32_t relu_mask2(uint32_t dyw, uint32_t yw) {
+    const uint32_t m = ((yw & 0xFFFFu) ? 0xFFFFu : 0u) | ((yw >> 16) ? 0xFFFF0000u : 0u);
+    return dyw & m;
+}
+__device__ __forceinline__ uint32_t relu_mask1(uint32_t dyb, uint32_t yb) { return yb ? dyb : 0u; }
+
+// ------------------------------------------------------------------ conv1 (Cin = 1)
+
+// y[p][16] = relu(b + sum_tap w[co][tap] * x[pix(p, tap)] / 64), x uint8 edge counts [n][h][w].
+__global__ void __launch_bounds__(256) conv1_fwd_kernel(const uint8_t *x, int n, int h, int w, const bf16 *wt,
+                                                       const float *b, bf16 *y) {
+    __shared__ float ws[16 * 9], bs[16];
+    for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(wt[i]);
+    if (threadIdx.x < 16) bs[threadIdx.x] = b[threadIdx.x];
+    __syncthreads();
+    const int64_t P = (int64_t)n * h * w;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const int img = (int)(p / ((int64_t)h * w));
+        const int rem = (int)(p - (int64_t)img * h * w);
+        const int oy = rem / w, ox = rem - (rem / w) * w;
+        float v[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int iy = oy + t / 3 - 1, ix = ox + t % 3 - 1;
+            v[t] = (iy >= 0 && iy < h && ix >= 0 && ix < w) ? (float)x[((int64_t)img * h + iy) * w + ix] * (1.f / 64.f)
+                                                             : 0.f;
+        }
+        uint32_t out[8];
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+            float s0 = bs[c], s1 = bs[c + 1];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                s0 += ws[c * 9 + t] * v[t];
+                s1 += ws[(c + 1) * 9 + t] * v[t];
+            }
+            out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(y + p * 16);
+        dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+        dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// dw1[co][tap] += sum_p dy_pre[p][co] * x[pix(p, tap)],  db1[co] += sum_p dy_pre[p][co].
+// Block: 16 channels x 16 pixel lanes.
+__global__ void __launch_bounds__(256) conv1_wgrad_kernel(const uint8_t *x, const bf16 *y, const bf16 *dy, int n,
+                                                         int h, int w, float *dw, float *db) {
+    const int co = threadIdx.x & 15, lane = threadIdx.x >> 4;
+    float acc[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) acc[t] = 0.f;
+    const int64_t P = (int64_t)n * h * w;
+    for (int64_t p = (int64_t)blockIdx.x * 16 + lane; p < P; p += (int64_t)gridDim.x * 16) {
+        const float g = __uint_as_float(relu_mask1(bits16(dy + p * 16 + co), bits16(y + p * 16 + co)) << 16);
+        if (g == 0.f) continue;
+        const int img = (int)(p / ((int64_t)h * w));
+        const int rem = (int)(p - (int64_t)img * h * w);
+        const int oy = rem / w, ox = rem - (rem / w) * w;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int iy = oy + t / 3 - 1, ix = ox + t % 3 - 1;
+            if (iy >= 0 && iy < h && ix >= 0 && ix < w)
+                acc[t] += g * ((float)x[((int64_t)img * h + iy) * w + ix] * (1.f / 64.f));
+        }
+        acc[9] += g;
+    }
+    __shared__ float red[16][16][10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) red[lane][co][t] = acc[t];
+    __syncthreads();
+    if (threadIdx.x < 160) {
+        const int c = threadIdx.x / 10, t = threadIdx.x % 10;
+        float s = 0.f;
+        for (int l = 0; l < 16; ++l) s += red[l][c][t];
+        if (t < 9) atomicAdd(dw + c * 9 + t, s);
+        else atomicAdd(db + c, s);
+    }
+}
+
+// ------------------------------------------------------------------ conv2..4 on tensor cores
+
+struct ConvGeom {
+    int n, h, w, oh, ow, stride;
+};
+
+__device__ __forceinline__ void decode(int64_t p, int hh, int ww, int &img, int &yy, int &xx) {
+    img = (int)(p / ((int64_t)hh * ww));
+    const int rem = (int)(p - (int64_t)img * hh * ww);
+    yy = rem / ww;
+    xx = rem - yy * ww;
+}
+
+// Forward: each warp computes 16 output pixels x COUT channels.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16 *x, ConvGeom G, const bf16 *wt, const float *b,
+                                                      bf16 *y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t M = (int64_t)G.n * G.oh * G.ow;
+    const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+    if (m0 >= M) return;
+    int img[2], oy[2], ox[2];
+    bool rv[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int64_t p = m0 + g + 8 * r;
+        rv[r] = p < M;
+        decode(rv[r] ? p : 0, G.oh, G.ow, img[r], oy[r], ox[r]);
+    }
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < COUT / 8; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const bf16 *src[2];
+        bool ok[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int iy = oy[r] * G.stride + ky - 1, ix = ox[r] * G.stride + kx - 1;
+            ok[r] = rv[r] && iy >= 0 && iy < G.h && ix >= 0 && ix < G.w;
+            src[r] = x + (((int64_t)img[r] * G.h + (ok[r] ? iy : 0)) * G.w + (ok[r] ? ix : 0)) * CIN;
+        }
+#pragma unroll
+        for (int cb = 0; cb < CIN / 16; ++cb) {
+            uint32_t a[4];
+            a[0] = ok[0] ? ld_u32(src[0] + cb * 16 + 2 * t) : 0u;
+            a[1] = ok[1] ? ld_u32(src[1] + cb * 16 + 2 * t) : 0u;
+            a[2] = ok[0] ? ld_u32(src[0] + cb * 16 + 2 * t + 8) : 0u;
+            a[3] = ok[1] ? ld_u32(src[1] + cb * 16 + 2 * t + 8) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < COUT / 8; ++nt) {
+                const bf16 *wp = wt + ((int64_t)(nt * 8 + g) * 9 + tap) * CIN + cb * 16;
+                mma_bf16(acc[nt], a, ld_u32(wp + 2 * t), ld_u32(wp + 2 * t + 8));
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < COUT / 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = b[c], b1 = b[c + 1];
+        if (rv[0])
+            *reinterpret_cast<uint32_t *>(y + (m0 + g) * COUT + c) =
+                to_bf16x2(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
+        if (rv[1])
+            *reinterpret_cast<uint32_t *>(y + (m0 + g + 8) * COUT + c) =
+                to_bf16x2(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
+    }
+}
+
+// Input gradient: each warp computes 16 input pixels x CIN channels of
+// dx[i][ci] = sum_{tap, co} dy_pre[o(i, tap)][co] * w[co][tap][ci], where
+// o(i, tap) is the output pixel whose tap `tap` reads input pixel i.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv_dgrad_kernel(const bf16 *y, const bf16 *dy, ConvGeom G, const bf16 *wt,
+                                                        bf16 *dx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t M = (int64_t)G.n * G.h * G.w;
+    const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+    if (m0 >= M) return;
+    int img[2], iy[2], ix[2];
+    bool rv[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int64_t p = m0 + g + 8 * r;
+        rv[r] = p < M;
+        decode(rv[r] ? p : 0, G.h, G.w, img[r], iy[r], ix[r]);
+    }
+    float acc[CIN / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < CIN / 8; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        int64_t off[2];
+        bool ok[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int ny = iy[r] + 1 - ky, nx = ix[r] + 1 - kx;
+            const int oy = ny / G.stride, ox = nx / G.stride;
+            ok[r] = rv[r] && ny >= 0 && nx >= 0 && ny % G.stride == 0 && nx % G.stride == 0 && oy < G.oh &&
+                    ox < G.ow;
+            off[r] = ok[r] ? (((int64_t)img[r] * G.oh + oy) * G.ow + ox) * COUT : 0;
+        }
+#pragma unroll
+        for (int cb = 0; cb < COUT / 16; ++cb) {
+            uint32_t a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = q & 1, kk = cb * 16 + 2 * t + (q >> 1) * 8;
+                a[q] = ok[r] ? relu_mask2(ld_u32(dy + off[r] + kk), ld_u32(y + off[r] + kk)) : 0u;
+            }
+#pragma unroll
+            for (int nt = 0; nt < CIN / 8; ++nt) {
+                const int ci = nt * 8 + g;
+                const int co0 = cb * 16 + 2 * t;
+                const uint32_t b0 = pack2(bits16(wt + ((int64_t)co0 * 9 + tap) * CIN + ci),
+                                          bits16(wt + ((int64_t)(co0 + 1) * 9 + tap) * CIN + ci));
+                const uint32_t b1 = pack2(bits16(wt + ((int64_t)(co0 + 8) * 9 + tap) * CIN + ci),
+                                          bits16(wt + ((int64_t)(co0 + 9) * 9 + tap) * CIN + ci));
+                mma_bf16(acc[nt], a, b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < CIN / 8; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        if (rv[0]) *reinterpret_cast<uint32_t *>(dx + (m0 + g) * CIN + c) = to_bf16x2(acc[nt][0], acc[nt][1]);
+        if (rv[1]) *reinterpret_cast<uint32_t *>(dx + (m0 + g + 8) * CIN + c) = to_bf16x2(acc[nt][2], acc[nt][3]);
+    }
+}
+
+// Weight gradient: dw[co][tap][ci] += sum_p dy_pre[p][co] * x[pix(p, tap)][ci]
+// over this CTA's chunk of output pixels (M = COUT, N = 9*CIN, K = pixels).
+// Warp w takes n-tiles w, w+4, ...; the chunk's partial sums go to dw by fp32
+// atomics.  db[co] gets the bias gradient the same way.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf16 *y, const bf16 *dy, ConvGeom G,
+                                                        int chunk, float *dw, float *db) {
+    constexpr int NT = 9 * CIN / 8;            // n8 tiles over (tap, ci)
+    constexpr int NTW = (NT + 3) / 4;          // tiles per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t P = (int64_t)G.n * G.oh * G.ow;
+    const int64_t p_begin = (int64_t)blockIdx.x * chunk;
+    const int64_t p_end = (p_begin + chunk < P) ? p_begin + chunk : P;
+    float acc[COUT / 16][NTW][4];
+#pragma unroll
+    for (int mt = 0; mt < COUT / 16; ++mt)
+#pragma unroll
+        for (int j = 0; j < NTW; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[mt][j][i] = 0.f;
+    float bacc = 0.f;   // bias partial: thread (warp 0) sums channel lane for its pixels
+    for (int64_t k0 = p_begin; k0 < p_end; k0 += 16) {
+        // A fragments: rows co, columns = 16 pixels k0 .. k0+15 (dy masked by ReLU)
+        int64_t pk[4];
+        bool pv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pk[q] = k0 + 2 * t + (q & 1) + (q >> 1) * 8;   // pixels 2t, 2t+1, 2t+8, 2t+9
+            pv[q] = pk[q] < p_end;
+        }
+        uint32_t a[COUT / 16][4];
+#pragma unroll
+        for (int mt = 0; mt < COUT / 16; ++mt) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int co = mt * 16 + g + 8 * rr;
+                uint32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    v[q] = pv[q] ? relu_mask1(bits16(dy + pk[q] * COUT + co), bits16(y + pk[q] * COUT + co)) : 0u;
+                a[mt][rr] = pack2(v[0], v[1]);       // k = 2t, 2t+1
+                a[mt][2 + rr] = pack2(v[2], v[3]);   // k = 2t+8, 2t+9
+            }
+        }
+        // pixel coordinates of the 4 pixels this thread reads for B
+        int img[4], oy[4], ox[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) decode(pv[q] ? pk[q] : 0, G.oh, G.ow, img[q], oy[q], ox[q]);
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) {
+            const int nt = warp + 4 * j;
+            if (nt >= NT) break;
+            const int ncol = nt * 8 + g;             // (tap, ci) column of this thread
+            const int tap = ncol / CIN, ci = ncol - tap * CIN;
+            const int ky = tap / 3, kx = tap % 3;
+            uint32_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int iy = oy[q] * G.stride + ky - 1, ix = ox[q] * G.stride + kx - 1;
+                const bool ok = pv[q] && iy >= 0 && iy < G.h && ix >= 0 && ix < G.w;
+                v[q] = ok ? bits16(x + (((int64_t)img[q] * G.h + iy) * G.w + ix) * CIN + ci) : 0u;
+            }
+            const uint32_t b0 = pack2(v[0], v[1]), b1 = pack2(v[2], v[3]);
+#pragma unroll
+            for (int mt = 0; mt < COUT / 16; ++mt) mma_bf16(acc[mt][j], a[mt], b0, b1);
+        }
+        if (warp == 0) {   // bias: lane = channel
+            for (int q = 0; q < 16 && k0 + q < p_end; ++q) {
+                const int64_t pp = k0 + q;
+                if (lane < COUT)
+                    bacc += __uint_as_float(relu_mask1(bits16(dy + pp * COUT + lane), bits16(y + pp * COUT + lane))
+                                            << 16);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < COUT / 16; ++mt) {
+#pragma unroll
+        for (int j = 0; j < NTW; ++j) {
+            const int nt = warp + 4 * j;
+            if (nt >= NT) break;
+            const int ncol = nt * 8 + 2 * t;
+            const int co0 = mt * 16 + g;
+            // column ncol = tap * CIN + ci maps to dw[co][tap][ci] = dw[co * 9 * CIN + ncol]
+            atomicAdd(dw + (int64_t)co0 * 9 * CIN + ncol, acc[mt][j][0]);
+            atomicAdd(dw + (int64_t)co0 * 9 * CIN + ncol + 1, acc[mt][j][1]);
+            atomicAdd(dw + (int64_t)(co0 + 8) * 9 * CIN + ncol, acc[mt][j][2]);
+            atomicAdd(dw + (int64_t)(co0 + 8) * 9 * CIN + ncol + 1, acc[mt][j][3]);
+        }
+    }
+    if (warp == 0 && lane < COUT) atomicAdd(db + lane, bacc);
+}
+
+// ------------------------------------------------------------------ pool + head
+
+constexpr int kPH = 4, kPW = 8, kC4 = 32, kFeat = kPH * kPW * kC4, kOut = 44;
+
+__device__ __forceinline__ int bin_lo(int i, int n_in, int n_out) { return i * n_in / n_out; }
+__device__ __forceinline__ int bin_hi(int i, int n_in, int n_out) { return ((i + 1) * n_in + n_out - 1) / n_out; }
+
+// One CTA per sample: feat[1024] (adaptive average pool, (bin row, bin col,
+// channel) order), logits[44] = wh . feat + bh.
+__global__ void __launch_bounds__(256) pool_head_fwd_kernel(const bf16 *y4, int h4, int w4, const float *wh,
+                                                           const float *bh, float *feat, float *logits) {
+    __shared__ float f[kFeat];
+    const int s = blockIdx.x;
+    const bf16 *src = y4 + (int64_t)s * h4 * w4 * kC4;
+    for (int q = threadIdx.x; q < kFeat; q += blockDim.x) {
+        const int c = q % kC4, bin = q / kC4, bi = bin / kPW, bj = bin % kPW;
+        const int y0 = bin_lo(bi, h4, kPH), y1 = bin_hi(bi, h4, kPH);
+        const int x0 = bin_lo(bj, w4, kPW), x1 = bin_hi(bj, w4, kPW);
+        float acc = 0.f;
+        for (int yy = y0; yy < y1; ++yy)
+            for (int xx = x0; xx < x1; ++xx) acc += __bfloat162float(src[((int64_t)yy * w4 + xx) * kC4 + c]);
+        f[q] = acc / (float)((y1 - y0) * (x1 - x0));
+        feat[(int64_t)s * kFeat + q] = f[q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = warp; o < kOut; o += blockDim.x >> 5) {
+        float acc = 0.f;
+        for (int q = lane; q < kFeat; q += 32) acc += wh[o * kFeat + q] * f[q];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+        if (lane == 0) logits[(int64_t)s * kOut + o] = acc + bh[o];
+    }
+}
+
+// One CTA per sample: dfeat = wh^T dlogits, then dy4 (each conv4 output pixel
+// collects dfeat / bin area from every bin that covers it).
+__global__ void __launch_bounds__(256) pool_head_bwd_kernel(const float *dlogits, const float *wh, int h4, int w4,
+                                                           bf16 *dy4) {
+    __shared__ float df[kFeat], dl[kOut];
+    const int s = blockIdx.x;
+    if (threadIdx.x < kOut) dl[threadIdx.x] = dlogits[(int64_t)s * kOut + threadIdx.x];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kFeat; q += blockDim.x) {
+        float acc = 0.f;
+        for (int o = 0; o < kOut; ++o) acc += wh[o * kFeat + q] * dl[o];
+        const int bin = q / kC4, bi = bin / kPW, bj = bin % kPW;
+        const int area = (bin_hi(bi, h4, kPH) - bin_lo(bi, h4, kPH)) * (bin_hi(bj, w4, kPW) - bin_lo(bj, w4, kPW));
+        df[q] = acc / (float)area;
+    }
+    __syncthreads();
+    bf16 *dst = dy4 + (int64_t)s * h4 * w4 * kC4;
+    for (int q = threadIdx.x; q < h4 * w4 * kC4; q += blockDim.x) {
+        const int c = q % kC4, pix = q / kC4, yy = pix / w4, xx = pix % w4;
+        float acc = 0.f;
+        for (int bi = 0; bi < kPH; ++bi) {
+            if (yy < bin_lo(bi, h4, kPH) || yy >= bin_hi(bi, h4, kPH)) continue;
+            for (int bj = 0; bj < kPW; ++bj)
+                if (xx >= bin_lo(bj, w4, kPW) && xx < bin_hi(bj, w4, kPW)) acc += df[(bi * kPW + bj) * kC4 + c];
+        }
+        dst[q] = __float2bfloat16_rn(acc);
+    }
+}
+
+// dwh[o][q] += sum_s dlogits[s][o] * feat[s][q]; dbh[o] += sum_s dlogits[s][o].
+__global__ void __launch_bounds__(256) head_wgrad_kernel(const float *dlogits, const float *feat, int n, float *dwh,
+                                                        float *dbh) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < kOut * kFeat) {
+        const int o = idx / kFeat, q = idx % kFeat;
+        float acc = 0.f;
+        for (int s = 0; s < n; ++s) acc += dlogits[(int64_t)s * kOut + o] * feat[(int64_t)s * kFeat + q];
+        dwh[idx] += acc;
+    }
+    if (idx < kOut) {
+        float acc = 0.f;
+        for (int s = 0; s < n; ++s) acc += dlogits[(int64_t)s * kOut + idx];
+        dbh[idx] += acc;
+    }
+}
+
+// ------------------------------------------------------------------ loss, optimiser
+
+// Mean binary cross-entropy with logits over n*k outputs and its gradient.
+__global__ void __launch_bounds__(256) bce_kernel(const float *z, const float *tgt, int64_t nk, float *loss,
+                                                 float *dz) {
+    __shared__ float red[8];
+    float part = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = z[i], t = tgt[i];
+        part += fmaxf(x, 0.f) - x * t + log1pf(expf(-fabsf(x)));
+        dz[i] = (1.f / (1.f + expf(-x)) - t) / (float)nk;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s / (float)nk);
+    }
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(float *p, const float *g, float *m, float *v, int64_t count,
+                                                  float lr, float b1, float b2, float eps, float c1, float c2,
+                                                  bf16 *p16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (p16) p16[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+int blocks_for(int64_t work, int per_block, int cap = 4096) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+}  // namespace ld
+
+using namespace ld;
+
+namespace {
+ld_status launch_status(const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return LD_OK;
+    char msg[256];
+    snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    set_last_error(msg);
+    return LD_ERR_CUDA;
+}
+ld_status bad(const char *msg) {
+    set_last_error(msg);
+    return LD_ERR_INVALID;
+}
+bool shape_ok(int cin, int cout) {
+    return (cin == 1 && cout == 16) || (cin == 16 && cout == 32) || (cin == 32 && cout == 32);
+}
+}  // namespace
+
+extern "C" {
+
+ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,
+                             int32_t stride, const void *d_w, const float *d_b, void *d_y, void *stream) {
+    if (!d_x || !d_w || !d_b || !d_y || n < 1 || h < 1 || w < 1 || (stride != 1 && stride != 2) ||
+        !shape_ok(cin, cout))
+        return bad("ld_conv3x3_forward: bad argument (supported: 1->16, 16->32, 32->32; stride 1 or 2)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cin == 1) {
+        if (stride != 1) return bad("ld_conv3x3_forward: the 1-channel layer has stride 1");
+        conv1_fwd_kernel<<<blocks_for((int64_t)n * h * w, 256), 256, 0, s>>>(
+            (const uint8_t *)d_x, n, h, w, (const bf16 *)d_w, d_b, (bf16 *)d_y);
+        return launch_status("conv1_fwd");
+    }
+    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride};
+    const int64_t M = (int64_t)n * G.oh * G.ow;
+    const int grid = (int)((M + 63) / 64);
+    if (cin == 16)
+        conv_fwd_kernel<16, 32><<<grid, 128, 0, s>>>((const bf16 *)d_x, G, (const bf16 *)d_w, d_b, (bf16 *)d_y);
+    else
+        conv_fwd_kernel<32, 32><<<grid, 128, 0, s>>>((const bf16 *)d_x, G, (const bf16 *)d_w, d_b, (bf16 *)d_y);
+    return launch_status("conv_fwd");
+}
+
+ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,
+                              int32_t stride, const void *d_w, const void *d_y, const void *d_dy, void *d_dx,
+                              float *d_dw, float *d_db, void *stream) {
+    if (!d_x || !d_w || !d_y || !d_dy || !d_dw || !d_db || n < 1 || h < 1 || w < 1 ||
+        (stride != 1 && stride != 2) || !shape_ok(cin, cout))
+        return bad("ld_conv3x3_backward: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cin == 1) {
+        if (stride != 1 || d_dx) return bad("ld_conv3x3_backward: the 1-channel layer: stride 1, no dx");
+        conv1_wgrad_kernel<<<blocks_for((int64_t)n * h * w, 16 * 64, 1024), 256, 0, s>>>(
+            (const uint8_t *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy, n, h, w, d_dw, d_db);
+        return launch_status("conv1_wgrad");
+    }
+    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride};
+    const int64_t P = (int64_t)n * G.oh * G.ow;
+    const int chunk = 2048;
+    const int wgrid = (int)((P + chunk - 1) / chunk);
+    if (cin == 16)
+        conv_wgrad_kernel<16, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
+                                                        G, chunk, d_dw, d_db);
+    else
+        conv_wgrad_kernel<32, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
+                                                        G, chunk, d_dw, d_db);
+    ld_status st = launch_status("conv_wgrad");
+    if (st != LD_OK || !d_dx) return st;
+    const int64_t Mi = (int64_t)n * h * w;
+    const int dgrid = (int)((Mi + 63) / 64);
+    if (cin == 16)
+        conv_dgrad_kernel<16, 32><<<dgrid, 128, 0, s>>>((const bf16 *)d_y, (const bf16 *)d_dy, G,
+                                                        (const bf16 *)d_w, (bf16 *)d_dx);
+    else
+        conv_dgrad_kernel<32, 32><<<dgrid, 128, 0, s>>>((const bf16 *)d_y, (const bf16 *)d_dy, G,
+                                                        (const bf16 *)d_w, (bf16 *)d_dx);
+    return launch_status("conv_dgrad");
+}
+
+ld_status ld_pool_head_forward(const void *d_y4, int32_t n, int32_t h4, int32_t w4, const float *d_wh,
+                               const float *d_bh, float *d_feat, float *d_logits, void *stream) {
+    if (!d_y4 || !d_wh || !d_bh || !d_feat || !d_logits || n < 1 || h4 < kPH || w4 < kPW)
+        return bad("ld_pool_head_forward: bad argument");
+    pool_head_fwd_kernel<<<n, 256, 0, (cudaStream_t)stream>>>((const bf16 *)d_y4, h4, w4, d_wh, d_bh, d_feat,
+                                                              d_logits);
+    return launch_status("pool_head_fwd");
+}
+
+ld_status ld_pool_head_backward(const float *d_feat, const float *d_dlogits, const float *d_wh, int32_t n,
+                                int32_t h4, int32_t w4, float *d_dwh, float *d_dbh, void *d_dy4, void *stream) {
+    if (!d_feat || !d_dlogits || !d_wh || !d_dwh || !d_dbh || !d_dy4 || n < 1 || h4 < kPH || w4 < kPW)
+        return bad("ld_pool_head_backward: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    head_wgrad_kernel<<<(kOut * kFeat + 255) / 256, 256, 0, s>>>(d_dlogits, d_feat, n, d_dwh, d_dbh);
+    ld_status st = launch_status("head_wgrad");
+    if (st != LD_OK) return st;
+    pool_head_bwd_kernel<<<n, 256, 0, s>>>(d_dlogits, d_wh, h4, w4, (bf16 *)d_dy4);
+    return launch_status("pool_head_bwd");
+}
+
+ld_status ld_bce_loss(const float *d_logits, const float *d_target, int32_t n, int32_t k, float *d_loss,
+                      float *d_dlogits, void *stream) {
+    if (!d_logits || !d_target || !d_loss || !d_dlogits || n < 1 || k < 1) return bad("ld_bce_loss: bad argument");
+    const int64_t nk = (int64_t)n * k;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_loss, 0, sizeof(float), s);
+    if (e != cudaSuccess) return launch_status("ld_bce_loss memset");
+    bce_kernel<<<blocks_for(nk, 256, 256), 256, 0, s>>>(d_logits, d_target, nk, d_loss, d_dlogits);
+    return launch_status("bce");
+}
+
+ld_status ld_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v, int64_t count, float lr,
+                       float beta1, float beta2, float eps, int32_t step, void *d_param_bf16, void *stream) {
+    if (!d_param || !d_grad || !d_m || !d_v || count < 1 || step < 1) return bad("ld_adam_step: bad argument");
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    adam_kernel<<<blocks_for(count, 256), 256, 0, (cudaStream_t)stream>>>(d_param, d_grad, d_m, d_v, count, lr,
+                                                                         beta1, beta2, eps, c1, c2,
+                                                                         (bf16 *)d_param_bf16);
+    return launch_status("adam");
+}
+
+}  // extern "C"

@@ -33,6 +33,7 @@ struct SobelFrame {
     int32_t *count;
     int32_t *status_init;  // nullable: set to LD_ERR_TIMEOUT until the frame's peaks are merged
     int32_t *npeaks_init;  // nullable: set to 0 likewise
+    uint8_t *pool;         // nullable: 8x8 edge counts [ceil(h/8)][ceil(w/8)] (0..64)
     int64_t cap;
     int32_t w, h, pitch;
     int32_t tile_begin;    // first CTA of this frame

@@ -211,6 +211,34 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
         }
     }
 
+    // 8x8 edge-count pool: the CTA's tile (512 px x 8R rows) is a whole number
+    // of 8x8 blocks, so each block is counted in this CTA's shared memory and
+    // written once.  A warp's R rows lie in one 8-row block (ya is a multiple of
+    // R, R divides 8); a lane's 16 pixels are 2 blocks.
+    __shared__ uint32_t pool_s[R][kSobelTileW / 8];
+    if (F.pool != nullptr) {
+        for (int i = threadIdx.x; i < R * (kSobelTileW / 8); i += kSobelThreads) (&pool_s[0][0])[i] = 0;
+        __syncthreads();
+        if (ya < F.h && x0 < F.w) {
+            uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                c0 += __popc(masks[r] & 0xFFu);
+                c1 += __popc(masks[r] >> 8);
+            }
+            const int br = (warp * R) >> 3;
+            if (c0) atomicAdd(&pool_s[br][lane * 2], c0);
+            if (c1) atomicAdd(&pool_s[br][lane * 2 + 1], c1);
+        }
+        __syncthreads();
+        const int pw = (F.w + 7) >> 3, ph = (F.h + 7) >> 3;
+        const int bx0 = tx * (kSobelTileW / 8), by0 = (ty * R * (kSobelThreads / 32)) >> 3;
+        for (int i = threadIdx.x; i < R * (kSobelTileW / 8); i += kSobelThreads) {
+            const int br = i / (kSobelTileW / 8), bc = i % (kSobelTileW / 8);
+            if (by0 + br < ph && bx0 + bc < pw) F.pool[(size_t)(by0 + br) * pw + bx0 + bc] = (uint8_t)pool_s[br][bc];
+        }
+    }
+
     // block-wide exclusive prefix of the edge counts, one atomic per CTA
     int cnt = 0;
 #pragma unroll

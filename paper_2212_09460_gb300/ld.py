@@ -43,6 +43,19 @@ class ld_frame(ctypes.Structure):
                 ("pitch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ld_synth_stripe(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("c", ctypes.c_int64), ("tx", ctypes.c_int64),
+                ("ty", ctypes.c_int64), ("t0", ctypes.c_int64), ("dash", ctypes.c_int32), ("gap", ctypes.c_int32),
+                ("value", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ld_synth_frame(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("pitch", ctypes.c_int32), ("n_stripes", ctypes.c_int32), ("base", ctypes.c_uint64 * 3),
+                ("k_top", ctypes.c_int64), ("k_road", ctypes.c_int64), ("salt_thr", ctypes.c_uint64),
+                ("stripes", ld_synth_stripe * 4)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _SIGS = {
@@ -63,6 +76,17 @@ _SIGS = {
     "ld_autotune": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.c_int32, _P],
     "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
                     ctypes.POINTER(ctypes.c_int32)],
+    "ld_synth_frames": [_P, ctypes.c_int32, _P],
+    "ld_edge_pool_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P],
+    "ld_conv3x3_forward": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.c_int32, _P, _P, _P, _P],
+    "ld_conv3x3_backward": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                            ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P],
+    "ld_pool_head_forward": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P],
+    "ld_pool_head_backward": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P],
+    "ld_bce_loss": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P],
+    "ld_adam_step": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                     ctypes.c_float, ctypes.c_int32, _P, _P],
     "ld_ctx_enable_timing": [_P, ctypes.c_int],
     "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
 }
@@ -194,6 +218,71 @@ def ld_ctx_stage_ms(ctx: int) -> tuple[float, float, int]:
     return ms[0], ms[1], int(ms[2])
 
 
+def ld_synth_frames(d_descs, n, stream) -> None:
+    _check(load().ld_synth_frames(d_descs, n, stream))
+
+
+def synth_descriptors(specs, bufs):
+    """ld_synth_frame array (host bytes) for (seed, w, h, style) specs and their
+    uint8 [h][pitch] device buffers."""
+    from . import synth
+    arr = (ld_synth_frame * len(specs))()
+    for i, ((seed, w, h, style), buf) in enumerate(zip(specs, bufs)):
+        fp = synth.frame_params(seed, w, h, style)
+        d = arr[i]
+        d.img, d.w, d.h, d.pitch = buf.data_ptr(), w, h, buf.stride(0)
+        d.n_stripes = len(fp["stripes"])
+        for k in range(3):
+            d.base[k] = fp["base"][k]
+        d.k_top, d.k_road, d.salt_thr = fp["k_top"], fp["k_road"], fp["salt_thr"]
+        for k, st in enumerate(fp["stripes"]):
+            s = d.stripes[k]
+            s.nx, s.ny, s.c, s.tx, s.ty, s.t0 = st.nx, st.ny, st.c, st.tx, st.ty, st.t0
+            s.dash, s.gap, s.value, s.reserved = st.dash, st.gap, st.value, 0
+    return arr
+
+
+def synth_frames_device(specs, device, stream=None):
+    """Generate frames on the device: list of uint8 [h][pitch] tensors (pitch = w
+    rounded up to 16), byte-identical to synth.road_frame for each spec."""
+    torch = _torch()
+    bufs = [torch.empty((h, (w + 15) // 16 * 16), dtype=torch.uint8, device=device) for _, w, h, _ in specs]
+    arr = synth_descriptors(specs, bufs)
+    raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
+    ld_synth_frames(raw.data_ptr(), len(specs), _stream_handle(stream))
+    return bufs, raw   # keep `raw` (the descriptors) alive until the kernel has run
+
+
+def ld_edge_pool_batch(ctx, frames, p, d_pool, stream) -> None:
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_edge_pool_batch(ctx, arr, len(arr), ctypes.byref(p), d_pool, stream))
+
+
+def ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream) -> None:
+    _check(load().ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream))
+
+
+def ld_conv3x3_backward(d_x, n, h, w, cin, cout, stride, d_w, d_y, d_dy, d_dx, d_dw, d_db, stream) -> None:
+    _check(load().ld_conv3x3_backward(d_x, n, h, w, cin, cout, stride, d_w, d_y, d_dy, d_dx, d_dw, d_db, stream))
+
+
+def ld_pool_head_forward(d_y4, n, h4, w4, d_wh, d_bh, d_feat, d_logits, stream) -> None:
+    _check(load().ld_pool_head_forward(d_y4, n, h4, w4, d_wh, d_bh, d_feat, d_logits, stream))
+
+
+def ld_pool_head_backward(d_feat, d_dlogits, d_wh, n, h4, w4, d_dwh, d_dbh, d_dy4, stream) -> None:
+    _check(load().ld_pool_head_backward(d_feat, d_dlogits, d_wh, n, h4, w4, d_dwh, d_dbh, d_dy4, stream))
+
+
+def ld_bce_loss(d_logits, d_target, n, k, d_loss, d_dlogits, stream) -> None:
+    _check(load().ld_bce_loss(d_logits, d_target, n, k, d_loss, d_dlogits, stream))
+
+
+def ld_adam_step(d_param, d_grad, d_m, d_v, count, lr, beta1, beta2, eps, step, d_param_bf16, stream) -> None:
+    _check(load().ld_adam_step(d_param, d_grad, d_m, d_v, count, lr, beta1, beta2, eps, step, d_param_bf16,
+                               stream))
+
+
 def ld_last_error() -> str:
     return load().ld_last_error().decode()
 
@@ -312,6 +401,16 @@ class Context:
     def prepare(self, frames, widths=None) -> "PreparedBatch":
         """Build the frame descriptors once, for repeated detect_batch calls on the same tensors."""
         return PreparedBatch(_frames_array(self._descs(frames, widths)), frames[0].device)
+
+    def edge_pool(self, frames, p: ld_params, widths=None, out=None, stream=None):
+        """8x8 OR-pooled edge maps of equal-size frames: uint8 [n][ceil(h/8)][ceil(w/8)]."""
+        torch = _torch()
+        descs = self._descs(frames, widths)
+        w, h = descs[0][1], descs[0][2]
+        if out is None:
+            out = torch.empty((len(descs), (h + 7) // 8, (w + 7) // 8), dtype=torch.uint8, device=frames[0].device)
+        ld_edge_pool_batch(self.handle, descs, p, out.data_ptr(), _stream_handle(stream))
+        return out
 
     def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
         """Steps 1-4 on a list of uint8 CUDA tensors (or a PreparedBatch);

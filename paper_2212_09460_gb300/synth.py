@@ -182,6 +182,19 @@ def road_frame(seed: int, w: int, h: int, style: FrameStyle = LATENCY_640x480) -
     return v.astype(np.uint8)
 
 
+def frame_params(seed: int, w: int, h: int, style: FrameStyle = LATENCY_640x480) -> dict:
+    """The integer parameters road_frame draws for a frame, for a device-side
+    generator that reproduces it: stream bases, Q32 noise scales, salt
+    threshold and stripe geometry."""
+    return {
+        "base": [int(_stream_base(seed, s)) for s in (1, 2, 3)],
+        "k_top": int(round(style.sigma / _IH8_STD * 2.0 ** 32)),
+        "k_road": int(round(style.sigma_road / _IH8_STD * 2.0 ** 32)),
+        "salt_thr": int(style.salt * 2.0 ** 32) if style.salt > 0 else 0,
+        "stripes": frame_stripes(seed, w, h, style),
+    }
+
+
 def pitched(frame: np.ndarray, pitch: int | None = None, fill: int | None = None,
             seed: int = 0) -> np.ndarray:
     """Copy a [h][w] frame into a [h][pitch] buffer (pitch a multiple of 16).
