@@ -82,6 +82,7 @@ struct ld_ctx {
     std::map<int, int32_t *> trig;        // n_theta -> device Q16 table
     std::map<int, std::vector<int32_t>> trig_host;
     DevBuf edges, small, cand;            // detect_batch / hough_peaks scratch
+    DevBuf prop;                          // proposal path: edge-count maps, activations, pair lists
     std::vector<cudaEvent_t> ev;   // 3 events per timed call, reused in order
     int timed_calls = 0;           // timed calls since the last ld_ctx_stage_ms
     bool timing = false;
@@ -323,6 +324,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->edges.release();
         ctx->small.release();
         ctx->cand.release();
+        ctx->prop.release();
     }
     delete ctx;
     return LD_OK;
@@ -795,6 +797,174 @@ ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, c
         }
         e = launch_sobel(SL, ctas, s);
         if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+    }
+    return LD_OK;
+}
+
+ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                                   const ld_proposal_net *net, const ld_proposal_params *prp, ld_peak *d_peaks,
+                                   int32_t *d_n_peaks, int32_t *d_status, int32_t *d_fallback,
+                                   int32_t *d_active_pairs, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (p.n_theta % 36 != 0) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: n_theta must be a multiple of 36");
+    ld_proposal_params q = prp ? *prp : ld_proposal_params{0.5f, 0.9f, 2, 0};
+    if (q.reserved != 0 || q.margin < 0 || !(q.p_band >= 0.f && q.p_band <= 1.f) ||
+        !(q.p_fallback >= 0.f && q.p_fallback <= 1.f))
+        return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: bad proposal parameters");
+    if (!h_frames || n < 1 || n > kMaxLaunchFrames)
+        return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: need 1 <= n <= %d frames", kMaxLaunchFrames);
+    if (!d_peaks || !d_n_peaks || !d_status) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: NULL output");
+    if (!net || !net->wh || !net->bh) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: NULL network");
+    for (int i = 0; i < 4; ++i)
+        if (!net->w[i] || !net->b[i]) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: NULL network layer");
+    const int w = h_frames[0].w, h = h_frames[0].h;
+    for (int i = 0; i < n; ++i)
+        if (h_frames[i].w != w || h_frames[i].h != h)
+            return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: frames must share one size");
+    const int ph = (h + 7) / 8, pw = (w + 7) / 8;
+    int hs[5] = {ph, ph, 0, 0, 0}, ws[5] = {pw, pw, 0, 0, 0};
+    for (int l = 2; l <= 4; ++l) {
+        hs[l] = (hs[l - 1] - 1) / 2 + 1;
+        ws[l] = (ws[l - 1] - 1) / 2 + 1;
+    }
+    if (hs[4] < 4 || ws[4] < 8) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: frame %dx%d too small", w, h);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        const ld_frame &f = h_frames[i];
+        st = check_size(f.w, f.h, p, ht);
+        if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
+        if (!f.img || f.pitch < f.w || (f.pitch & 15) || !aligned16(f.img) || f.reserved != 0)
+            return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
+    }
+    const int M = cand_m(p);
+    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta);
+    const int n_pairs = p.n_theta / 2;
+    const int64_t epf = ((int64_t)w * h + 3) / 4 * 4;
+    if (!ctx->edges.ensure((size_t)(n * epf) * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
+    if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
+    if (!ctx->cand.ensure((size_t)n * hp.n_tiles * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    // proposal scratch, carved in 256-byte aligned pieces
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_pool = carve((size_t)n * ph * pw);
+    const size_t o_y1 = carve((size_t)n * hs[1] * ws[1] * 16 * 2);
+    const size_t o_y2 = carve((size_t)n * hs[2] * ws[2] * 32 * 2);
+    const size_t o_y3 = carve((size_t)n * hs[3] * ws[3] * 32 * 2);
+    const size_t o_y4 = carve((size_t)n * hs[4] * ws[4] * 32 * 2);
+    const size_t o_feat = carve((size_t)n * 1024 * 4);
+    const size_t o_logit = carve((size_t)n * 44 * 4);
+    const size_t o_list = carve((size_t)n * n_pairs * 4);
+    const size_t o_cnt = carve((size_t)n * 4);
+    const size_t o_fb = carve((size_t)n * 4);
+    const size_t o_tiles = carve((size_t)n * 4);
+    const size_t o_ub = carve((size_t)(n + 1) * 4);
+    if (!ctx->prop.ensure(off)) return fail(LD_ERR_NOMEM, "scratch proposal");
+    uint8_t *pb = (uint8_t *)ctx->prop.p;
+    uint8_t *pool = pb + o_pool;
+    void *y[5] = {nullptr, pb + o_y1, pb + o_y2, pb + o_y3, pb + o_y4};
+    float *feat = (float *)(pb + o_feat), *logits = (float *)(pb + o_logit);
+    int32_t *plist = (int32_t *)(pb + o_list), *pcnt = (int32_t *)(pb + o_cnt);
+    int32_t *fb = d_fallback ? d_fallback : (int32_t *)(pb + o_fb);
+    int32_t *tiles = (int32_t *)(pb + o_tiles), *ub = (int32_t *)(pb + o_ub);
+    uint32_t *edges = (uint32_t *)ctx->edges.p;
+    const Small sm = small_of(ctx->small.p);
+    uint64_t *cand = (uint64_t *)ctx->cand.p;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    cudaError_t e = cudaMemsetAsync(sm.counts, 0, kSmallInts * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
+    // Steps 1-2 with the edge-count map
+    SobelLaunch SL;
+    std::memset(&SL, 0, sizeof SL);
+    SL.n = n;
+    SL.threshold = p.threshold;
+    SL.border = p.border;
+    const int tx = (w + kSobelTileW - 1) / kSobelTileW;
+    SL.rows_per_warp = rows_for(ctx, h_frames, 0, n, p.n_theta, (int64_t)n * tx * ((h + 15) / 16));
+    const int rows_cta = SL.rows_per_warp * (kSobelThreads / 32);
+    const int per_frame_ctas = tx * ((h + rows_cta - 1) / rows_cta);
+    for (int i = 0; i < n; ++i) {
+        SobelFrame &F = SL.f[i];
+        F.img = h_frames[i].img;
+        F.edges = edges + i * epf;
+        F.count = sm.counts + i;
+        F.status_init = d_status + i;
+        F.npeaks_init = d_n_peaks + i;
+        F.pool = pool + (size_t)i * ph * pw;
+        F.cap = (int64_t)w * h;
+        F.w = w;
+        F.h = h;
+        F.pitch = h_frames[i].pitch;
+        F.tile_begin = i * per_frame_ctas;
+        F.tiles_x = tx;
+    }
+    e = launch_sobel(SL, n * per_frame_ctas, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+    // the network
+    static const int cin[4] = {1, 16, 32, 32}, cout[4] = {16, 32, 32, 32}, stride[4] = {1, 2, 2, 2};
+    const void *x = pool;
+    for (int l = 0; l < 4; ++l) {
+        st = ld_conv3x3_forward(x, n, hs[l], ws[l], cin[l], cout[l], stride[l], net->w[l], net->b[l], y[l + 1], s);
+        if (st != LD_OK) return st;
+        x = y[l + 1];
+    }
+    st = ld_pool_head_forward(y[4], n, hs[4], ws[4], net->wh, net->bh, feat, logits, s);
+    if (st != LD_OK) return st;
+    // bands -> active pairs -> work units
+    e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, plist, pcnt, fb, tiles,
+                            ub, s);
+    if (e != cudaSuccess) return cuda_fail(e, "band selection");
+    // Steps 3-4 on the kept pairs
+    HoughLaunch HL;
+    std::memset(&HL, 0, sizeof HL);
+    HL.n = n;
+    HL.n_theta = p.n_theta;
+    HL.mode = kHoughCandidates;
+    HL.cand_m = M;
+    HL.min_votes = p.min_votes;
+    HL.top_k = p.top_k;
+    HL.nms_theta = p.nms_theta;
+    HL.nms_rho = p.nms_rho;
+    HL.trig = dt;
+    HL.queue = sm.queue;
+    HL.unit_begin_dev = ub;
+    for (int i = 0; i < n; ++i) {
+        HoughFrame &HF = HL.f[i];
+        HF.edges = edges + i * epf;
+        HF.count = sm.counts + i;
+        HF.cap = (int64_t)w * h;
+        HF.cand = cand + (size_t)i * hp.n_tiles * M;
+        HF.flags = sm.flags + i;
+        HF.done = sm.done + i;
+        HF.peaks = d_peaks + (size_t)i * p.top_k;
+        HF.n_peaks = d_n_peaks + i;
+        HF.status = d_status + i;
+        HF.pair_list = plist + (size_t)i * n_pairs;
+        HF.pair_count = pcnt + i;
+        HF.w = w;
+        HF.h = h;
+        HF.D = hp.D;
+        HF.n_rho = hp.n_rho;
+        HF.n_splits = 1;
+        HF.pairs_per_tile = hp.pairs;
+        HF.n_tiles = hp.n_tiles;
+    }
+    const int max_units = n * hp.n_tiles;
+    e = launch_hough(HL, max_units < ctx->num_sms ? max_units : ctx->num_sms, hp.pairs,
+                     (int64_t)hp.pairs * hp.n_rho, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+    if (d_active_pairs) {
+        e = cudaMemcpyAsync(d_active_pairs, pcnt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "active pairs copy");
     }
     return LD_OK;
 }

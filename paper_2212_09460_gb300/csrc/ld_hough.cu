@@ -79,16 +79,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-// theta of the low / high half of pair slot p of a tile starting at pair j0.
-__device__ __forceinline__ int theta_lo(int j0, int p) { return j0 + p; }
-__device__ __forceinline__ int theta_hi(int j0, int p, int n_theta) {
-    int j = j0 + p;
+// theta of the low / high half of pair slot p (tj: the tile's pair indices).
+__device__ __forceinline__ int theta_lo(const int *tj, int p) { return tj[p]; }
+__device__ __forceinline__ int theta_hi(const int *tj, int p, int n_theta) {
+    const int j = tj[p];
     return j == 0 ? n_theta / 2 : n_theta - j;
 }
 
 // Ordered column q of a tile (theta ascending) -> (slot, half).
-// Low halves carry theta j0..j0+np-1 (< n/2), high halves theta > n/2 except
-// slot 0 of the first tile, whose high half is theta = n/2.
+// The tile's pair indices ascend, so low halves carry ascending theta < n/2
+// and high halves theta > n/2 descending in the slot, except pair 0, whose
+// high half is theta = n/2.
 __device__ __forceinline__ void ordered_col(int q, int np, bool has0, int &slot, int &half) {
     if (q < np) { slot = q; half = 0; return; }
     int q2 = q - np;
@@ -147,13 +148,21 @@ __device__ __forceinline__ void vote_chunk(const uint32_t *buf, const uint32_t *
 // wait gave up (the frame is flagged; the CTA must stop).
 template <int PMAX>
 __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFrame &F, int local, uint32_t &seq,
-                                           uint8_t *smem_raw, uint64_t *bars, SelectSmem &S, int &abort_flag) {
+                                           uint8_t *smem_raw, uint64_t *bars, SelectSmem &S, int &abort_flag,
+                                           int *tj) {
     const int ns = F.n_splits;
     const int tile = local / ns, split = local % ns;
     const int n_theta = L.n_theta;
     const int j0 = tile * F.pairs_per_tile;
-    const int np = min(F.pairs_per_tile, n_theta / 2 - j0);
-    const bool has0 = (j0 == 0);
+    // pairs of this tile: contiguous j0.., or the next entries of the
+    // frame's active-pair list (restricted vote)
+    const int n_avail = F.pair_list ? *F.pair_count : n_theta / 2;
+    const int np = min(F.pairs_per_tile, n_avail - j0);
+    if (threadIdx.x < PMAX) tj[threadIdx.x] = (threadIdx.x < np) ? (F.pair_list ? F.pair_list[j0 + threadIdx.x]
+                                                                                 : j0 + (int)threadIdx.x)
+                                                                  : 0;
+    __syncthreads();
+    const bool has0 = (tj[0] == 0);
     const int n_rho = F.n_rho;
     const uint32_t W = (uint32_t)F.w, H = (uint32_t)F.h;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -168,8 +177,8 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
     for (int p = 0; p < PMAX; ++p) {
         cq[p] = 0; sq[p] = 0; kq[p] = 0;
         if (p < np) {
-            cq[p] = (uint32_t)L.trig[2 * (j0 + p)];
-            sq[p] = (uint32_t)L.trig[2 * (j0 + p) + 1];
+            cq[p] = (uint32_t)L.trig[2 * tj[p]];
+            sq[p] = (uint32_t)L.trig[2 * tj[p] + 1];
             kq[p] = 32768u + ((uint32_t)F.D + (uint32_t)(p * n_rho)) * 65536u;
         }
     }
@@ -248,7 +257,7 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
 
     if (L.mode == kHoughFullAcc) {
         for (int p = 0; p < np; ++p) {
-            const int ta = theta_lo(j0, p), tb = theta_hi(j0, p, n_theta);
+            const int ta = theta_lo(tj, p), tb = theta_hi(tj, p, n_theta);
             int32_t *ga = F.acc + (size_t)ta * n_rho;
             int32_t *gb = F.acc + (size_t)tb * n_rho;
             for (int r = tid; r < n_rho; r += kHoughThreads) {
@@ -313,11 +322,11 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
                     const int p = i / n_rho, r = i - p * n_rho;
                     if (a >= Lth) {
                         const int slot = atomicAdd(&S.surv, 1);
-                        if (slot < kMaxSurv) keys[slot] = peak_key(a, theta_lo(j0, p), r);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(a, theta_lo(tj, p), r);
                     }
                     if (b >= Lth) {
                         const int slot = atomicAdd(&S.surv, 1);
-                        if (slot < kMaxSurv) keys[slot] = peak_key(b, theta_hi(j0, p, n_theta), r);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(b, theta_hi(tj, p, n_theta), r);
                     }
                 }
             }
@@ -380,7 +389,7 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
         rho = (int)(li - (int64_t)q * n_rho);
         int slot, half;
         ordered_col(q, np, has0, slot, half);
-        theta = half ? theta_hi(j0, slot, n_theta) : theta_lo(j0, slot);
+        theta = half ? theta_hi(tj, slot, n_theta) : theta_lo(tj, slot);
         const uint32_t wv = acc[slot * n_rho + rho];
         return (int32_t)(half ? (wv >> 16) : (wv & 0xFFFFu));
     };
@@ -436,7 +445,9 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     __shared__ SelectSmem S;
     __shared__ MergeSmem MS;
     __shared__ int abort_flag, unit_s, last_s;
+    __shared__ int tile_j[PMAX];
     const int tid = threadIdx.x;
+    const int total_units = L.unit_begin_dev ? L.unit_begin_dev[L.n] : L.total_units;
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
@@ -448,25 +459,28 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
         if (tid == 0) unit_s = atomicAdd(L.queue, 1);
         __syncthreads();
         const int u = unit_s;
-        if (u >= L.total_units) break;   // block-uniform
+        if (u >= total_units) break;   // block-uniform
+        const int32_t *ub = L.unit_begin_dev;
         int lo = 0, hi = L.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (L.f[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+            if ((ub ? ub[mid] : L.f[mid].unit_begin) <= u) lo = mid; else hi = mid - 1;
         }
         const HoughFrame &F = L.f[lo];
-        if (!hough_unit<PMAX>(L, F, u - F.unit_begin, seq, smem_raw, bars, S, abort_flag)) break;
+        const int begin = ub ? ub[lo] : F.unit_begin;
+        const int n_tiles = ub ? ub[lo + 1] - ub[lo] : F.n_tiles;
+        if (!hough_unit<PMAX>(L, F, u - begin, seq, smem_raw, bars, S, abort_flag, tile_j)) break;
         if (L.mode == kHoughCandidates) {
             __syncthreads();   // this tile's candidates are written
             if (tid == 0) {
                 __threadfence();
-                last_s = (atomicAdd(F.done, 1) == F.n_tiles - 1) ? 1 : 0;
+                last_s = (atomicAdd(F.done, 1) == n_tiles - 1) ? 1 : 0;
             }
             __syncthreads();
             if (last_s) {   // block-uniform
                 __threadfence();
                 const int32_t fl = F.flags ? __ldcg(F.flags) : 0;
-                block_merge(F.cand, (int64_t)F.n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
+                block_merge(F.cand, (int64_t)n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
                             F.n_peaks, F.status, fl, MS);
             }
         }

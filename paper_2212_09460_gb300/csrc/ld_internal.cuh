@@ -74,6 +74,8 @@ struct HoughFrame {
     ld_peak *peaks;        // candidate mode: merged peaks [top_k]
     int32_t *n_peaks;
     int32_t *status;       // nullable
+    const int32_t *pair_list;   // nullable: restricted vote, ascending active pair indices (device)
+    const int32_t *pair_count;  // with pair_list: number of active pairs (device)
     int32_t w, h, D, n_rho;
     int32_t unit_begin;    // first work unit of this frame
     int32_t n_splits;      // units sharing one theta tile (edge ranges)
@@ -91,6 +93,7 @@ struct HoughLaunch {
     int32_t top_k, nms_theta, nms_rho;   // candidate mode: the merge
     int32_t pad_;
     int32_t *queue;        // work-queue head (zeroed before the launch)
+    const int32_t *unit_begin_dev;   // nullable: device [n + 1] unit offsets (restricted vote)
     const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
     HoughFrame f[kMaxLaunchFrames];
 };
@@ -160,6 +163,12 @@ int hough_max_pairs(int n_rho);
 #define LD_HOUGH_PAIR_SIZES(X) X(2) X(3) X(4) X(5) X(6) X(8) X(9) X(10) X(12) X(15) X(16) X(18) X(20) X(24) X(30)
 // Smallest compiled tile size >= pairs (0 if none).
 int hough_template_pairs(int pairs);
+
+// Proposal: band logits -> per-frame ascending active-pair lists, counts,
+// fallback flags, tile counts and the device prefix unit_begin [n + 1].
+cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p_band, float p_fallback, int margin,
+                                int pairs_per_tile, int32_t *pair_list, int32_t *pair_count, int32_t *fallback,
+                                int32_t *tiles, int32_t *unit_begin, cudaStream_t s);
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);

@@ -56,6 +56,16 @@ class ld_synth_frame(ctypes.Structure):
                 ("stripes", ld_synth_stripe * 4)]
 
 
+class ld_proposal_net(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p * 4), ("b", ctypes.c_void_p * 4), ("wh", ctypes.c_void_p),
+                ("bh", ctypes.c_void_p)]
+
+
+class ld_proposal_params(ctypes.Structure):
+    _fields_ = [("p_band", ctypes.c_float), ("p_fallback", ctypes.c_float), ("margin", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _SIGS = {
@@ -77,6 +87,11 @@ _SIGS = {
     "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
                     ctypes.POINTER(ctypes.c_int32)],
     "ld_synth_frames": [_P, ctypes.c_int32, _P],
+    "ld_proposal_targets": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                            _P, _P],
+    "ld_detect_batch_proposal": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
+                                 ctypes.POINTER(ld_proposal_net), ctypes.POINTER(ld_proposal_params), _P, _P, _P, _P,
+                                 _P, _P],
     "ld_edge_pool_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P],
     "ld_conv3x3_forward": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                            ctypes.c_int32, _P, _P, _P, _P],
@@ -258,6 +273,23 @@ def ld_edge_pool_batch(ctx, frames, p, d_pool, stream) -> None:
     _check(load().ld_edge_pool_batch(ctx, arr, len(arr), ctypes.byref(p), d_pool, stream))
 
 
+def ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, d_targets, stream) -> None:
+    _check(load().ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, d_targets, stream))
+
+
+def proposal_params(p_band=0.5, p_fallback=0.9, margin=2) -> ld_proposal_params:
+    q = ld_proposal_params()
+    q.p_band, q.p_fallback, q.margin, q.reserved = p_band, p_fallback, margin, 0
+    return q
+
+
+def ld_detect_batch_proposal(ctx, frames, p, net, q, d_peaks, d_n_peaks, d_status, d_fallback, d_active,
+                             stream) -> None:
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_batch_proposal(ctx, arr, len(arr), ctypes.byref(p), ctypes.byref(net), ctypes.byref(q),
+                                           d_peaks, d_n_peaks, d_status, d_fallback, d_active, stream))
+
+
 def ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream) -> None:
     _check(load().ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream))
 
@@ -401,6 +433,24 @@ class Context:
     def prepare(self, frames, widths=None) -> "PreparedBatch":
         """Build the frame descriptors once, for repeated detect_batch calls on the same tensors."""
         return PreparedBatch(_frames_array(self._descs(frames, widths)), frames[0].device)
+
+    def detect_batch_proposal(self, frames, p: ld_params, net, q: ld_proposal_params | None = None, widths=None,
+                              out=None, stream=None):
+        """Steps 1-4 with the learned proposal (net: a ProposalNet); returns
+        (peaks [n][top_k][3], n_peaks [n], status [n], fallback [n], active_pairs [n])."""
+        torch = _torch()
+        if isinstance(frames, PreparedBatch):
+            descs, dev = frames.array, frames.device
+        else:
+            descs, dev = self._descs(frames, widths), frames[0].device
+        n = len(descs)
+        if out is None:
+            out = (torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev),) + tuple(
+                torch.zeros(n, dtype=torch.int32, device=dev) for _ in range(4))
+        pk, npk, st, fb, act = out
+        ld_detect_batch_proposal(self.handle, descs, p, net.c_struct(), q or proposal_params(), pk.data_ptr(),
+                                 npk.data_ptr(), st.data_ptr(), fb.data_ptr(), act.data_ptr(), _stream_handle(stream))
+        return out
 
     def edge_pool(self, frames, p: ld_params, widths=None, out=None, stream=None):
         """8x8 OR-pooled edge maps of equal-size frames: uint8 [n][ceil(h/8)][ceil(w/8)]."""

@@ -3,7 +3,7 @@ Adam, checkpoints.  Every computation runs in libld.so's kernels; this module
 only owns the device buffers and orders the calls.
 
 The paper has no learned stage.  The network predicts, from the 8x8
-OR-pooled edge map of a frame, which 5-degree theta bands hold the frame's
+edge-count map of a frame (edge pixels per block), which 5-degree theta bands hold the frame's
 top Hough peaks (36 logits) and which of 8 row bands their lines cross
 (8 logits).  Voting restricted to the predicted bands finds exactly the
 peaks of the full vote whenever the bands contain them (ld_detect_batch_
@@ -80,12 +80,21 @@ class ProposalNet:
         net.step_count = int(z["step"])
         return net
 
+    def c_struct(self) -> "ld.ld_proposal_net":
+        """Device pointers of the current weights, for ld_detect_batch_proposal."""
+        s = ld.ld_proposal_net()
+        for i in range(4):
+            s.w[i] = self.w16[f"w{i}"].data_ptr()
+            s.b[i] = self.p[f"b{i}"].data_ptr()
+        s.wh, s.bh = self.p["wh"].data_ptr(), self.p["bh"].data_ptr()
+        return s
+
     # ---------------------------------------------------------------- passes
     def _stream(self):
         return self.torch.cuda.current_stream(self.device).cuda_stream
 
     def forward(self, pool) -> Acts:
-        """pool: uint8 [n][h][w] (0/1) on the device -> activations and logits [n][44]."""
+        """pool: uint8 [n][h][w] edge counts (0..64) on the device -> activations and logits [n][44]."""
         torch = self.torch
         n, h, w = pool.shape
         s = self._stream()

@@ -1,0 +1,93 @@
+"""The proposal path (ld_detect_batch_proposal) is exact where it votes.
+
+With forced band probabilities (head weights 0, biases +-20), the kept theta
+pairs are known; the peaks must equal the oracle's greedy over the full
+accumulator with every other theta row removed.  With the fallback forced,
+the path must equal the plain ld_detect_batch.  Also: the training targets
+kernel against the oracle's definition."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.cnn as cnn
+from paper_2212_09460_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+W, H, NT = 1920, 1080, 360
+
+
+def _frames(seeds):
+    raw = [synth.road_frame(s, W, H, synth.THROUGHPUT_1080P) for s in seeds]
+    return raw, [torch.from_numpy(r).cuda() for r in raw]
+
+
+def _forced_net(bands):
+    from paper_2212_09460_gb300.proposal import ProposalNet, init_numpy
+    p = init_numpy(0)
+    p["wh"][:] = 0.0
+    p["bh"][:] = -20.0
+    p["bh"][list(bands)] = 20.0
+    return ProposalNet(p, 0)
+
+
+def _voted_rows(bands, margin, n_theta=NT):
+    bpb = n_theta // 36
+    on = np.zeros(n_theta, bool)
+    for b in bands:
+        on[max(0, b * bpb - margin): min(n_theta, (b + 1) * bpb + margin)] = True
+    pairs = [j for j in range(n_theta // 2) if (on[0] or on[n_theta // 2]) if j == 0] + \
+            [j for j in range(1, n_theta // 2) if on[j] or on[n_theta - j]]
+    rows = np.zeros(n_theta, bool)
+    for j in pairs:
+        rows[j] = True
+        rows[n_theta // 2 if j == 0 else n_theta - j] = True
+    return rows, len(pairs)
+
+
+@pytest.mark.parametrize("bands,margin", [([27, 10], 2), ([0, 18, 35], 0), ([5], 4)])
+def test_restricted_vote_matches_masked_oracle(ctx, ldlib, ora, bands, margin):
+    raw, dev = _frames([4000, 4001, 4002])
+    p = ldlib.params(n_theta=NT, top_k=4, border=1)
+    net = _forced_net(bands)
+    q = ldlib.proposal_params(0.5, 0.9, margin)
+    pk, npk, st, fb, act = (t.cpu().numpy() for t in ctx.detect_batch_proposal(dev, p, net, q))
+    rows, n_pairs = _voted_rows(bands, margin)
+    for i, r in enumerate(raw):
+        e = ora.edge_list(ora.binarize(ora.sobel_mag(r, border=1), 128))
+        acc = ora.hough(e, W, H, NT)
+        acc[~rows] = 0
+        ref = ora.peaks(acc, 4)
+        assert st[i] == 0 and fb[i] == 0 and act[i] == n_pairs
+        assert npk[i] == len(ref)
+        np.testing.assert_array_equal(pk[i, : npk[i]], ref)
+
+
+def test_fallback_equals_plain_path(ctx, ldlib, ora):
+    raw, dev = _frames([4100, 4101])
+    p = ldlib.params(n_theta=NT, top_k=4, border=1)
+    net = _forced_net([])                      # every band at sigmoid(-20): falls back
+    pk, npk, st, fb, act = (t.cpu().numpy() for t in ctx.detect_batch_proposal(dev, p, net))
+    plain = ctx.detect_batch(dev, p)
+    torch.cuda.synchronize()
+    ppk, pn, pst = (t.cpu().numpy() for t in plain)
+    assert (fb == 1).all() and (act == NT // 2).all() and (st == 0).all()
+    np.testing.assert_array_equal(npk, pn)
+    np.testing.assert_array_equal(pk, ppk)
+    ref = ora.detect(raw[0], NT, 4, border=1)
+    np.testing.assert_array_equal(pk[0, : npk[0]], ref)
+
+
+def test_targets_kernel_matches_oracle(ctx, ldlib):
+    raw, dev = _frames([4200, 4201, 4202, 4203])
+    p = ldlib.params(n_theta=NT, top_k=4, border=1)
+    pk, npk, st = ctx.detect_batch(dev, p)
+    tgt = torch.empty((4, 44), dtype=torch.float32, device="cuda")
+    ldlib.ld_proposal_targets(pk.data_ptr(), npk.data_ptr(), 4, 4, W, H, NT, tgt.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    pkc, nc, tg = pk.cpu().numpy(), npk.cpu().numpy(), tgt.cpu().numpy()
+    for i in range(4):
+        peaks = pkc[i, : nc[i]]
+        np.testing.assert_array_equal(tg[i, :36], cnn.theta_band_targets(peaks, NT))
+        np.testing.assert_array_equal(tg[i, 36:], cnn.row_band_targets(peaks, W, H, NT))
