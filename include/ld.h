@@ -290,12 +290,15 @@ LD_API ld_status ld_adam_step(float *d_param, const float *d_grad, float *d_m, f
                               int32_t step, void *d_param_bf16, void *stream);
 
 /* Training targets [n][44] for the network from a batch's peaks (as written
- * by ld_detect_batch, top_k per frame): 1 for the 5-degree theta band of each
- * peak (n_theta a multiple of 36), and 1 for each of the 8 row bands (h/8
- * rows each) that holds a row where the peak's line crosses the w x h frame. */
+ * by ld_detect_batch, top_k per frame).  A peak counts if it is among the
+ * first always_k or has at least rel_votes times the first peak's votes.
+ * Targets: 1 for the 5-degree theta band of each counted peak (n_theta a
+ * multiple of 36), and 1 for each of the 8 row bands (h/8 rows each) holding
+ * a row where a counted peak's line crosses the w x h frame. */
 LD_API ld_status ld_proposal_targets(const ld_peak *d_peaks, const int32_t *d_n_peaks,
                                      int32_t n, int32_t top_k, int32_t w, int32_t h,
-                                     int32_t n_theta, float *d_targets, void *stream);
+                                     int32_t n_theta, int32_t always_k, float rel_votes,
+                                     float *d_targets, void *stream);
 
 /* Device pointers of a trained network (layouts as above). */
 typedef struct {
@@ -306,8 +309,8 @@ typedef struct {
 } ld_proposal_net;
 
 typedef struct {
-    float p_band;           /* vote a band if sigmoid(logit) >= p_band              [0.5] */
-    float p_fallback;       /* full vote if every band's probability < p_fallback  [0.9] */
+    float p_band;           /* vote a band if sigmoid(logit) >= p_band              [0.05] */
+    float p_fallback;       /* full vote if every band's probability < p_fallback  [0.5]  */
     int32_t margin;         /* extra theta bins voted on each side of a kept band  [2]   */
     int32_t reserved;       /* must be 0 */
 } ld_proposal_params;
@@ -322,8 +325,9 @@ typedef struct {
  * kept bins can only precede a full-vote peak in the order if an earlier pick
  * suppresses it).  Outputs as ld_detect_batch, plus per frame: d_fallback[f]
  * = 1 if the full vote ran, d_active_pairs[f] = theta pairs voted (both
- * nullable).  p->n_theta must be a multiple of 36; the frame size must leave
- * conv4 at least 4 x 8 (about w >= 450, h >= 200).
+ * nullable).  pp may be NULL for the defaults.  p->n_theta must be a
+ * multiple of 36; the frame size must leave conv4 at least 4 x 8 (about
+ * w >= 450, h >= 200).
  */
 LD_API ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
                                           const ld_params *p, const ld_proposal_net *net,

@@ -810,7 +810,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     ld_status st = check_params(&p);
     if (st != LD_OK) return st;
     if (p.n_theta % 36 != 0) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: n_theta must be a multiple of 36");
-    ld_proposal_params q = prp ? *prp : ld_proposal_params{0.5f, 0.9f, 2, 0};
+    ld_proposal_params q = prp ? *prp : ld_proposal_params{0.05f, 0.5f, 2, 0};
     if (q.reserved != 0 || q.margin < 0 || !(q.p_band >= 0.f && q.p_band <= 1.f) ||
         !(q.p_fallback >= 0.f && q.p_fallback <= 1.f))
         return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: bad proposal parameters");

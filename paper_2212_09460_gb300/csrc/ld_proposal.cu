@@ -80,20 +80,25 @@ __global__ void prefix_kernel(const int32_t *tiles, int n, int32_t *unit_begin) 
     }
 }
 
-// Training targets from a frame's peaks (one CTA per frame): theta band of
-// each peak, and every 135-row band (of 8) holding a row y at which the
-// peak's line rho = x cos(theta) + y sin(theta) is inside the frame,
-// 0 <= x <= w - 1 (|cos theta| <= 1e-9: the row y = rho / sin theta).
+// Training targets from a frame's peaks (one CTA per frame).  A peak counts
+// if it is among the first `always_k` or has >= rel_votes times the first
+// peak's votes.  Targets: the theta band of each counted peak, and every
+// h/8-row band holding a row y at which the counted peak's line
+// rho = x cos(theta) + y sin(theta) is inside the frame, 0 <= x <= w - 1
+// (|cos theta| <= 1e-9: the row y = rho / sin theta).
 __global__ void __launch_bounds__(256) targets_kernel(const ld_peak *peaks, const int32_t *n_peaks, int top_k, int w,
-                                                     int h, int n_theta, int D, float *targets) {
+                                                     int h, int n_theta, int D, int always_k, float rel_votes,
+                                                     float *targets) {
     __shared__ int on[kOut];
     const int f = blockIdx.x;
     if (threadIdx.x < kOut) on[threadIdx.x] = 0;
     __syncthreads();
     const int np = n_peaks[f];
+    const float vmin = np > 0 ? rel_votes * (float)peaks[(int64_t)f * top_k].votes : 0.f;
     for (int q = threadIdx.x; q < np * h; q += blockDim.x) {
         const int k = q / h, y = q % h;
         const ld_peak pk = peaks[(int64_t)f * top_k + k];
+        if (k >= always_k && (float)pk.votes < vmin) continue;
         if (y == 0) on[pk.theta_idx * kBands / n_theta] = 1;
         const double ang = M_PI * (double)pk.theta_idx / (double)n_theta;
         const double c = cos(ang), s = sin(ang), rho = (double)(pk.rho_idx - D);
@@ -127,9 +132,10 @@ cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p
 }  // namespace ld
 
 extern "C" ld_status ld_proposal_targets(const ld_peak *d_peaks, const int32_t *d_n_peaks, int32_t n, int32_t top_k,
-                                        int32_t w, int32_t h, int32_t n_theta, float *d_targets, void *stream) {
+                                        int32_t w, int32_t h, int32_t n_theta, int32_t always_k, float rel_votes,
+                                        float *d_targets, void *stream) {
     if (!d_peaks || !d_n_peaks || !d_targets || n < 1 || top_k < 1 || w < 3 || h < 3 || n_theta < 36 ||
-        n_theta % 36 != 0 || n_theta > ld::kMaxTheta) {
+        n_theta % 36 != 0 || n_theta > ld::kMaxTheta || always_k < 0 || !(rel_votes >= 0.f)) {
         ld::set_last_error("ld_proposal_targets: bad argument (n_theta a multiple of 36)");
         return LD_ERR_INVALID;
     }
@@ -138,7 +144,7 @@ extern "C" ld_status ld_proposal_targets(const ld_peak *d_peaks, const int32_t *
     while (D * D < r2) ++D;
     while (D > 0 && (D - 1) * (D - 1) >= r2) --D;
     ld::targets_kernel<<<n, 256, 0, (cudaStream_t)stream>>>(d_peaks, d_n_peaks, top_k, w, h, n_theta, (int)D,
-                                                            d_targets);
+                                                            always_k, rel_votes, d_targets);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         ld::set_last_error(cudaGetErrorString(e));

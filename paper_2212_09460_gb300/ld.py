@@ -88,7 +88,7 @@ _SIGS = {
                     ctypes.POINTER(ctypes.c_int32)],
     "ld_synth_frames": [_P, ctypes.c_int32, _P],
     "ld_proposal_targets": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                            _P, _P],
+                            ctypes.c_int32, ctypes.c_float, _P, _P],
     "ld_detect_batch_proposal": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
                                  ctypes.POINTER(ld_proposal_net), ctypes.POINTER(ld_proposal_params), _P, _P, _P, _P,
                                  _P, _P],
@@ -273,11 +273,13 @@ def ld_edge_pool_batch(ctx, frames, p, d_pool, stream) -> None:
     _check(load().ld_edge_pool_batch(ctx, arr, len(arr), ctypes.byref(p), d_pool, stream))
 
 
-def ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, d_targets, stream) -> None:
-    _check(load().ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, d_targets, stream))
+def ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, always_k, rel_votes, d_targets,
+                        stream) -> None:
+    _check(load().ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, always_k, rel_votes, d_targets,
+                                      stream))
 
 
-def proposal_params(p_band=0.5, p_fallback=0.9, margin=2) -> ld_proposal_params:
+def proposal_params(p_band=0.05, p_fallback=0.5, margin=2) -> ld_proposal_params:
     q = ld_proposal_params()
     q.p_band, q.p_fallback, q.margin, q.reserved = p_band, p_fallback, margin, 0
     return q

@@ -1,10 +1,14 @@
 """Train the theta-band proposal network on the GPU, and evaluate it.
 
 Training data: seeded synthetic 1920x1080 dashed-lane frames (the throughput
-frame style) generated on the device, labelled by the plain path: top-4
-Hough peaks (360 theta bins, 5x5 suppression) with the 1-pixel frame
-border cleared, so that the labels are the lane lines and not the image
-border.  Input: the 8x8 edge-count map of the same binary image.  Every step
+frame style) generated on the device, labelled by the plain path with the
+1-pixel frame border cleared (so that the labels are the lane lines, not the
+image border): 360 theta bins, 5x5 suppression, top-16 peaks, of which the
+first 4 and every peak with at least 40% of the first one's votes count.
+The counted set holds every band the top-4 peaks the proposal must find lie
+in, plus the bands of other strong lane lines (a frame's 4th and 5th lane
+edges often differ by a few votes, so which of them is in the top 4 is not
+predictable from the image; restricted voting is exact for any superset).  Input: the 8x8 edge-count map of the same binary image.  Every step
 (generation, Sobel, voting, targets, network forward/backward, Adam) runs in
 libld.so's kernels.
 
@@ -27,6 +31,7 @@ from . import ld, synth
 from .proposal import ProposalNet
 
 W, H, N_THETA, TOP_K = 1920, 1080, 360, 4
+LABEL_TOP_K, LABEL_ALWAYS, LABEL_REL = 16, 4, 0.4
 TRAIN_SEED0, EVAL_SEED0 = 1_000_000, 9_000_000
 
 
@@ -49,10 +54,11 @@ class FrameSource:
 def labelled_batch(torch, ctx, src, seeds, p):
     frames = src.fill(seeds)
     pool = ctx.edge_pool(frames, p)
-    pk, npk, st = ctx.detect_batch(frames, p)
+    p_lab = ld.params(n_theta=p.n_theta, top_k=LABEL_TOP_K, border=p.border)
+    pk, npk, st = ctx.detect_batch(frames, p_lab)
     tgt = torch.empty((len(frames), 44), dtype=torch.float32, device=src.device)
-    ld.ld_proposal_targets(pk.data_ptr(), npk.data_ptr(), len(frames), TOP_K, W, H, N_THETA, tgt.data_ptr(),
-                           torch.cuda.current_stream(src.device).cuda_stream)
+    ld.ld_proposal_targets(pk.data_ptr(), npk.data_ptr(), len(frames), LABEL_TOP_K, W, H, N_THETA, LABEL_ALWAYS,
+                           LABEL_REL, tgt.data_ptr(), torch.cuda.current_stream(src.device).cuda_stream)
     return frames, pool, tgt
 
 
@@ -78,7 +84,7 @@ def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every:
     return net, log
 
 
-def evaluate(weights: str, frames: int, batch: int = 64, p_band=0.5, p_fallback=0.9, margin=2):
+def evaluate(weights: str, frames: int, batch: int = 64, p_band=0.05, p_fallback=0.5, margin=2):
     """Proposal vs plain on held-out frames: peak agreement, fallback rate,
     voted fraction, and device time of both paths (frames resident)."""
     import torch
@@ -130,8 +136,8 @@ def main():
     ap.add_argument("--out", default="proposal_1080p.npz")
     ap.add_argument("--eval", default=None, help="weights file to evaluate instead of training")
     ap.add_argument("--frames", type=int, default=10000)
-    ap.add_argument("--p-band", type=float, default=0.5)
-    ap.add_argument("--p-fallback", type=float, default=0.9)
+    ap.add_argument("--p-band", type=float, default=0.05)
+    ap.add_argument("--p-fallback", type=float, default=0.5)
     ap.add_argument("--margin", type=int, default=2)
     a = ap.parse_args()
     from . import build

@@ -78,16 +78,19 @@ def test_fallback_equals_plain_path(ctx, ldlib, ora):
     np.testing.assert_array_equal(pk[0, : npk[0]], ref)
 
 
-def test_targets_kernel_matches_oracle(ctx, ldlib):
+@pytest.mark.parametrize("always_k,rel", [(4, 0.0), (4, 0.4), (0, 0.6), (16, 1.0)])
+def test_targets_kernel_matches_oracle(ctx, ldlib, always_k, rel):
     raw, dev = _frames([4200, 4201, 4202, 4203])
-    p = ldlib.params(n_theta=NT, top_k=4, border=1)
+    p = ldlib.params(n_theta=NT, top_k=16, border=1)
     pk, npk, st = ctx.detect_batch(dev, p)
     tgt = torch.empty((4, 44), dtype=torch.float32, device="cuda")
-    ldlib.ld_proposal_targets(pk.data_ptr(), npk.data_ptr(), 4, 4, W, H, NT, tgt.data_ptr(),
+    ldlib.ld_proposal_targets(pk.data_ptr(), npk.data_ptr(), 4, 16, W, H, NT, always_k, rel, tgt.data_ptr(),
                               torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     pkc, nc, tg = pk.cpu().numpy(), npk.cpu().numpy(), tgt.cpu().numpy()
     for i in range(4):
         peaks = pkc[i, : nc[i]]
-        np.testing.assert_array_equal(tg[i, :36], cnn.theta_band_targets(peaks, NT))
-        np.testing.assert_array_equal(tg[i, 36:], cnn.row_band_targets(peaks, W, H, NT))
+        keep = [k for k in range(len(peaks)) if k < always_k or peaks[k, 2] >= np.float32(rel) * np.float32(peaks[0, 2])]
+        sel = peaks[keep]
+        np.testing.assert_array_equal(tg[i, :36], cnn.theta_band_targets(sel, NT))
+        np.testing.assert_array_equal(tg[i, 36:], cnn.row_band_targets(sel, W, H, NT))
