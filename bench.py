@@ -199,6 +199,71 @@ def batching_and_latency(torch, ld, dev, mixed_host, flush):
     return batching, latency
 
 
+def proposal_vs_plain(torch, ld, dev, flush, check_frames: int = 1024, reps: int = 10):
+    """The learned-proposal path against the plain path on held-out 1080p frames
+    (border CLEAR, the setting the network was trained for): identical-peak
+    rate and fallback rate over `check_frames` frames, and frames/s of both
+    paths on one resident 64-frame batch (back-to-back calls, L2 flushed)."""
+    from paper_2212_09460_gb300 import serving, train_proposal as tp
+    from paper_2212_09460_gb300.proposal import ProposalNet
+    net = ProposalNet.load(serving.WEIGHTS, dev.index)
+    p = ld.params(n_theta=N_THETA, top_k=TOP_K, border=ld.LD_BORDER_CLEAR)
+    q = ld.proposal_params()
+    src = tp.FrameSource(torch, dev, N_FRAMES)
+    same = fb = act = total = 0
+    with ld.Context(dev.index) as c:
+        c.autotune(src.fill(tp.EVAL_SEED0 + np.arange(16)), p, iters=2)
+        for b0 in range(0, check_frames, N_FRAMES):
+            prep = c.prepare(src.fill(tp.EVAL_SEED0 + b0 + np.arange(N_FRAMES)))
+            a = [t.cpu().numpy() for t in c.detect_batch(prep, p)]
+            b = [t.cpu().numpy() for t in c.detect_batch_proposal(prep, p, net, q)]
+            assert (a[2] == 0).all() and (b[2] == 0).all()
+            for i in range(N_FRAMES):
+                same += int(a[1][i] == b[1][i] and np.array_equal(a[0][i, : a[1][i]], b[0][i, : b[1][i]]))
+            fb, act, total = fb + int(b[3].sum()), act + int(b[4].sum()), total + N_FRAMES
+        out_a = (torch.zeros((N_FRAMES, TOP_K, 3), dtype=torch.int32, device=dev),) + tuple(
+            torch.zeros(N_FRAMES, dtype=torch.int32, device=dev) for _ in range(2))
+        out_b = (torch.zeros((N_FRAMES, TOP_K, 3), dtype=torch.int32, device=dev),) + tuple(
+            torch.zeros(N_FRAMES, dtype=torch.int32, device=dev) for _ in range(4))
+        stream = torch.cuda.current_stream(dev)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for e0, e1 in e:
+                flush()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return sum(e0.elapsed_time(e1) for e0, e1 in e) / reps
+
+        ms_a = timed(lambda: c.detect_batch(prep, p, out=out_a, stream=stream))
+        ms_b = timed(lambda: c.detect_batch_proposal(prep, p, net, q, out=out_b, stream=stream))
+    return {"workload": f"held-out 1920x1080 frames (seeds {tp.EVAL_SEED0}+), border CLEAR, {N_THETA} theta, "
+                        f"top-{TOP_K}; defaults p_band {q.p_band:.2f}, p_fallback {q.p_fallback:.2f}, "
+                        f"margin {q.margin}",
+            "identical_peaks": same / total, "frames_checked": total, "fallback_rate": fb / total,
+            "voted_theta_fraction": act / total / (N_THETA // 2),
+            "plain_ms_per_64": ms_a, "proposal_ms_per_64": ms_b,
+            "plain_frames_per_s": N_FRAMES / (ms_a / 1e3), "proposal_frames_per_s": N_FRAMES / (ms_b / 1e3),
+            "speedup": ms_a / ms_b}
+
+
+def serving_run(seconds: float, rate_scale: float, workers: int = 3):
+    """The 8-camera serving loop (3 x 1280x720, 3 x 1920x1080, 2 x 3840x2160,
+    Poisson, 30 frames/s each x rate_scale): latency percentiles, arrival to
+    peaks on the host."""
+    from paper_2212_09460_gb300 import serving
+    srv = serving.Server(workers=workers)
+    try:
+        st = srv.serve(seconds, rate_scale=rate_scale)
+    finally:
+        srv.close()
+    return {"seconds": seconds, "offered_frames_per_s": 8 * 30 * rate_scale, **serving.summarize(st)}
+
+
 def cpu_baseline(frames: np.ndarray, budget_s: float = 12.0):
     """The oracle as it stands, single-threaded, on as many frames as fit the budget."""
     import oracle
@@ -256,7 +321,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the mixed-resolution batching and single-frame latency measurements")
+                    help="skip the mixed-resolution batching, single-frame latency, proposal and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the 8-camera serving run at the nominal 30 frames/s per camera (0: skip)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames per GPU (the workload is 64; smaller values are for profiling captures)")
     args = ap.parse_args()
@@ -406,6 +473,10 @@ def main():
         if mixed_host is not None:
             extra["batching"], extra["latency_640x480"] = batching_and_latency(
                 torch, ld, dev, mixed_host, lambda: flush.fill_(7))
+            extra["proposal"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9))
+            if args.serve_seconds > 0:
+                extra["serving"] = {"nominal": serving_run(args.serve_seconds, 1.0),
+                                    "loaded_x20": serving_run(min(args.serve_seconds, 3.0), 20.0)}
         with_cpu = not args.no_cpu_baseline
         cpu = cpu_baseline(host_frames) if with_cpu else None
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

@@ -46,10 +46,22 @@ def _mix64(z: np.ndarray) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
+_U64 = (1 << 64) - 1
+
+
+def _mix64_int(z: int) -> int:
+    """_mix64 on one Python integer (the per-frame scalars; no numpy overhead)."""
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _U64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _U64
+    return z ^ (z >> 31)
+
+
+def _stream_base_int(seed: int, stream: int) -> int:
+    return _mix64_int(((int(seed) * 8 + int(stream)) + 0x9E3779B97F4A7C15) & _U64)
+
+
 def _stream_base(seed: int, stream: int) -> np.uint64:
-    with np.errstate(over="ignore"):
-        s = np.array([(int(seed) * 8 + int(stream)) & ((1 << 64) - 1)], np.uint64)
-        return _mix64(s + _GAMMA)[0]
+    return np.uint64(_stream_base_int(seed, stream))
 
 
 def _draws(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
@@ -63,13 +75,13 @@ class _Scalars:
     """Sequential uniform draws for the per-frame parameters (stream 0)."""
 
     def __init__(self, seed: int):
-        self.seed = seed
+        self.base = _stream_base_int(seed, 0)
         self.i = 0
 
     def u(self) -> float:
-        v = _draws(self.seed, 0, np.array([self.i]))[0]
+        v = _mix64_int((self.base + (self.i + 1) * 0x9E3779B97F4A7C15) & _U64)
         self.i += 1
-        return float(v >> np.uint64(11)) / float(1 << 53)
+        return float(v >> 11) / float(1 << 53)
 
     def randint(self, lo: int, hi: int) -> int:
         """Uniform integer in [lo, hi]."""
@@ -187,7 +199,7 @@ def frame_params(seed: int, w: int, h: int, style: FrameStyle = LATENCY_640x480)
     generator that reproduces it: stream bases, Q32 noise scales, salt
     threshold and stripe geometry."""
     return {
-        "base": [int(_stream_base(seed, s)) for s in (1, 2, 3)],
+        "base": [_stream_base_int(seed, s) for s in (1, 2, 3)],
         "k_top": int(round(style.sigma / _IH8_STD * 2.0 ** 32)),
         "k_road": int(round(style.sigma_road / _IH8_STD * 2.0 ** 32)),
         "salt_thr": int(style.salt * 2.0 ** 32) if style.salt > 0 else 0,
