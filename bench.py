@@ -49,6 +49,27 @@ MEASURED_TRAFFIC = {
 }
 
 
+def rank_seeds(rank: int, frames_per_rank: int) -> list[int]:
+    """Frame seeds of one rank: ranks take disjoint consecutive blocks, so N
+    ranks process N x frames_per_rank distinct frames (weak scaling)."""
+    return [SEED0 + rank * frames_per_rank + i for i in range(frames_per_rank)]
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise max of per-rank timings (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(world: int, frames_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job frames/s: every rank's frames over the slowest rank's time."""
+    return world * frames_per_rank * steps / (total_ms / 1000.0)
+
+
 def measured_traffic(kernel: str, frames: int):
     """Per-launch DRAM bytes scaled from the recorded capture, or None if the kernel changed."""
     import hashlib
@@ -339,7 +360,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     # frames are generated before any CUDA call (spawn pool)
-    seeds = [SEED0 + rank * nf + i for i in range(nf)]
+    seeds = rank_seeds(rank, nf)
     host_frames = make_frames(seeds)
     mixed_host = make_mixed_frames() if (rank == 0 and not args.no_extra) else None
 
@@ -438,10 +459,7 @@ def main():
     assert int(st_h.abs().sum()) == 0 and bool((npk_h == TOP_K).all())
 
     # max over ranks
-    if dist:
-        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
 
     if rank == 0:
         import json as _json
@@ -451,8 +469,8 @@ def main():
         hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
         sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        value = world * nf * args.steps / (total_ms / 1000.0)
-        e2e_val = world * nf / (e2e_ms / 1000.0)
+        value = job_throughput(world, nf, args.steps, total_ms)
+        e2e_val = job_throughput(world, nf, 1, e2e_ms)
 
         # algorithmic work per step: Hough E*n_theta votes per frame;
         # Sobel 1 B/px read + 4 B per edge written
