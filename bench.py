@@ -220,7 +220,7 @@ def batching_and_latency(torch, ld, dev, mixed_host, flush):
     return batching, latency
 
 
-def proposal_vs_plain(torch, ld, dev, flush, check_frames: int = 1024, reps: int = 10):
+def proposal_vs_plain(torch, ld, dev, flush, check_frames: int = 1024, reps: int = 10, p_fallback=None):
     """The learned-proposal path against the plain path on held-out 1080p frames
     (border CLEAR, the setting the network was trained for): identical-peak
     rate and fallback rate over `check_frames` frames, and frames/s of both
@@ -229,7 +229,7 @@ def proposal_vs_plain(torch, ld, dev, flush, check_frames: int = 1024, reps: int
     from paper_2212_09460_gb300.proposal import ProposalNet
     net = ProposalNet.load(serving.WEIGHTS, dev.index)
     p = ld.params(n_theta=N_THETA, top_k=TOP_K, border=ld.LD_BORDER_CLEAR)
-    q = ld.proposal_params()
+    q = ld.proposal_params() if p_fallback is None else ld.proposal_params(p_fallback=p_fallback)
     src = tp.FrameSource(torch, dev, N_FRAMES)
     same = fb = act = total = 0
     with ld.Context(dev.index) as c:
@@ -495,6 +495,9 @@ def main():
             extra["batching"], extra["latency_640x480"] = batching_and_latency(
                 torch, ld, dev, mixed_host, lambda: flush.fill_(7))
             extra["proposal"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9))
+            # the configuration's literal fallback rule (max band probability < 0.9)
+            extra["proposal_fallback_0.9"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9),
+                                                               check_frames=512, p_fallback=0.9)
             if args.serve_seconds > 0:
                 extra["serving"] = {"nominal": serving_run(args.serve_seconds, 1.0),
                                     "loaded_x20": serving_run(min(args.serve_seconds, 3.0), 20.0)}
