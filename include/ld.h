@@ -206,20 +206,22 @@ LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
 /*
  * Autotuner for ld_detect_batch.  For every distinct frame size among
  * h_frames (device images, as in ld_detect_batch), it times ld_detect_batch
- * on the frames of that size for each candidate voting tile size (theta
- * pairs per CTA: the compiled sizes from 1/8 of the largest that fits shared
- * memory up to it) and each
- * Sobel strip height (2, 4 or 8 rows per warp), `iters` times each, and keeps
- * the fastest pair in the context; later ld_detect_batch calls on frames of
- * that size and n_theta use it.  Results do not depend on the choice.  Runs
+ * on the frames of that size, `iters` calls per candidate: first the voting
+ * stage for each candidate voting tile size (theta pairs per CTA: the
+ * compiled sizes from 1/8 of the largest that fits shared memory up to it),
+ * then the Sobel stage for each run length (1, 2 or 4 groups of 8 rows per
+ * warp), and keeps the fastest of each in the context; later ld_detect_batch
+ * calls on frames of that size and n_theta use them.  Results do not depend
+ * on the choice.  Stage timings recorded before the call are discarded.  Runs
  * and synchronises `stream`; allocates scratch like ld_detect_batch; must not
  * be captured.  iters >= 1.
  */
 LD_API ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
                              const ld_params *p, int32_t iters, void *stream);
 
-/* The voting tile size (theta pairs per CTA) and Sobel rows per warp that
- * ld_detect_batch uses for w x h frames with p->n_theta (tuned or default). */
+/* The voting tile size (theta pairs per CTA) and the Sobel run length (in
+ * groups of 8 rows per warp) that ld_detect_batch uses for w x h frames with
+ * p->n_theta (tuned or default). */
 LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *p,
                              int32_t *pairs_per_tile, int32_t *sobel_rows);
 

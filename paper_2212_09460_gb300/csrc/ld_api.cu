@@ -202,12 +202,14 @@ ld_params defaults() {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Sobel rows per warp: 4 (60 registers, 4 CTAs per SM) when that still gives
-// >= 2 CTAs per SM, else 2 (shorter strips, more CTAs for small images).
-int pick_rows(int64_t tiles_x, int64_t total_rows_tiles_at_r2, int num_sms) {
-    (void)tiles_x;
-    if (total_rows_tiles_at_r2 / 2 >= 2 * num_sms) return 4;
-    return 2;
+// Sobel 8-row groups per warp task: the longest runs (4 groups) that still
+// give at least 3 CTAs per SM for the launch group, else shorter ones (small
+// frames need the CTAs more than the longer runs).  ctas_at_g1 is the CTA
+// count with 1 group per task.
+int pick_sobel_groups(int64_t ctas_at_g1, int num_sms) {
+    if (ctas_at_g1 / 4 >= 3 * num_sms) return 4;
+    if (ctas_at_g1 / 2 >= 3 * num_sms) return 2;
+    return 1;
 }
 
 // Small per-context scratch: per-frame edge counts, error flags and finished
@@ -234,7 +236,39 @@ HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
     hp.pairs = pairs < 1 ? 1 : (pairs > pmax ? pmax : pairs);
     if (hp.pairs > n_pairs) hp.pairs = n_pairs;
     hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
+    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;   // pairs are split evenly over the tiles
     return hp;
+}
+
+// Fraction of the persistent CTAs' slots that `units` equal work units fill.
+double wave_fill(int64_t units, int num_sms) {
+    const int64_t waves = (units + num_sms - 1) / num_sms;
+    return waves > 0 ? (double)units / (double)(waves * num_sms) : 1.0;
+}
+
+// For a launch group whose frames share one plan: the tile count in
+// [T, 1.25 T] (and at least 2 pairs per tile) whose units fill the last wave of
+// the persistent launch best; more tiles only when that gains > 2% of fill.
+void balance_tiles(std::vector<HoughPlan> &plans, int n_pairs, int num_sms) {
+    const int gn = (int)plans.size();
+    for (int k = 1; k < gn; ++k)
+        if (plans[k].n_tiles != plans[0].n_tiles || plans[k].n_rho != plans[0].n_rho) return;
+    const int T0 = plans[0].n_tiles;
+    if ((int64_t)gn * T0 < num_sms) return;
+    int best = T0;
+    double best_fill = wave_fill((int64_t)gn * T0, num_sms);
+    for (int T = T0 + 1; T <= T0 + (T0 + 3) / 4 && 2 * T <= n_pairs; ++T) {
+        const double f = wave_fill((int64_t)gn * T, num_sms);
+        if (f > best_fill + 0.02) {
+            best = T;
+            best_fill = f;
+        }
+    }
+    if (best == T0) return;
+    for (HoughPlan &hp : plans) {
+        hp.n_tiles = best;
+        hp.pairs = (n_pairs + best - 1) / best;
+    }
 }
 
 HoughPlan plan_hough(int w, int h, int n_theta) {
@@ -256,7 +290,6 @@ HoughPlan plan_hough(int w, int h, int n_theta) {
     }
     hp.n_tiles = (n_pairs + pmax - 1) / pmax;
     hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
-    hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
     return hp;
 }
 
@@ -267,9 +300,9 @@ HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta) {
     return plan_hough(w, h, n_theta);
 }
 
-// Sobel rows per warp for a launch group: forced, else the tuned value of the
-// group's largest frame size, else the default heuristic.
-int rows_for(const ld_ctx *ctx, const ld_frame *fr, int g0, int g1, int n_theta, int64_t tiles_r2) {
+// Sobel 8-row groups per warp task for a launch group: forced, else the tuned
+// value of the group's largest frame size, else the default heuristic.
+int rows_for(const ld_ctx *ctx, const ld_frame *fr, int g0, int g1, int n_theta) {
     if (ctx->force_rows > 0) return ctx->force_rows;
     int64_t best_px = -1;
     int rows = 0;
@@ -281,7 +314,10 @@ int rows_for(const ld_ctx *ctx, const ld_frame *fr, int g0, int g1, int n_theta,
             rows = it->second.second;
         }
     }
-    return rows > 0 ? rows : pick_rows(0, tiles_r2, ctx->num_sms);
+    if (rows > 0) return rows;
+    int64_t ctas_g1 = 0;
+    for (int i = g0; i < g1; ++i) ctas_g1 += sobel_frame_ctas(fr[i].w, fr[i].h, 1);
+    return pick_sobel_groups(ctas_g1, ctx->num_sms);
 }
 
 ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
@@ -380,11 +416,11 @@ ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable) {
     return LD_OK;
 }
 
-ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]) {
-    if (!ctx || !ms) return fail(LD_ERR_INVALID, "ld_ctx_stage_ms: NULL argument");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+}  // extern "C"
+
+namespace {
+// Sum and reset the stage times of the calls timed so far (caller holds ctx->mu).
+ld_status stage_sums(ld_ctx *ctx, float ms[3]) {
     ms[0] = ms[1] = 0.f;
     ms[2] = (float)ctx->timed_calls;
     for (int c = 0; c < ctx->timed_calls; ++c) {
@@ -400,6 +436,17 @@ ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]) {
     }
     ctx->timed_calls = 0;
     return LD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]) {
+    if (!ctx || !ms) return fail(LD_ERR_INVALID, "ld_ctx_stage_ms: NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    return stage_sums(ctx, ms);
 }
 
 ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
@@ -424,10 +471,7 @@ ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_
     L.n = 1;
     L.threshold = p.threshold;
     L.border = p.border;
-    const int tiles_x = (w + kSobelTileW - 1) / kSobelTileW;
-    const int64_t r2tiles = (int64_t)tiles_x * ((h + 15) / 16);
-    L.rows_per_warp = pick_rows(tiles_x, r2tiles, ctx->num_sms);
-    const int rows_cta = L.rows_per_warp * (kSobelThreads / 32);
+    L.groups = pick_sobel_groups(sobel_frame_ctas(w, h, 1), ctx->num_sms);
     SobelFrame &F = L.f[0];
     F.img = d_img;
     F.bin = d_bin;
@@ -438,9 +482,8 @@ ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_
     F.h = h;
     F.pitch = pitch;
     F.tile_begin = 0;
-    F.tiles_x = tiles_x;
-    const int n_ctas = tiles_x * ((h + rows_cta - 1) / rows_cta);
-    e = launch_sobel(L, n_ctas, s);
+    F.tiles_x = sobel_strips(w);
+    e = launch_sobel(L, sobel_frame_ctas(w, h, L.groups), s);
     if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
     return LD_OK;
 }
@@ -589,7 +632,8 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         int64_t ed = 0, ca = 0;
         for (int i = g0; i < g1; ++i) {
             ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
-            ca += (int64_t)plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles * M;
+            const int T0 = plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles;
+            ca += (int64_t)std::min(p.n_theta / 2, T0 + (T0 + 3) / 4) * M;   // room for balance_tiles
         }
         if (ed > max_edges) max_edges = ed;
         if (ca > max_cand) max_cand = ca;
@@ -617,13 +661,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         SLn.n = gn;
         SLn.threshold = p.threshold;
         SLn.border = p.border;
-        int64_t tiles_r2 = 0;
-        for (int i = g0; i < g1; ++i) {
-            const int tx = (h_frames[i].w + kSobelTileW - 1) / kSobelTileW;
-            tiles_r2 += (int64_t)tx * ((h_frames[i].h + 15) / 16);
-        }
-        SLn.rows_per_warp = rows_for(ctx, h_frames, g0, g1, p.n_theta, tiles_r2);
-        const int rows_cta = SLn.rows_per_warp * (kSobelThreads / 32);
+        SLn.groups = rows_for(ctx, h_frames, g0, g1, p.n_theta);
         // per-frame scratch offsets and plans (frame order)
         eoffs.assign(gn, 0);
         coffs.assign(gn, 0);
@@ -632,6 +670,10 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         for (int k = 0; k < gn; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
             plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta);
+        }
+        balance_tiles(plans, p.n_theta / 2, ctx->num_sms);
+        for (int k = 0; k < gn; ++k) {
+            const ld_frame &fr = h_frames[g0 + k];
             eoffs[k] = eoff;
             coffs[k] = coff;
             eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
@@ -652,8 +694,8 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             SF.h = fr.h;
             SF.pitch = fr.pitch;
             SF.tile_begin = sob_ctas;
-            SF.tiles_x = (fr.w + kSobelTileW - 1) / kSobelTileW;
-            sob_ctas += SF.tiles_x * ((fr.h + rows_cta - 1) / rows_cta);
+            SF.tiles_x = sobel_strips(fr.w);
+            sob_ctas += sobel_frame_ctas(fr.w, fr.h, SLn.groups);
         }
         // voting work units: frames with the most work (pixels x tile size)
         // first, so that the persistent CTAs end together (longest first)
@@ -771,11 +813,7 @@ ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, c
         SL.n = g1 - g0;
         SL.threshold = p.threshold;
         SL.border = p.border;
-        int64_t tiles_r2 = 0;
-        for (int i = g0; i < g1; ++i)
-            tiles_r2 += (int64_t)((h_frames[i].w + kSobelTileW - 1) / kSobelTileW) * ((h_frames[i].h + 15) / 16);
-        SL.rows_per_warp = rows_for(ctx, h_frames, g0, g1, p.n_theta, tiles_r2);
-        const int rows_cta = SL.rows_per_warp * (kSobelThreads / 32);
+        SL.groups = rows_for(ctx, h_frames, g0, g1, p.n_theta);
         int ctas = 0;
         int64_t eoff = 0;
         for (int i = g0; i < g1; ++i) {
@@ -790,8 +828,8 @@ ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, c
             F.h = fr.h;
             F.pitch = fr.pitch;
             F.tile_begin = ctas;
-            F.tiles_x = (fr.w + kSobelTileW - 1) / kSobelTileW;
-            ctas += F.tiles_x * ((fr.h + rows_cta - 1) / rows_cta);
+            F.tiles_x = sobel_strips(fr.w);
+            ctas += sobel_frame_ctas(fr.w, fr.h, SL.groups);
             eoff += ((int64_t)fr.w * fr.h + 3) / 4 * 4;
             poff += (int64_t)((fr.h + 7) / 8) * ((fr.w + 7) / 8);
         }
@@ -888,10 +926,8 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     SL.n = n;
     SL.threshold = p.threshold;
     SL.border = p.border;
-    const int tx = (w + kSobelTileW - 1) / kSobelTileW;
-    SL.rows_per_warp = rows_for(ctx, h_frames, 0, n, p.n_theta, (int64_t)n * tx * ((h + 15) / 16));
-    const int rows_cta = SL.rows_per_warp * (kSobelThreads / 32);
-    const int per_frame_ctas = tx * ((h + rows_cta - 1) / rows_cta);
+    SL.groups = rows_for(ctx, h_frames, 0, n, p.n_theta);
+    const int per_frame_ctas = sobel_frame_ctas(w, h, SL.groups);
     for (int i = 0; i < n; ++i) {
         SobelFrame &F = SL.f[i];
         F.img = h_frames[i].img;
@@ -905,7 +941,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         F.h = h;
         F.pitch = h_frames[i].pitch;
         F.tile_begin = i * per_frame_ctas;
-        F.tiles_x = tx;
+        F.tiles_x = sobel_strips(w);
     }
     e = launch_sobel(SL, n * per_frame_ctas, s);
     if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
@@ -982,8 +1018,7 @@ ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *pp, in
     if (pairs_per_tile) *pairs_per_tile = hp.pairs;
     if (sobel_rows) {
         const ld_frame f = {nullptr, w, h, w, 0};
-        const int tx = (w + kSobelTileW - 1) / kSobelTileW;
-        *sobel_rows = rows_for(ctx, &f, 0, 1, p.n_theta, (int64_t)tx * ((h + 15) / 16));
+        *sobel_rows = rows_for(ctx, &f, 0, 1, p.n_theta);
     }
     return LD_OK;
 }
@@ -1010,9 +1045,6 @@ ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
     ld_peak *d_peaks = (ld_peak *)outs;
     int32_t *d_np = (int32_t *)(d_peaks + max_n * p.top_k);
     int32_t *d_st = d_np + max_n;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
     st = LD_OK;
     for (auto &kv : groups) {
         const int w = kv.first.first, h = kv.first.second;
@@ -1026,27 +1058,45 @@ ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         LD_HOUGH_PAIR_SIZES(LD_CAND)
 #undef LD_CAND
         if (pair_cands.empty()) pair_cands.push_back(std::max(1, pmax));
+        // the voting tile size by the voting stage's time, then the Sobel run
+        // length by the Sobel stage's time (the two stages are independent)
+        auto time_stage = [&](int P, int R, int stage, float *out) -> ld_status {
+            ctx->force_pairs = P;
+            ctx->force_rows = R;
+            ld_status r = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);   // warm-up
+            if (r != LD_OK) return r;
+            float junk[3];
+            r = stage_sums(ctx, junk);   // drop earlier timed calls
+            if (r != LD_OK) return r;
+            ctx->timing = true;
+            for (int it = 0; it < iters && r == LD_OK; ++it)
+                r = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);
+            ctx->timing = false;
+            if (r != LD_OK) return r;
+            float ms[3];
+            r = stage_sums(ctx, ms);
+            *out = ms[stage];
+            return r;
+        };
+        const bool timing_was = ctx->timing;
+        const int r0 = rows_for(ctx, fr.data(), 0, 1, p.n_theta);
         float best_ms = 1e30f;
-        int best_p = 0, best_r = 0;
+        int best_p = pair_cands[0], best_r = r0;
         for (int P : pair_cands) {
-            for (int R : {2, 4, 8}) {
-                ctx->force_pairs = P;
-                ctx->force_rows = R;
-                st = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);   // warm-up
-                if (st != LD_OK) break;
-                cudaEventRecord(e0, s);
-                for (int it = 0; it < iters && st == LD_OK; ++it)
-                    st = detect_impl(ctx, fr.data(), (int)fr.size(), p, d_peaks, d_np, d_st, s);
-                cudaEventRecord(e1, s);
-                if (st != LD_OK) break;
-                e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) { best_ms = ms; best_p = P; best_r = R; }
-            }
+            float t = 0.f;
+            st = time_stage(P, r0, 1, &t);
             if (st != LD_OK) break;
+            if (t < best_ms) { best_ms = t; best_p = P; }
         }
+        best_ms = 1e30f;
+        for (int R : {1, 2, 4}) {
+            if (st != LD_OK) break;
+            float t = 0.f;
+            st = time_stage(best_p, R, 0, &t);
+            if (st != LD_OK) break;
+            if (t < best_ms) { best_ms = t; best_r = R; }
+        }
+        ctx->timing = timing_was;
         ctx->force_pairs = 0;
         ctx->force_rows = 0;
         if (st != LD_OK) break;
@@ -1054,8 +1104,6 @@ ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
     }
     ctx->force_pairs = 0;
     ctx->force_rows = 0;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     cudaFree(outs);
     return st;
 }

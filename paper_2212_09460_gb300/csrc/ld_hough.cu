@@ -147,17 +147,19 @@ __device__ __forceinline__ void vote_chunk(const uint32_t *buf, const uint32_t *
 // fixes the stage and phase of every mbarrier).  Returns false if a bounded
 // wait gave up (the frame is flagged; the CTA must stop).
 template <int PMAX>
-__device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFrame &F, int local, uint32_t &seq,
-                                           uint8_t *smem_raw, uint64_t *bars, SelectSmem &S, int &abort_flag,
-                                           int *tj) {
+__device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFrame &F, int local, int n_tiles,
+                                           uint32_t &seq, uint8_t *smem_raw, uint64_t *bars, SelectSmem &S,
+                                           int &abort_flag, int *tj) {
     const int ns = F.n_splits;
     const int tile = local / ns, split = local % ns;
     const int n_theta = L.n_theta;
-    const int j0 = tile * F.pairs_per_tile;
-    // pairs of this tile: contiguous j0.., or the next entries of the
-    // frame's active-pair list (restricted vote)
+    // pairs of this tile: the frame's pairs (all n_theta/2, or the active-pair
+    // list of a restricted vote) split as evenly as possible over its n_tiles
+    // tiles, the first n_avail % n_tiles tiles taking one more (<= PMAX)
     const int n_avail = F.pair_list ? *F.pair_count : n_theta / 2;
-    const int np = min(F.pairs_per_tile, n_avail - j0);
+    const int base = n_avail / n_tiles, extra = n_avail % n_tiles;
+    const int np = base + (tile < extra ? 1 : 0);
+    const int j0 = tile * base + min(tile, extra);
     if (threadIdx.x < PMAX) tj[threadIdx.x] = (threadIdx.x < np) ? (F.pair_list ? F.pair_list[j0 + threadIdx.x]
                                                                                  : j0 + (int)threadIdx.x)
                                                                   : 0;
@@ -469,7 +471,7 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
         const HoughFrame &F = L.f[lo];
         const int begin = ub ? ub[lo] : F.unit_begin;
         const int n_tiles = ub ? ub[lo + 1] - ub[lo] : F.n_tiles;
-        if (!hough_unit<PMAX>(L, F, u - begin, seq, smem_raw, bars, S, abort_flag, tile_j)) break;
+        if (!hough_unit<PMAX>(L, F, u - begin, n_tiles, seq, smem_raw, bars, S, abort_flag, tile_j)) break;
         if (L.mode == kHoughCandidates) {
             __syncthreads();   // this tile's candidates are written
             if (tid == 0) {
@@ -490,12 +492,15 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
 
 template <int PMAX>
 cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t s) {
-    static bool attr_set = false;   // per-process; set before the first launch
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemLimit - kStaticSmemReserve);
+    static uint64_t attr_set = 0;   // devices 0..63 whose attribute is set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(attr_set >> dev & 1u)) {
+        e = cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit - kStaticSmemReserve);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev < 64) attr_set |= uint64_t(1) << dev;
     }
     hough_kernel<PMAX><<<n_ctas, kHoughThreads, smem, s>>>(L);
     return cudaGetLastError();

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/ld.h"
@@ -23,8 +24,18 @@ constexpr int32_t kFlagTimeout = 1;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 // ---------------------------------------------------------------- Sobel
-constexpr int kSobelThreads = 256;      // 8 warps
-constexpr int kSobelTileW = 512;        // 32 lanes x 16 pixels
+constexpr int kSobelThreads = 256;      // 8 warps, each an independent task
+constexpr int kSobelWarps = kSobelThreads / 32;
+constexpr int kSobelStripW = 480;       // output pixels of a warp row (lanes 1..30 x 16)
+
+// Sobel geometry: a warp task is a strip of kSobelStripW columns by a run of
+// 8 * groups rows; a CTA takes kSobelWarps consecutive tasks of one frame.
+inline int sobel_strips(int w) { return (w + kSobelStripW - 1) / kSobelStripW; }
+inline int sobel_frame_ctas(int w, int h, int groups) {
+    const int run = 8 * groups;
+    const int tasks = sobel_strips(w) * ((h + run - 1) / run);
+    return (tasks + kSobelWarps - 1) / kSobelWarps;
+}
 
 struct SobelFrame {
     const uint8_t *img;
@@ -37,7 +48,7 @@ struct SobelFrame {
     int64_t cap;
     int32_t w, h, pitch;
     int32_t tile_begin;    // first CTA of this frame
-    int32_t tiles_x;
+    int32_t tiles_x;       // column strips (sobel_strips(w))
     int32_t pad_;
 };
 
@@ -45,7 +56,7 @@ struct SobelLaunch {
     int32_t n;
     int32_t threshold;
     int32_t border;
-    int32_t rows_per_warp;
+    int32_t groups;        // 8-row groups per warp task
     SobelFrame f[kMaxLaunchFrames];
 };
 

@@ -3,141 +3,157 @@
 // (Sec. 2.2, Sec. 4.2), and compaction of the 255 pixels into the packed
 // (y << 16) | x edge list the voting stage reads (Sec. 4.3).
 //
-// GB300 design (differs from the paper's 16x16-thread-block K80 kernel,
-// Eq. 6): one warp covers 512 contiguous pixels of a row with one 16-byte
-// load per lane, so every row is read with fully coalesced 512-byte warp
-// transactions.  A warp issues the loads of all R + 2 rows of its strip
-// (R output rows plus two halo rows) before computing, so that many bytes
-// are in flight per SM, then slides the 3x3 window down in registers; the
-// left/right neighbour bytes come from the adjacent lanes through shuffles,
-// and zero padding is virtual (never materialised).  Edge bits are compacted with a
-// block-wide prefix sum and one global atomic per CTA.
+// Arithmetic.  With T, M, B the rows above, at and below the pixel,
+// P = M + B, Q = T + M and R = B - T (per column), the Sobel components are
+// gx = (P+Q)(x+1) - (P+Q)(x-1) and gy = R(x-1) + 2R(x) + R(x+1), and
+//   gx + gy = 2 [P(x+1) - Q(x-1) + R(x)] = 2u,
+//   gy - gx = 2 [P(x-1) - Q(x+1) + R(x)] = 2w,
+// so |Gx| + |Gy| = max(|gx + gy|, |gx - gy|) = 2 max(|u|, |w|), and for a
+// threshold T in [1, 255] the saturated magnitude min(|Gx|+|Gy|, 255) >= T
+// exactly when max(|u|, |w|) >= ceil(T/2).  Q of a row is P of the row above
+// and R = P - Q, so a row costs one P, one R, u and w.
+//
+// Every quantity is an integer of magnitude < 2048, computed exactly in
+// fp16x2 in units of 2^-24: the fp16 numbers k * 2^-24 for |k| < 2048 are
+// exactly the subnormals and the lowest normal binade, spaced 2^-24 apart,
+// and the bit pattern of k * 2^-24 (k >= 0) is k itself.  So a pixel byte
+// placed in the low byte of a half is its value, sums and differences are
+// exact (no flush to zero: the instructions carry no .ftz), and the edge
+// flags are accumulated into bit masks by fused multiply-adds with weights
+// 2^j units.  Two pixels per instruction, on the fp16 pipe.
+//
+// Layout.  A lane holds 16 pixels of a row; its 32-bit word j (j = 0..7)
+// holds pixels (j, j + 8) as a half pair, so the x+1 and x-1 neighbours of
+// word j are the words j+1 and j-1, and only the words at the lane's ends
+// need the adjacent lanes (one shuffle each way per row).  A warp loads 512
+// contiguous bytes per row (16-byte copies, fully coalesced) and produces the
+// middle 480 pixels: lanes 0 and 31 only supply the left and right halo.  A
+// warp slides down a run of 8*G rows, prefetching 6 rows ahead into shared
+// memory (cp.async);
+// every 8 rows it takes one atomic on the frame's edge counter for the
+// warp's edges (a warp prefix sum gives each lane its slots) and writes them.
+// Zero padding is virtual: loads outside the image read 0.
 #include "ld_internal.cuh"
 
 namespace ld {
 namespace {
 
-struct Row {
-    uint32_t v[4];   // 16 pixels
-    uint32_t l, r;   // pixel x0-1 and x0+16
-};
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kStage = 1024;   // edge staging slots per warp (8-row group)
 
-__device__ __forceinline__ uint4 ldg_nc_v4(const void *p) {
+__device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2_sub(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// acc + (max(|u|, |w|) >= tau ? wt : 0), per half.
+__device__ __forceinline__ uint32_t h2_edge_acc(uint32_t u, uint32_t w, uint32_t tau, uint32_t wt, uint32_t acc) {
+    uint32_t au, aw, m, c, d;
+    asm("abs.f16x2 %0, %1;" : "=r"(au) : "r"(u));
+    asm("abs.f16x2 %0, %1;" : "=r"(aw) : "r"(w));
+    asm("max.f16x2 %0, %1, %2;" : "=r"(m) : "r"(au), "r"(aw));
+    asm("set.ge.f16x2.f16x2 %0, %1, %2;" : "=r"(c) : "r"(m), "r"(tau));   // 1.0 or 0.0
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(c), "r"(wt), "r"(acc));
+    return d;
+}
+
+// Row prefetch through shared memory: each lane copies its own 16 bytes of
+// a row with cp.async (zero-filled beyond the image: rows outside [0, h),
+// columns outside [0, w)), so rows wait in shared memory rather than in
+// registers.  A lane only ever reads back its own bytes, after its own
+// cp.async.wait_group, so no barrier is needed.
+constexpr int kRing = 8;       // row slots per warp
+constexpr int kAhead = 6;      // rows in flight ahead of the one being used
+// dynamic shared memory: the row rings and the edge staging slots (64 KB)
+constexpr int kSobelSmem = kSobelWarps * (kRing * 512 + kStage * 4);
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int nbytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start the copy of this lane's 16 bytes of row y into its slot (nb bytes
+// of the row from column x, the rest zero-filled; nb = 0 outside the image
+// or the run) and close the copy group: one group per row, possibly empty.
+__device__ __forceinline__ void fetch_row(const uint8_t *img, int pitch, int h, int x, int nb_lane, int y,
+                                          bool want, uint32_t slot) {
+    const bool ok = want && (unsigned)y < (unsigned)h && nb_lane > 0;
+    const uint8_t *src = ok ? img + (size_t)y * pitch + x : img;
+    cp_async16(slot, src, ok ? nb_lane : 0);
+    cp_async_commit();
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
     uint4 v;
-    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
 }
 
-// The 16 pixels of row y starting at x0 as one 16-byte vector; pixels
-// outside the image (x >= w, y outside [0, h)) read as 0.
-__device__ __forceinline__ uint4 load_vec(const SobelFrame &F, int x0, int y) {
-    uint4 q = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < F.h && x0 < F.w) {
-        q = ldg_nc_v4(F.img + (size_t)y * F.pitch + x0);
-        const int nvalid = F.w - x0;
-        if (nvalid < 16) {
-            uint32_t *v = reinterpret_cast<uint32_t *>(&q);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = nvalid - 4 * i;
-                v[i] &= k >= 4 ? 0xFFFFFFFFu : (k <= 0 ? 0u : ((1u << (8 * k)) - 1u));
-            }
-        }
-    }
-    return q;
+// 16 bytes -> 8 half pairs (p_j, p_{j+8}) in units of 2^-24.
+__device__ __forceinline__ void to_halves(const uint4 q, uint32_t (&Bb)[8]) {
+    const uint32_t t0 = __byte_perm(q.x, q.z, 0x5140);   // p0 p8 p1 p9
+    const uint32_t t1 = __byte_perm(q.x, q.z, 0x7362);   // p2 p10 p3 p11
+    const uint32_t t2 = __byte_perm(q.y, q.w, 0x5140);   // p4 p12 p5 p13
+    const uint32_t t3 = __byte_perm(q.y, q.w, 0x7362);   // p6 p14 p7 p15
+    Bb[0] = __byte_perm(t0, 0u, 0x4140);
+    Bb[1] = __byte_perm(t0, 0u, 0x4342);
+    Bb[2] = __byte_perm(t1, 0u, 0x4140);
+    Bb[3] = __byte_perm(t1, 0u, 0x4342);
+    Bb[4] = __byte_perm(t2, 0u, 0x4140);
+    Bb[5] = __byte_perm(t2, 0u, 0x4342);
+    Bb[6] = __byte_perm(t3, 0u, 0x4140);
+    Bb[7] = __byte_perm(t3, 0u, 0x4342);
 }
 
-// Pixel x0-1 (lane 0) or x0+16 (lane 31) of row y, 0 outside the image.
-__device__ __forceinline__ uint32_t load_edge_byte(const SobelFrame &F, int x, int y) {
-    return (y >= 0 && y < F.h && x >= 0 && x < F.w) ? (uint32_t)F.img[(size_t)y * F.pitch + x] : 0u;
-}
-
-// Assemble a row from its vector and the neighbour bytes, which come from
-// the adjacent lanes (lanes 0 and 31 use the bytes they loaded themselves).
-// All 32 lanes of the warp must call this (shuffles).
-__device__ __forceinline__ Row make_row(uint4 q, uint32_t own_l, uint32_t own_r, int lane) {
-    Row R;
-    R.v[0] = q.x; R.v[1] = q.y; R.v[2] = q.z; R.v[3] = q.w;
-    uint32_t left = __shfl_up_sync(0xFFFFFFFFu, q.w >> 24, 1);
-    uint32_t right = __shfl_down_sync(0xFFFFFFFFu, q.x & 0xFFu, 1);
-    R.l = (lane == 0) ? own_l : left;
-    R.r = (lane == 31) ? own_r : right;
-    return R;
-}
-
-// A row in 16-bit lanes: E[k] = pixels (4k, 4k+2), O[k] = pixels (4k+1, 4k+3)
-// of the lane's 16, plus the neighbour pixels x0-1 (l) and x0+16 (r).
-struct URow {
-    uint32_t E[4], O[4];
-    uint32_t l, r;
+// Sliding state of a lane: row y (Mb) as halves, and Q = P of row y-1
+// (T + M) with its two end words shifted in from the adjacent lanes:
+// Qm0 = Q at (x-1) for word 0, Qp7 = Q at (x+1) for word 7.  The top row
+// itself is not needed: R = B - T = P - Q.
+struct Window {
+    uint32_t Mb[8], Q[8];
+    uint32_t Qm0, Qp7;
 };
 
-__device__ __forceinline__ URow unpack(const Row &R) {
-    URow U;
+// Advance the window by one row (the new bottom row q) and, if EMIT, return
+// the edge mask of the middle row: bit i set iff pixel i of the lane's 16 is
+// an edge.  All 32 lanes of the warp must call this (shuffles).
+template <bool EMIT>
+__device__ __forceinline__ uint32_t step(Window &S, const uint4 q, uint32_t tau) {
+    uint32_t Bb[8], P[8];
+    to_halves(q, Bb);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        U.E[k] = __byte_perm(R.v[k], 0u, 0x4240);   // bytes 0, 2 -> lanes 0, 1
-        U.O[k] = __byte_perm(R.v[k], 0u, 0x4341);   // bytes 1, 3
-    }
-    U.l = R.l;
-    U.r = R.r;
-    return U;
-}
-
-// Eq. 1 and the threshold for the 16 pixels of the middle row, two pixels per
-// 32-bit operation (16-bit lanes, every lane kept non-negative by a bias so
-// no borrow crosses lanes):
-//   S = T + 2M + B (vertical smoothing), D = B - T + 255,
-//   gx(x) = S(x+1) - S(x-1),  gy(x) = D(x-1) + 2D(x) + D(x+1) - 1020,
-//   |gx| + |gy| = max(|gx + gy|, |gx - gy|), tested against thr with four
-//   compares whose result lands in bit 15 of each lane.
-// Returns bit i set iff |Gx| + |Gy| >= thr at pixel x0 + i.
-__device__ __forceinline__ uint32_t sobel16(const URow &T, const URow &M, const URow &B, uint32_t thr) {
-    uint32_t SE[5], SO[5], DE[5], DO[5];
+    for (int j = 0; j < 8; ++j) P[j] = h2_add(S.Mb[j], Bb[j]);   // M + B
+    const uint32_t nx = __shfl_down_sync(kFull, P[0], 1);   // next lane's pixels (16, 24)
+    const uint32_t pv = __shfl_up_sync(kFull, P[7], 1);     // previous lane's pixels (-9, -1)
+    const uint32_t Pp7 = __byte_perm(P[0], nx, 0x5432);     // P at (8, 16): x+1 of word 7
+    const uint32_t Pm0 = __byte_perm(P[7], pv, 0x1076);     // P at (-1, 7): x-1 of word 0
+    uint32_t acc = 0;
+    if (EMIT) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        SE[k] = T.E[k] + B.E[k] + 2u * M.E[k];
-        SO[k] = T.O[k] + B.O[k] + 2u * M.O[k];
-        DE[k] = B.E[k] + 0x00FF00FFu - T.E[k];
-        DO[k] = B.O[k] + 0x00FF00FFu - T.O[k];
-    }
-    // neighbours: S(-1), D(-1) in the high lane of index "-1" (stored at [4] of
-    // the odd arrays), S(16), D(16) in the low lane of index 4 of the even arrays
-    const uint32_t sl = T.l + B.l + 2u * M.l, dl = B.l + 255u - T.l;
-    const uint32_t sr = T.r + B.r + 2u * M.r, dr = B.r + 255u - T.r;
-    SE[4] = sr;
-    DE[4] = dr;
-    SO[4] = sl << 16;
-    DO[4] = dl << 16;
-    const uint32_t K1 = (0x8000u - 2040u - thr) * 0x10001u;
-    const uint32_t K2 = (0x8000u + 2040u - thr) * 0x10001u;
-    uint32_t bits = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t sOm = __funnelshift_l(SO[k == 0 ? 4 : k - 1], SO[k], 16);   // S(4k-1), S(4k+1)
-        const uint32_t dOm = __funnelshift_l(DO[k == 0 ? 4 : k - 1], DO[k], 16);
-        const uint32_t sEp = __funnelshift_r(SE[k], SE[k + 1], 16);               // S(4k+2), S(4k+4)
-        const uint32_t dEp = __funnelshift_r(DE[k], DE[k + 1], 16);
-        // biased by 1020 per lane, in [0, 2040]
-        const uint32_t gxE = SO[k] + 0x03FC03FCu - sOm;   // pixels 4k, 4k+2
-        const uint32_t gxO = sEp + 0x03FC03FCu - SE[k];   // pixels 4k+1, 4k+3
-        const uint32_t gyE = dOm + 2u * DE[k] + DO[k];
-        const uint32_t gyO = DE[k] + 2u * DO[k] + dEp;
-        uint32_t t[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t G = h ? gxO : gxE, Hh = h ? gyO : gyE;
-            const uint32_t s1 = G + Hh;                     // gx + gy + 2040
-            const uint32_t s2 = G + 0x07F807F8u - Hh;       // gx - gy + 2040
-            t[h] = ((s1 + K1) | (K2 - s1) | (s2 + K1) | (K2 - s2)) & 0x80008000u;
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t R = h2_sub(P[j], S.Q[j]);   // B - T, exact
+            const uint32_t Pp = j < 7 ? P[j + 1] : Pp7, Pm = j > 0 ? P[j - 1] : Pm0;
+            const uint32_t Qp = j < 7 ? S.Q[j + 1] : S.Qp7, Qm = j > 0 ? S.Q[j - 1] : S.Qm0;
+            const uint32_t u = h2_add(h2_sub(Pp, Qm), R);
+            const uint32_t w = h2_add(h2_sub(Pm, Qp), R);
+            acc = h2_edge_acc(u, w, tau, 0x00010001u << j, acc);   // + 2^j units per edge
         }
-        // bit 14: pixel 4k, 15: 4k+1, 30: 4k+2, 31: 4k+3
-        const uint32_t w = (t[0] >> 1) | t[1];
-        bits |= ((w >> 14) & 3u) << (4 * k);
-        bits |= ((w >> 28) & 12u) << (4 * k);
     }
-    return bits;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        S.Mb[j] = Bb[j];
+        S.Q[j] = P[j];
+    }
+    S.Qm0 = Pm0;
+    S.Qp7 = Pp7;
+    return __byte_perm(acc, 0u, 0x4420);   // bits 0-7: pixels 0-7, bits 8-15: pixels 8-15
 }
 
 // 4 mask bits -> 4 bytes of 0x00 / 0xFF.
@@ -145,14 +161,14 @@ __device__ __forceinline__ uint32_t spread4(uint32_t nib) {
     return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
 }
 
-template <int R>
-__global__ void __launch_bounds__(kSobelThreads)
+template <bool BIN, bool POOL>
+__global__ void __launch_bounds__(kSobelThreads, 3)
 sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
     // frame of this CTA (binary search over tile_begin)
     const int t = blockIdx.x;
     int lo = 0, hi = L.n - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (L.f[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
     const SobelFrame &F = L.f[lo];
@@ -161,118 +177,157 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
         if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
         if (F.npeaks_init) *F.npeaks_init = 0;
     }
-    const int tx = local % F.tiles_x, ty = local / F.tiles_x;
+    const uint8_t *const img = F.img;
+    const int w = F.w, h = F.h, pitch = F.pitch, strips = F.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = tx * kSobelTileW + lane * 16;
-    const int ya = ty * (R * (kSobelThreads / 32)) + warp * R;
+    const int run_rows = 8 * L.groups;
+    const int runs = (h + run_rows - 1) / run_rows;
+    const int task = local * kSobelWarps + warp;
+    if (task >= strips * runs) return;   // warp-uniform; no block barrier below
+    const int sx = task % strips, sy = task / strips;
+    const int xl = sx * kSobelStripW - 16 + 16 * lane;   // first pixel held by this lane
+    const int y0 = sy * run_rows;
+    const int y_last = min(h, y0 + run_rows);           // one past the last output row
+    const int nb_lane = xl < 0 ? 0 : min(16, max(0, w - xl));   // bytes of a row this lane reads
 
-    // valid-column mask of this lane's 16 pixels
+    // output pixels of this lane: lanes 1..30, inside the image
     uint32_t colmask = 0;
-    if (x0 < F.w) colmask = (F.w - x0 >= 16) ? 0xFFFFu : ((1u << (F.w - x0)) - 1u);
-    if (L.border == LD_BORDER_CLEAR) {
-        if (x0 == 0) colmask &= ~1u;
-        int xr = F.w - 1 - x0;
+    if (lane >= 1 && lane <= 30 && nb_lane > 0) colmask = (1u << nb_lane) - 1u;
+    const bool clear = L.border == LD_BORDER_CLEAR;
+    if (clear) {
+        if (xl == 0) colmask &= ~1u;
+        const int xr = w - 1 - xl;
         if (xr >= 0 && xr < 16) colmask &= ~(1u << xr);
     }
+    const uint32_t tau_u = (uint32_t)(L.threshold + 1) >> 1;   // ceil(T / 2), T in [1, 255]
+    const uint32_t tau = tau_u | (tau_u << 16);                  // in units of 2^-24
 
-    uint32_t masks[R];
+    // this lane's row slots: ring_s[warp][k % kRing][lane * 16]; relative
+    // row k is image row y0 - 1 + k, output row y0 + r needs k = r .. r + 2,
+    // and the run needs k = 0 .. n_k - 1
+    extern __shared__ __align__(16) uint8_t smem_dyn[];
+    uint8_t(*ring_s)[kRing][512] = reinterpret_cast<uint8_t(*)[kRing][512]>(smem_dyn);
+    uint32_t(*stage_s)[kStage] = reinterpret_cast<uint32_t(*)[kStage]>(smem_dyn + kSobelWarps * kRing * 512);
+    const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(&ring_s[warp][0][lane * 16]);
+    const int n_k = y_last - y0 + 2;
 #pragma unroll
-    for (int r = 0; r < R; ++r) masks[r] = 0;
+    for (int k = 0; k < kAhead; ++k)
+        fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + k, k < n_k, slot0 + (uint32_t)(k % kRing) * 512u);
 
-    if (ya < F.h) {   // warp-uniform
-        // issue every load of the strip first (R + 2 rows), then compute
-        uint4 raw[R + 2];
-        uint32_t eb[R + 2];
+    // window primed with rows y0-1 and y0 (the first step only builds P)
+    Window S;
+    {
+        cp_async_wait<kAhead - 1>();
+        to_halves(lds128(slot0), S.Mb);
 #pragma unroll
-        for (int j = 0; j < R + 2; ++j) raw[j] = load_vec(F, x0, ya - 1 + j);
-#pragma unroll
-        for (int j = 0; j < R + 2; ++j)
-            eb[j] = (lane == 0) ? load_edge_byte(F, x0 - 1, ya - 1 + j)
-                                : ((lane == 31) ? load_edge_byte(F, x0 + 16, ya - 1 + j) : 0u);
-        URow top = unpack(make_row(raw[0], eb[0], eb[0], lane));
-        URow mid = unpack(make_row(raw[1], eb[1], eb[1], lane));
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int y = ya + r;
-            URow bot = unpack(make_row(raw[r + 2], eb[r + 2], eb[r + 2], lane));
-            uint32_t bits = (y < F.h) ? (sobel16(top, mid, bot, (uint32_t)L.threshold) & colmask) : 0u;
-            if (L.border == LD_BORDER_CLEAR && (y == 0 || y == F.h - 1)) bits = 0;
-            masks[r] = bits;
-            if (F.bin != nullptr && x0 < F.pitch && y < F.h) {
-                uint4 o;
-                o.x = spread4(bits & 0xF);
-                o.y = spread4((bits >> 4) & 0xF);
-                o.z = spread4((bits >> 8) & 0xF);
-                o.w = spread4((bits >> 12) & 0xF);
-                *reinterpret_cast<uint4 *>(F.bin + (size_t)y * F.pitch + x0) = o;
-            }
-            top = mid;
-            mid = bot;
-        }
+        for (int j = 0; j < 8; ++j) S.Q[j] = 0u;
+        S.Qm0 = S.Qp7 = 0u;
+        fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + kAhead, kAhead < n_k,
+                  slot0 + (uint32_t)(kAhead % kRing) * 512u);
+        cp_async_wait<kAhead - 1>();
+        const uint4 q1 = lds128(slot0 + 512u);
+        fetch_row(img, pitch, h, xl, nb_lane, y0 + kAhead, kAhead + 1 < n_k,
+                  slot0 + (uint32_t)((kAhead + 1) % kRing) * 512u);
+        step<false>(S, q1, tau);
     }
 
-    // 8x8 edge-count pool: the CTA's tile (512 px x 8R rows) is a whole number
-    // of 8x8 blocks, so each block is counted in this CTA's shared memory and
-    // written once.  A warp's R rows lie in one 8-row block (ya is a multiple of
-    // R, R divides 8); a lane's 16 pixels are 2 blocks.
-    __shared__ uint32_t pool_s[R][kSobelTileW / 8];
-    if (F.pool != nullptr) {
-        for (int i = threadIdx.x; i < R * (kSobelTileW / 8); i += kSobelThreads) (&pool_s[0][0])[i] = 0;
-        __syncthreads();
-        if (ya < F.h && x0 < F.w) {
+    for (int yg = y0; yg < y_last; yg += 8) {   // warp-uniform
+        uint32_t m2[4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = yg + r;
+            const int k = y - y0 + 2;             // bottom row of output row y
+            cp_async_wait<kAhead - 1>();
+            const uint4 q = lds128(slot0 + (uint32_t)(k % kRing) * 512u);
+            const int kn = k + kAhead;            // next row to fetch
+            fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + kn, kn < n_k, slot0 + (uint32_t)(kn % kRing) * 512u);
+            uint32_t mk = step<true>(S, q, tau) & colmask;
+            if (y >= y_last || (clear && (y == 0 || y == h - 1))) mk = 0;
+            if (r & 1) m2[r >> 1] |= mk << 16; else m2[r >> 1] = mk;
+            if (BIN && y < y_last && lane >= 1 && lane <= 30 && xl < pitch) {
+                uint4 o;
+                o.x = spread4(mk & 0xF);
+                o.y = spread4((mk >> 4) & 0xF);
+                o.z = spread4((mk >> 8) & 0xF);
+                o.w = spread4((mk >> 12) & 0xF);
+                *reinterpret_cast<uint4 *>(F.bin + (size_t)y * pitch + xl) = o;
+            }
+        }
+
+        // 8x8 edge counts: this lane's two blocks of the 8-row group
+        if (POOL && lane >= 1 && lane <= 30) {
             uint32_t c0 = 0, c1 = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                c0 += __popc(masks[r] & 0xFFu);
-                c1 += __popc(masks[r] >> 8);
+            for (int k = 0; k < 4; ++k) {
+                c0 += __popc(m2[k] & 0x00FF00FFu);
+                c1 += __popc(m2[k] & 0xFF00FF00u);
             }
-            const int br = (warp * R) >> 3;
-            if (c0) atomicAdd(&pool_s[br][lane * 2], c0);
-            if (c1) atomicAdd(&pool_s[br][lane * 2 + 1], c1);
+            const int pw = (w + 7) >> 3;
+            const int bx = xl >> 3;
+            uint8_t *row = F.pool + (size_t)(yg >> 3) * pw;
+            if (bx < pw) row[bx] = (uint8_t)c0;
+            if (bx + 1 < pw) row[bx + 1] = (uint8_t)c1;
         }
-        __syncthreads();
-        const int pw = (F.w + 7) >> 3, ph = (F.h + 7) >> 3;
-        const int bx0 = tx * (kSobelTileW / 8), by0 = (ty * R * (kSobelThreads / 32)) >> 3;
-        for (int i = threadIdx.x; i < R * (kSobelTileW / 8); i += kSobelThreads) {
-            const int br = i / (kSobelTileW / 8), bc = i % (kSobelTileW / 8);
-            if (by0 + br < ph && bx0 + bc < pw) F.pool[(size_t)(by0 + br) * pw + bx0 + bc] = (uint8_t)pool_s[br][bc];
-        }
-    }
 
-    // block-wide exclusive prefix of the edge counts, one atomic per CTA
-    int cnt = 0;
+        // the group's edges: warp prefix sum, one atomic, then each lane's own
+        const int cnt = __popc(m2[0]) + __popc(m2[1]) + __popc(m2[2]) + __popc(m2[3]);
+        int incl = cnt;
 #pragma unroll
-    for (int r = 0; r < R; ++r) cnt += __popc(masks[r]);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    __shared__ int warp_tot[kSobelThreads / 32];
-    __shared__ int cta_base;
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < kSobelThreads / 32; ++w) {
-            int v = warp_tot[w];
-            warp_tot[w] = tot;
-            tot += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
         }
-        cta_base = tot ? atomicAdd(F.count, tot) : 0;
-    }
-    __syncthreads();
-    int64_t pos = (int64_t)cta_base + warp_tot[warp] + (incl - cnt);
+        const int tot = __shfl_sync(kFull, incl, 31);
+        if (tot == 0) continue;   // warp-uniform
+        int base = 0;
+        if (lane == 31) base = atomicAdd(F.count, tot);
+        base = __shfl_sync(kFull, base, 31);
+        const int64_t pos0 = (int64_t)base + (incl - cnt);
+        if (tot <= kStage && (int64_t)base + tot <= F.cap) {
+            // each lane writes its edges to the warp's staging slots, then the
+            // warp copies them out with coalesced stores
+            uint32_t *st = &stage_s[warp][incl - cnt];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        uint32_t bits = masks[r];
-        const uint32_t yy = (uint32_t)(ya + r) << 16;
-        while (bits) {
-            int i = __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (pos < F.cap) F.edges[pos] = yy | (uint32_t)(x0 + i);
-            ++pos;
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = m2[k];
+                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
+                while (m) {
+                    const int i = 31 - __clz(m);
+                    m ^= 1u << i;
+                    // bit i < 16: pixel i of row yg+2k; i >= 16: pixel i-16 of the next row
+                    *st++ = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
+                }
+            }
+            __syncwarp();
+            uint32_t *dst = F.edges + base;
+            for (int i = lane; i < tot; i += 32) dst[i] = stage_s[warp][i];
+            __syncwarp();
+        } else if ((int64_t)base + tot <= F.cap) {   // warp-uniform: every slot fits
+            uint32_t *dst = F.edges + pos0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = m2[k];
+                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
+                while (m) {
+                    const int i = 31 - __clz(m);
+                    m ^= 1u << i;
+                    // bit i < 16: pixel i of row yg+2k; i >= 16: pixel i-16 of the next row
+                    *dst++ = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
+                }
+            }
+        } else {                                // overflow: write what fits, count all
+            int64_t pos = pos0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = m2[k];
+                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
+                while (m) {
+                    const int i = 31 - __clz(m);
+                    m ^= 1u << i;
+                    if (pos < F.cap) F.edges[pos] = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
+                    ++pos;
+                }
+            }
         }
     }
 }
@@ -281,12 +336,16 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
 
 cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s) {
     if (n_ctas <= 0) return cudaSuccess;
-    switch (L.rows_per_warp) {
-        case 2: sobel_bin_edges_kernel<2><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
-        case 4: sobel_bin_edges_kernel<4><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
-        case 8: sobel_bin_edges_kernel<8><<<n_ctas, kSobelThreads, 0, s>>>(L); break;
-        default: return cudaErrorInvalidValue;
-    }
+    if (L.groups < 1 || L.groups > 64) return cudaErrorInvalidValue;
+    // the optional outputs are uniform over a launch (all frames or none)
+    const bool bin = L.f[0].bin != nullptr, pool = L.f[0].pool != nullptr;
+    for (int i = 1; i < L.n; ++i)
+        if ((L.f[i].bin != nullptr) != bin || (L.f[i].pool != nullptr) != pool) return cudaErrorInvalidValue;
+    auto kern = bin ? (pool ? sobel_bin_edges_kernel<true, true> : sobel_bin_edges_kernel<true, false>)
+                    : (pool ? sobel_bin_edges_kernel<false, true> : sobel_bin_edges_kernel<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSobelSmem);
+    if (e != cudaSuccess) return e;
+    kern<<<n_ctas, kSobelThreads, kSobelSmem, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 
 Integer work, so every comparison is bit-exact: the 0/255 map byte for byte,
 the edge list as a set (its order is unspecified), the accumulator cell for
-cell, the peaks entry for entry.  Sizes span several Sobel tiles (512 px x
-16..64 rows) and several theta tiles with ragged tails.
+cell, the peaks entry for entry.  Sizes span several Sobel warp strips (480
+output pixels wide, runs of 8-row groups) with ragged right and bottom
+edges, and several theta tiles with ragged tails.
 """
 import numpy as np
 import pytest
@@ -33,7 +34,7 @@ def _gpu_sobel(ctx, ld, img, w, threshold=128, border=0, cap=0):
 
 SOBEL_CASES = [
     (3, 3, 1), (17, 5, 2), (640, 480, 3), (513, 67, 4), (1000, 129, 5), (1920, 1080, 6), (31, 300, 7),
-    (1024, 17, 8),
+    (1024, 17, 8), (480, 9, 9), (481, 33, 10), (961, 40, 11), (959, 8, 12),
 ]
 
 
