@@ -258,7 +258,8 @@ LD_API ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32
  * conv weights bf16 [Cout][3][3][Cin]; biases, head, losses and gradients
  * fp32; "dy" is the gradient with respect to a layer's ReLU output.
  * Supported convs: 1->16 (stride 1), 16->32 and 32->32 (stride 1 or 2), all
- * 3x3 with zero padding 1; output size (h + 2 - 3) / stride + 1.
+ * 3x3 with zero padding 1; output size (h + 2 - 3) / stride + 1.  Sizes:
+ * w >= 2 and h * w * w < 2^32 (else LD_ERR_INVALID).
  */
 /* y = relu(conv(x, w) + b). */
 LD_API ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w,

@@ -55,39 +55,37 @@ __device__ __forceinline__ uint32_t relu_mask1(uint32_t dyb, uint32_t yb) { retu
 // ------------------------------------------------------------------ conv1 (Cin = 1)
 
 // y[p][16] = relu(b + sum_tap w[co][tap] * x[pix(p, tap)] / 64), x uint8 edge counts [n][h][w].
-__global__ void __launch_bounds__(256) conv1_fwd_kernel(const uint8_t *x, int n, int h, int w, const bf16 *wt,
+// Block 32 x 8 pixels of one image (grid x, y over the image, z = image).
+__global__ void __launch_bounds__(256) conv1_fwd_kernel(const uint8_t *x, int h, int w, const bf16 *wt,
                                                        const float *b, bf16 *y) {
     __shared__ float ws[16 * 9], bs[16];
-    for (int i = threadIdx.x; i < 16 * 9; i += blockDim.x) ws[i] = __bfloat162float(wt[i]);
-    if (threadIdx.x < 16) bs[threadIdx.x] = b[threadIdx.x];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int i = tid; i < 16 * 9; i += 256) ws[i] = __bfloat162float(wt[i]);
+    if (tid < 16) bs[tid] = b[tid];
     __syncthreads();
-    const int64_t P = (int64_t)n * h * w;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const int img = (int)(p / ((int64_t)h * w));
-        const int rem = (int)(p - (int64_t)img * h * w);
-        const int oy = rem / w, ox = rem - (rem / w) * w;
-        float v[9];
+    const int ox = blockIdx.x * 32 + threadIdx.x, oy = blockIdx.y * 8 + threadIdx.y, img = blockIdx.z;
+    if (ox >= w || oy >= h) return;
+    const uint8_t *xi = x + (int64_t)img * h * w;
+    float v[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int iy = oy + t / 3 - 1, ix = ox + t % 3 - 1;
+        v[t] = (iy >= 0 && iy < h && ix >= 0 && ix < w) ? (float)xi[iy * w + ix] * (1.f / 64.f) : 0.f;
+    }
+    uint32_t out[8];
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+        float s0 = bs[c], s1 = bs[c + 1];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            const int iy = oy + t / 3 - 1, ix = ox + t % 3 - 1;
-            v[t] = (iy >= 0 && iy < h && ix >= 0 && ix < w) ? (float)x[((int64_t)img * h + iy) * w + ix] * (1.f / 64.f)
-                                                             : 0.f;
+            s0 += ws[c * 9 + t] * v[t];
+            s1 += ws[(c + 1) * 9 + t] * v[t];
         }
-        uint32_t out[8];
-#pragma unroll
-        for (int c = 0; c < 16; c += 2) {
-            float s0 = bs[c], s1 = bs[c + 1];
-#pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                s0 += ws[c * 9 + t] * v[t];
-                s1 += ws[(c + 1) * 9 + t] * v[t];
-            }
-            out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(y + p * 16);
-        dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-        dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+        out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
     }
+    uint4 *dst = reinterpret_cast<uint4 *>(y + (((int64_t)img * h + oy) * w + ox) * 16);
+    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
 }
 
 // dw1[co][tap] += sum_p dy_pre[p][co] * x[pix(p, tap)],  db1[co] += sum_p dy_pre[p][co].
@@ -128,15 +126,18 @@ __global__ void __launch_bounds__(256) conv1_wgrad_kernel(const uint8_t *x, cons
 
 // ------------------------------------------------------------------ conv2..4 on tensor cores
 
+// Geometry of one layer.  Kernels index pixels within one image (grid y =
+// image) and split a pixel index into (row, column) by a multiply-high with
+// a precomputed magic number: floor(q / d) = umulhi(q, ceil(2^32 / d)) for
+// q * d < 2^32 (here q < 2^16 and d < 2^16).
 struct ConvGeom {
     int n, h, w, oh, ow, stride;
+    uint32_t w_magic, ow_magic;
 };
 
-__device__ __forceinline__ void decode(int64_t p, int hh, int ww, int &img, int &yy, int &xx) {
-    img = (int)(p / ((int64_t)hh * ww));
-    const int rem = (int)(p - (int64_t)img * hh * ww);
-    yy = rem / ww;
-    xx = rem - yy * ww;
+__device__ __forceinline__ void split_px(int q, int ww, uint32_t magic, int &yy, int &xx) {
+    yy = (int)__umulhi((uint32_t)q, magic);
+    xx = q - yy * ww;
 }
 
 // Forward: each warp computes 16 output pixels x COUT channels.
@@ -145,17 +146,20 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16 *x, ConvGeom G
                                                       bf16 *y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int64_t M = (int64_t)G.n * G.oh * G.ow;
-    const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+    const int M = G.oh * G.ow;   // output pixels of one image
+    const int m0 = (blockIdx.x * 4 + warp) * 16;
     if (m0 >= M) return;
+    const int im = blockIdx.y;
     int img[2], oy[2], ox[2];
     bool rv[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int64_t p = m0 + g + 8 * r;
+        const int p = m0 + g + 8 * r;
         rv[r] = p < M;
-        decode(rv[r] ? p : 0, G.oh, G.ow, img[r], oy[r], ox[r]);
+        img[r] = im;
+        split_px(rv[r] ? p : 0, G.ow, G.ow_magic, oy[r], ox[r]);
     }
+    bf16 *yi = y + (int64_t)im * M * COUT;
     float acc[COUT / 8][4];
 #pragma unroll
     for (int nt = 0; nt < COUT / 8; ++nt)
@@ -191,10 +195,10 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16 *x, ConvGeom G
         const int c = nt * 8 + 2 * t;
         const float b0 = b[c], b1 = b[c + 1];
         if (rv[0])
-            *reinterpret_cast<uint32_t *>(y + (m0 + g) * COUT + c) =
+            *reinterpret_cast<uint32_t *>(yi + (int64_t)(m0 + g) * COUT + c) =
                 to_bf16x2(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
         if (rv[1])
-            *reinterpret_cast<uint32_t *>(y + (m0 + g + 8) * COUT + c) =
+            *reinterpret_cast<uint32_t *>(yi + (int64_t)(m0 + g + 8) * COUT + c) =
                 to_bf16x2(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
     }
 }
@@ -207,17 +211,20 @@ __global__ void __launch_bounds__(128) conv_dgrad_kernel(const bf16 *y, const bf
                                                         bf16 *dx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int64_t M = (int64_t)G.n * G.h * G.w;
-    const int64_t m0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
+    const int M = G.h * G.w;   // input pixels of one image
+    const int m0 = (blockIdx.x * 4 + warp) * 16;
     if (m0 >= M) return;
+    const int im = blockIdx.y;
     int img[2], iy[2], ix[2];
     bool rv[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int64_t p = m0 + g + 8 * r;
+        const int p = m0 + g + 8 * r;
         rv[r] = p < M;
-        decode(rv[r] ? p : 0, G.h, G.w, img[r], iy[r], ix[r]);
+        img[r] = im;
+        split_px(rv[r] ? p : 0, G.w, G.w_magic, iy[r], ix[r]);
     }
+    bf16 *dxi = dx + (int64_t)im * M * CIN;
     float acc[CIN / 8][4];
 #pragma unroll
     for (int nt = 0; nt < CIN / 8; ++nt)
@@ -259,8 +266,10 @@ __global__ void __launch_bounds__(128) conv_dgrad_kernel(const bf16 *y, const bf
 #pragma unroll
     for (int nt = 0; nt < CIN / 8; ++nt) {
         const int c = nt * 8 + 2 * t;
-        if (rv[0]) *reinterpret_cast<uint32_t *>(dx + (m0 + g) * CIN + c) = to_bf16x2(acc[nt][0], acc[nt][1]);
-        if (rv[1]) *reinterpret_cast<uint32_t *>(dx + (m0 + g + 8) * CIN + c) = to_bf16x2(acc[nt][2], acc[nt][3]);
+        if (rv[0])
+            *reinterpret_cast<uint32_t *>(dxi + (int64_t)(m0 + g) * CIN + c) = to_bf16x2(acc[nt][0], acc[nt][1]);
+        if (rv[1])
+            *reinterpret_cast<uint32_t *>(dxi + (int64_t)(m0 + g + 8) * CIN + c) = to_bf16x2(acc[nt][2], acc[nt][3]);
     }
 }
 
@@ -275,9 +284,11 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf
     constexpr int NTW = (NT + 3) / 4;          // tiles per warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int64_t P = (int64_t)G.n * G.oh * G.ow;
-    const int64_t p_begin = (int64_t)blockIdx.x * chunk;
-    const int64_t p_end = (p_begin + chunk < P) ? p_begin + chunk : P;
+    // pixels [p_begin, p_end) of image blockIdx.y, as global pixel indices
+    const int Mi = G.oh * G.ow;
+    const int64_t ibase = (int64_t)blockIdx.y * Mi;
+    const int64_t p_begin = ibase + (int64_t)blockIdx.x * chunk;
+    const int64_t p_end = (blockIdx.x * chunk + chunk < Mi) ? p_begin + chunk : ibase + Mi;
     float acc[COUT / 16][NTW][4];
 #pragma unroll
     for (int mt = 0; mt < COUT / 16; ++mt)
@@ -312,7 +323,10 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf
         // pixel coordinates of the 4 pixels this thread reads for B
         int img[4], oy[4], ox[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) decode(pv[q] ? pk[q] : 0, G.oh, G.ow, img[q], oy[q], ox[q]);
+        for (int q = 0; q < 4; ++q) {
+            img[q] = blockIdx.y;
+            split_px(pv[q] ? (int)(pk[q] - ibase) : 0, G.ow, G.ow_magic, oy[q], ox[q]);
+        }
 #pragma unroll
         for (int j = 0; j < NTW; ++j) {
             const int nt = warp + 4 * j;
@@ -367,8 +381,8 @@ __device__ __forceinline__ int bin_hi(int i, int n_in, int n_out) { return ((i +
 
 // One CTA per sample: feat[1024] (adaptive average pool, (bin row, bin col,
 // channel) order), logits[44] = wh . feat + bh.
-__global__ void __launch_bounds__(256) pool_head_fwd_kernel(const bf16 *y4, int h4, int w4, const float *wh,
-                                                           const float *bh, float *feat, float *logits) {
+__global__ void __launch_bounds__(1024) pool_head_fwd_kernel(const bf16 *y4, int h4, int w4, const float *wh,
+                                                            const float *bh, float *feat, float *logits) {
     __shared__ float f[kFeat];
     const int s = blockIdx.x;
     const bf16 *src = y4 + (int64_t)s * h4 * w4 * kC4;
@@ -505,25 +519,33 @@ ld_status bad(const char *msg) {
 bool shape_ok(int cin, int cout) {
     return (cin == 1 && cout == 16) || (cin == 16 && cout == 32) || (cin == 32 && cout == 32);
 }
+uint32_t magic_of(int d) { return (uint32_t)(((uint64_t)1 << 32) / (uint64_t)d + 1); }
+// the magic-number split of a pixel index needs w >= 2 and (h*w)*w < 2^32
+bool size_ok(int h, int w) { return w >= 2 && (uint64_t)h * (uint64_t)w * (uint64_t)w < ((uint64_t)1 << 32); }
+ConvGeom geom(int n, int h, int w, int stride) {
+    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride, 0u, 0u};
+    G.w_magic = magic_of(w);
+    G.ow_magic = magic_of(G.ow);
+    return G;
+}
 }  // namespace
 
 extern "C" {
 
 ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,
                              int32_t stride, const void *d_w, const float *d_b, void *d_y, void *stream) {
-    if (!d_x || !d_w || !d_b || !d_y || n < 1 || h < 1 || w < 1 || (stride != 1 && stride != 2) ||
+    if (!d_x || !d_w || !d_b || !d_y || n < 1 || h < 1 || !size_ok(h, w) || (stride != 1 && stride != 2) ||
         !shape_ok(cin, cout))
         return bad("ld_conv3x3_forward: bad argument (supported: 1->16, 16->32, 32->32; stride 1 or 2)");
     cudaStream_t s = (cudaStream_t)stream;
     if (cin == 1) {
         if (stride != 1) return bad("ld_conv3x3_forward: the 1-channel layer has stride 1");
-        conv1_fwd_kernel<<<blocks_for((int64_t)n * h * w, 256), 256, 0, s>>>(
-            (const uint8_t *)d_x, n, h, w, (const bf16 *)d_w, d_b, (bf16 *)d_y);
+        conv1_fwd_kernel<<<dim3((w + 31) / 32, (h + 7) / 8, n), dim3(32, 8), 0, s>>>(
+            (const uint8_t *)d_x, h, w, (const bf16 *)d_w, d_b, (bf16 *)d_y);
         return launch_status("conv1_fwd");
     }
-    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride};
-    const int64_t M = (int64_t)n * G.oh * G.ow;
-    const int grid = (int)((M + 63) / 64);
+    const ConvGeom G = geom(n, h, w, stride);
+    const dim3 grid((G.oh * G.ow + 63) / 64, n);
     if (cin == 16)
         conv_fwd_kernel<16, 32><<<grid, 128, 0, s>>>((const bf16 *)d_x, G, (const bf16 *)d_w, d_b, (bf16 *)d_y);
     else
@@ -534,7 +556,7 @@ ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w, i
 ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,
                               int32_t stride, const void *d_w, const void *d_y, const void *d_dy, void *d_dx,
                               float *d_dw, float *d_db, void *stream) {
-    if (!d_x || !d_w || !d_y || !d_dy || !d_dw || !d_db || n < 1 || h < 1 || w < 1 ||
+    if (!d_x || !d_w || !d_y || !d_dy || !d_dw || !d_db || n < 1 || h < 1 || !size_ok(h, w) ||
         (stride != 1 && stride != 2) || !shape_ok(cin, cout))
         return bad("ld_conv3x3_backward: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -544,10 +566,9 @@ ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, 
             (const uint8_t *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy, n, h, w, d_dw, d_db);
         return launch_status("conv1_wgrad");
     }
-    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride};
-    const int64_t P = (int64_t)n * G.oh * G.ow;
+    const ConvGeom G = geom(n, h, w, stride);
     const int chunk = 2048;
-    const int wgrid = (int)((P + chunk - 1) / chunk);
+    const dim3 wgrid((G.oh * G.ow + chunk - 1) / chunk, n);
     if (cin == 16)
         conv_wgrad_kernel<16, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
                                                         G, chunk, d_dw, d_db);
@@ -556,8 +577,7 @@ ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, 
                                                         G, chunk, d_dw, d_db);
     ld_status st = launch_status("conv_wgrad");
     if (st != LD_OK || !d_dx) return st;
-    const int64_t Mi = (int64_t)n * h * w;
-    const int dgrid = (int)((Mi + 63) / 64);
+    const dim3 dgrid((h * w + 63) / 64, n);
     if (cin == 16)
         conv_dgrad_kernel<16, 32><<<dgrid, 128, 0, s>>>((const bf16 *)d_y, (const bf16 *)d_dy, G,
                                                         (const bf16 *)d_w, (bf16 *)d_dx);
@@ -571,8 +591,8 @@ ld_status ld_pool_head_forward(const void *d_y4, int32_t n, int32_t h4, int32_t 
                                const float *d_bh, float *d_feat, float *d_logits, void *stream) {
     if (!d_y4 || !d_wh || !d_bh || !d_feat || !d_logits || n < 1 || h4 < kPH || w4 < kPW)
         return bad("ld_pool_head_forward: bad argument");
-    pool_head_fwd_kernel<<<n, 256, 0, (cudaStream_t)stream>>>((const bf16 *)d_y4, h4, w4, d_wh, d_bh, d_feat,
-                                                              d_logits);
+    pool_head_fwd_kernel<<<n, 1024, 0, (cudaStream_t)stream>>>((const bf16 *)d_y4, h4, w4, d_wh, d_bh, d_feat,
+                                                               d_logits);
     return launch_status("pool_head_fwd");
 }
 
