@@ -265,6 +265,11 @@ LD_API ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32
 LD_API ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w,
                                     int32_t cin, int32_t cout, int32_t stride,
                                     const void *d_w, const float *d_b, void *d_y, void *stream);
+/* Faults recorded on CUDA device `device` by the tensor-core forward
+ * convolutions (16->32 and 32->32) since the previous call: a bounded wait
+ * for the tensor cores that gave up, after which that layer's output is
+ * unspecified.  Reads and clears; *flags = 0 when there was none. */
+LD_API ld_status ld_conv_faults(int32_t device, int32_t *flags);
 /* From dy (bf16, w.r.t. the ReLU output y): dw += dL/dw, db += dL/db (fp32,
  * accumulated: zero them first) and, if d_dx != NULL, dx = dL/dx (bf16).  The
  * 1-channel layer takes d_dx = NULL. */

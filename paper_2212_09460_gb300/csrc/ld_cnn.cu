@@ -7,11 +7,12 @@
 //   conv4 3x3 s2 32->32, each + bias + ReLU | adaptive average pool to 4x8 |
 //   linear 1024 -> 44 logits (36 theta bands + 8 row bands) | BCE loss.
 //
-// conv2..4 (forward, input gradient, weight gradient) are implicit GEMMs on
-// the bf16 tensor cores with fp32 accumulation (mma.sync m16n8k16): forward
-// M = output pixels, N = Cout, K = 9*Cin; input gradient M = input pixels,
-// N = Cin, K = 9*Cout (transposed stride-2 taps); weight gradient M = Cout,
-// N = 9*Cin, K = pixels (split over CTAs, fp32 atomics).  conv1 has a single
+// conv2..4 are implicit GEMMs on the bf16 tensor cores with fp32
+// accumulation: the forward pass (M = output pixels, N = Cout, K = 9*Cin) on
+// tcgen05 with a tensor-memory accumulator (ld_conv_tc.cu); the input
+// gradient (M = input pixels, N = Cin, K = 9*Cout, transposed stride-2 taps)
+// and the weight gradient (M = Cout, N = 9*Cin, K = pixels, split over CTAs,
+// fp32 atomics) with warp-level mma.sync m16n8k16 here.  conv1 has a single
 // input channel (K = 9) and runs on the CUDA cores.  Every output of the
 // forward pass depends only on its own sample, in a fixed summation order,
 // so a frame's logits are the same alone and in any batch.
@@ -138,69 +139,6 @@ struct ConvGeom {
 __device__ __forceinline__ void split_px(int q, int ww, uint32_t magic, int &yy, int &xx) {
     yy = (int)__umulhi((uint32_t)q, magic);
     xx = q - yy * ww;
-}
-
-// Forward: each warp computes 16 output pixels x COUT channels.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16 *x, ConvGeom G, const bf16 *wt, const float *b,
-                                                      bf16 *y) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int M = G.oh * G.ow;   // output pixels of one image
-    const int m0 = (blockIdx.x * 4 + warp) * 16;
-    if (m0 >= M) return;
-    const int im = blockIdx.y;
-    int img[2], oy[2], ox[2];
-    bool rv[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int p = m0 + g + 8 * r;
-        rv[r] = p < M;
-        img[r] = im;
-        split_px(rv[r] ? p : 0, G.ow, G.ow_magic, oy[r], ox[r]);
-    }
-    bf16 *yi = y + (int64_t)im * M * COUT;
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int nt = 0; nt < COUT / 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-        const bf16 *src[2];
-        bool ok[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int iy = oy[r] * G.stride + ky - 1, ix = ox[r] * G.stride + kx - 1;
-            ok[r] = rv[r] && iy >= 0 && iy < G.h && ix >= 0 && ix < G.w;
-            src[r] = x + (((int64_t)img[r] * G.h + (ok[r] ? iy : 0)) * G.w + (ok[r] ? ix : 0)) * CIN;
-        }
-#pragma unroll
-        for (int cb = 0; cb < CIN / 16; ++cb) {
-            uint32_t a[4];
-            a[0] = ok[0] ? ld_u32(src[0] + cb * 16 + 2 * t) : 0u;
-            a[1] = ok[1] ? ld_u32(src[1] + cb * 16 + 2 * t) : 0u;
-            a[2] = ok[0] ? ld_u32(src[0] + cb * 16 + 2 * t + 8) : 0u;
-            a[3] = ok[1] ? ld_u32(src[1] + cb * 16 + 2 * t + 8) : 0u;
-#pragma unroll
-            for (int nt = 0; nt < COUT / 8; ++nt) {
-                const bf16 *wp = wt + ((int64_t)(nt * 8 + g) * 9 + tap) * CIN + cb * 16;
-                mma_bf16(acc[nt], a, ld_u32(wp + 2 * t), ld_u32(wp + 2 * t + 8));
-            }
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < COUT / 8; ++nt) {
-        const int c = nt * 8 + 2 * t;
-        const float b0 = b[c], b1 = b[c + 1];
-        if (rv[0])
-            *reinterpret_cast<uint32_t *>(yi + (int64_t)(m0 + g) * COUT + c) =
-                to_bf16x2(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
-        if (rv[1])
-            *reinterpret_cast<uint32_t *>(yi + (int64_t)(m0 + g + 8) * COUT + c) =
-                to_bf16x2(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
-    }
 }
 
 // Input gradient: each warp computes 16 input pixels x CIN channels of
@@ -545,12 +483,13 @@ ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32_t w, i
         return launch_status("conv1_fwd");
     }
     const ConvGeom G = geom(n, h, w, stride);
-    const dim3 grid((G.oh * G.ow + 63) / 64, n);
-    if (cin == 16)
-        conv_fwd_kernel<16, 32><<<grid, 128, 0, s>>>((const bf16 *)d_x, G, (const bf16 *)d_w, d_b, (bf16 *)d_y);
-    else
-        conv_fwd_kernel<32, 32><<<grid, 128, 0, s>>>((const bf16 *)d_x, G, (const bf16 *)d_w, d_b, (bf16 *)d_y);
-    return launch_status("conv_fwd");
+    const ConvTcGeom T{n, h, w, G.oh, G.ow, stride};
+    const cudaError_t e = launch_conv_fwd_tc(d_x, T, cin, d_w, d_b, d_y, s);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
+    return launch_status("conv_fwd_tc");
 }
 
 ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,

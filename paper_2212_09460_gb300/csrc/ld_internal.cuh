@@ -175,6 +175,14 @@ int hough_max_pairs(int n_rho);
 // Smallest compiled tile size >= pairs (0 if none).
 int hough_template_pairs(int pairs);
 
+// Proposal network: forward 3x3 convolution on the tcgen05 tensor cores
+// (cin 16 or 32 -> 32 channels, NHWC bf16, + bias, ReLU).
+struct ConvTcGeom {
+    int n, h, w, oh, ow, stride;
+};
+cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, const void *w, const float *b, void *y,
+                               cudaStream_t s);
+
 // Proposal: band logits -> per-frame ascending active-pair lists, counts,
 // fallback flags, tile counts and the device prefix unit_begin [n + 1].
 cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p_band, float p_fallback, int margin,

@@ -102,6 +102,7 @@ _SIGS = {
     "ld_bce_loss": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P],
     "ld_adam_step": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, ctypes.c_int32, _P, _P],
+    "ld_conv_faults": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     "ld_ctx_enable_timing": [_P, ctypes.c_int],
     "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
 }
@@ -294,6 +295,13 @@ def ld_detect_batch_proposal(ctx, frames, p, net, q, d_peaks, d_n_peaks, d_statu
 
 def ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream) -> None:
     _check(load().ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream))
+
+
+def ld_conv_faults(device: int = 0) -> int:
+    """Tensor-core convolution faults recorded on `device` since the last call (read and cleared)."""
+    v = ctypes.c_int32(0)
+    _check(load().ld_conv_faults(device, ctypes.byref(v)))
+    return v.value
 
 
 def ld_conv3x3_backward(d_x, n, h, w, cin, cout, stride, d_w, d_y, d_dy, d_dx, d_dw, d_db, stream) -> None:

@@ -62,6 +62,7 @@ def test_forward_matches_oracle(ldlib):
     net = _net(ldlib, params)
     acts = net.forward(torch.from_numpy(x).cuda())
     torch.cuda.synchronize()
+    assert ldlib.ld_conv_faults(0) == 0          # no tensor-core wait gave up
     ref_logits, ref_acts = cnn.forward(params, x.astype(np.float64) / 64.0, keep=True)
     for i in range(4):
         got = acts.ys[i].float().cpu().numpy().transpose(0, 3, 1, 2)
@@ -111,3 +112,24 @@ def test_training_reduces_loss(ldlib):
     for _ in range(40):
         last = float(net.train_step(x, tgt, lr=3e-3).item())
     assert last < 0.7 * first
+
+
+@pytest.mark.parametrize("cin,stride,h,w", [(16, 2, 37, 41), (32, 2, 20, 23), (16, 1, 19, 13), (32, 1, 17, 18),
+                                            (32, 2, 135, 240)])
+def test_tensor_core_conv_matches_oracle(ldlib, cin, stride, h, w):
+    # every (channels, stride) form of the tcgen05 forward convolution, at
+    # sizes with ragged 16 x 8 output tiles, against float64 conv + ReLU
+    rng = np.random.default_rng(cin * 100 + stride * 10 + h)
+    x = torch.from_numpy(rng.standard_normal((2, h, w, cin)).astype(np.float32)).to(torch.bfloat16)
+    wt = torch.from_numpy(rng.uniform(-0.2, 0.2, (32, 3, 3, cin)).astype(np.float32)).to(torch.bfloat16)
+    b = torch.from_numpy(rng.uniform(-0.1, 0.1, 32).astype(np.float32))
+    oh, ow = (h - 1) // stride + 1, (w - 1) // stride + 1
+    y = torch.empty((2, oh, ow, 32), dtype=torch.bfloat16, device="cuda")
+    xd, wd, bd = x.cuda().contiguous(), wt.cuda().contiguous(), b.cuda()
+    ldlib.ld_conv3x3_forward(xd.data_ptr(), 2, h, w, cin, 32, stride, wd.data_ptr(), bd.data_ptr(), y.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert ldlib.ld_conv_faults(0) == 0
+    ref = torch.nn.functional.conv2d(x.double().permute(0, 3, 1, 2), wt.double().permute(0, 3, 1, 2),
+                                     b.double(), stride=stride, padding=1).relu().permute(0, 2, 3, 1).numpy()
+    assert _rel(y.float().cpu().numpy(), ref) < 1e-2
