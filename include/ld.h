@@ -344,6 +344,17 @@ LD_API ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames,
                                           int32_t *d_fallback, int32_t *d_active_pairs,
                                           void *stream);
 
+/* Inference of the proposal network on n edge-count maps d_pool [n][ph][pw]
+ * (uint8 counts 0..64 as ld_edge_pool_batch writes them): the network of the
+ * layer calls here, with conv1 fused into conv2 on the tensor cores (its
+ * output never leaves the SM; the logits are bit-identical to the layer calls),
+ * then conv3, conv4 and pool + head.  d_logits: fp32 [n][44].  Scratch lives in
+ * the context.  The map must leave conv4's output at least 4 x 8. */
+LD_API ld_status ld_proposal_logits(ld_ctx *ctx, const uint8_t *d_pool, int32_t n, int32_t ph,
+                                    int32_t pw, const ld_proposal_net *net, float *d_logits,
+                                    void *stream);
+
+
 /*
  * Synthetic input frames, generated on the device (for training the proposal
  * network and feeding the serving loop).  Not a step of the method: the

@@ -839,6 +839,64 @@ ld_status ld_edge_pool_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, c
     return LD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Layer sizes of the proposal network for an edge-count map ph x pw: conv1
+// keeps the size, conv2-4 halve it (stride 2).  False if conv4's output is
+// smaller than the 4 x 8 pooling grid.
+bool net_sizes(int ph, int pw, int hs[5], int ws[5]) {
+    hs[0] = hs[1] = ph;
+    ws[0] = ws[1] = pw;
+    for (int l = 2; l <= 4; ++l) {
+        hs[l] = (hs[l - 1] - 1) / 2 + 1;
+        ws[l] = (ws[l - 1] - 1) / 2 + 1;
+    }
+    return hs[4] >= 4 && ws[4] >= 8;
+}
+
+// The network's inference on n edge-count maps: conv1 fused into conv2 on the
+// tensor cores (the same arithmetic as the separate layer calls, so the same
+// bits), conv3, conv4 and pool + head -> logits [n][44].
+ld_status net_infer(const uint8_t *pool, int n, const int hs[5], const int ws[5], const ld_proposal_net *net,
+                    void *y2, void *y3, void *y4, float *feat, float *logits, cudaStream_t s) {
+    const ConvTcGeom G2{n, hs[1], ws[1], hs[2], ws[2], 2};
+    const cudaError_t e = launch_conv12_fused_tc(pool, G2, net->w[0], net->b[0], net->w[1], net->b[1], y2, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused conv1-2");
+    ld_status st = ld_conv3x3_forward(y2, n, hs[2], ws[2], 32, 32, 2, net->w[2], net->b[2], y3, s);
+    if (st != LD_OK) return st;
+    st = ld_conv3x3_forward(y3, n, hs[3], ws[3], 32, 32, 2, net->w[3], net->b[3], y4, s);
+    if (st != LD_OK) return st;
+    return ld_pool_head_forward(y4, n, hs[4], ws[4], net->wh, net->bh, feat, logits, s);
+}
+}  // namespace
+
+extern "C" {
+
+ld_status ld_proposal_logits(ld_ctx *ctx, const uint8_t *d_pool, int32_t n, int32_t ph, int32_t pw,
+                             const ld_proposal_net *net, float *d_logits, void *stream) {
+    if (!ctx || !d_pool || !d_logits || n < 1) return fail(LD_ERR_INVALID, "ld_proposal_logits: bad argument");
+    if (!net || !net->wh || !net->bh) return fail(LD_ERR_INVALID, "ld_proposal_logits: NULL network");
+    for (int i = 0; i < 4; ++i)
+        if (!net->w[i] || !net->b[i]) return fail(LD_ERR_INVALID, "ld_proposal_logits: NULL network layer");
+    int hs[5], ws[5];
+    if (ph < 1 || pw < 2 || ph > 32767 || pw > 32767 || !net_sizes(ph, pw, hs, ws))
+        return fail(LD_ERR_INVALID, "ld_proposal_logits: map %dx%d too small or too large", pw, ph);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_y2 = carve((size_t)n * hs[2] * ws[2] * 32 * 2);
+    const size_t o_y3 = carve((size_t)n * hs[3] * ws[3] * 32 * 2);
+    const size_t o_y4 = carve((size_t)n * hs[4] * ws[4] * 32 * 2);
+    const size_t o_feat = carve((size_t)n * 1024 * 4);
+    if (!ctx->prop.ensure(off)) return fail(LD_ERR_NOMEM, "scratch proposal");
+    uint8_t *pb = (uint8_t *)ctx->prop.p;
+    return net_infer(d_pool, n, hs, ws, net, pb + o_y2, pb + o_y3, pb + o_y4, (float *)(pb + o_feat), d_logits,
+                     (cudaStream_t)stream);
+}
+
 ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
                                    const ld_proposal_net *net, const ld_proposal_params *prp, ld_peak *d_peaks,
                                    int32_t *d_n_peaks, int32_t *d_status, int32_t *d_fallback,
@@ -863,12 +921,8 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         if (h_frames[i].w != w || h_frames[i].h != h)
             return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: frames must share one size");
     const int ph = (h + 7) / 8, pw = (w + 7) / 8;
-    int hs[5] = {ph, ph, 0, 0, 0}, ws[5] = {pw, pw, 0, 0, 0};
-    for (int l = 2; l <= 4; ++l) {
-        hs[l] = (hs[l - 1] - 1) / 2 + 1;
-        ws[l] = (ws[l - 1] - 1) / 2 + 1;
-    }
-    if (hs[4] < 4 || ws[4] < 8) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: frame %dx%d too small", w, h);
+    int hs[5], ws[5];
+    if (!net_sizes(ph, pw, hs, ws)) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: frame %dx%d too small", w, h);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
@@ -894,7 +948,6 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     size_t off = 0;
     auto carve = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
     const size_t o_pool = carve((size_t)n * ph * pw);
-    const size_t o_y1 = carve((size_t)n * hs[1] * ws[1] * 16 * 2);
     const size_t o_y2 = carve((size_t)n * hs[2] * ws[2] * 32 * 2);
     const size_t o_y3 = carve((size_t)n * hs[3] * ws[3] * 32 * 2);
     const size_t o_y4 = carve((size_t)n * hs[4] * ws[4] * 32 * 2);
@@ -908,7 +961,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     if (!ctx->prop.ensure(off)) return fail(LD_ERR_NOMEM, "scratch proposal");
     uint8_t *pb = (uint8_t *)ctx->prop.p;
     uint8_t *pool = pb + o_pool;
-    void *y[5] = {nullptr, pb + o_y1, pb + o_y2, pb + o_y3, pb + o_y4};
+    void *y[5] = {nullptr, nullptr, pb + o_y2, pb + o_y3, pb + o_y4};
     float *feat = (float *)(pb + o_feat), *logits = (float *)(pb + o_logit);
     int32_t *plist = (int32_t *)(pb + o_list), *pcnt = (int32_t *)(pb + o_cnt);
     int32_t *fb = d_fallback ? d_fallback : (int32_t *)(pb + o_fb);
@@ -946,14 +999,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     e = launch_sobel(SL, n * per_frame_ctas, s);
     if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
     // the network
-    static const int cin[4] = {1, 16, 32, 32}, cout[4] = {16, 32, 32, 32}, stride[4] = {1, 2, 2, 2};
-    const void *x = pool;
-    for (int l = 0; l < 4; ++l) {
-        st = ld_conv3x3_forward(x, n, hs[l], ws[l], cin[l], cout[l], stride[l], net->w[l], net->b[l], y[l + 1], s);
-        if (st != LD_OK) return st;
-        x = y[l + 1];
-    }
-    st = ld_pool_head_forward(y[4], n, hs[4], ws[4], net->wh, net->bh, feat, logits, s);
+    st = net_infer(pool, n, hs, ws, net, y[2], y[3], y[4], feat, logits, s);
     if (st != LD_OK) return st;
     // bands -> active pairs -> work units
     e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, plist, pcnt, fb, tiles,

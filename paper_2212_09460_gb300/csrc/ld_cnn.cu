@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(256) conv1_fwd_kernel(const uint8_t *x, int h,
     for (int c = 0; c < 16; c += 2) {
         float s0 = bs[c], s1 = bs[c + 1];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            s0 += ws[c * 9 + t] * v[t];
-            s1 += ws[(c + 1) * 9 + t] * v[t];
+        for (int t = 0; t < 9; ++t) {   // explicit fused multiply-adds: the fused inference path repeats them
+            s0 = __fmaf_rn(ws[c * 9 + t], v[t], s0);
+            s1 = __fmaf_rn(ws[(c + 1) * 9 + t], v[t], s1);
         }
         out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
     }

@@ -117,11 +117,67 @@ __device__ __forceinline__ void load_tile(const bf16 *x, const ConvTcGeom &G, co
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Persistent: CTA c takes tiles c, c + gridDim.x, ...; the copies of the next
-// tile run while the current one is multiplied and written (2 stages).
-template <int CIN, int S>
+// Fused first layer (inference): the input patch of a 16->32 stride-2 tile
+// is conv1's output, computed here from the uint8 edge-count map x0 [h][w]
+// (one image) exactly as the separate conv1 layer computes it (same fp32
+// fused multiply-adds in the same order, same rounding to bf16), and zero
+// outside the image (conv2's padding).  xs stages the counts / 64 of the
+// (PR + 2) x (PC + 2) region under the patch.
+struct Conv1Params {
+    const uint8_t *x0;
+    const bf16 *w1;   // [16][3][3][1]
+    const float *b1;  // [16]
+};
+
+__device__ __forceinline__ void compute_patch(const Conv1Params &C1, const ConvTcGeom &G, int tile,
+                                              int tiles_per_img, int tiles_x, uint8_t *Ps, float *xs,
+                                              const float *w1s, const float *b1s) {
+    constexpr int S = 2, QPP = 2, PR = Patch<2>::PR, PC = Patch<2>::PC, HC = Patch<2>::HC;
+    constexpr int XW = PC + 2, XN = (PR + 2) * (PC + 2);
+    const int tid = threadIdx.x;
+    const int img = tile / tiles_per_img, t = tile - img * tiles_per_img;
+    const int iy0 = (t / tiles_x) * kTileH * S - 1, ix0 = (t % tiles_x) * kTileW * S - 1;
+    const uint8_t *xi = C1.x0 + (int64_t)img * G.h * G.w;
+    for (int i = tid; i < XN; i += kTcThreads) {
+        const int yy = iy0 - 1 + i / XW, xx = ix0 - 1 + i % XW;
+        xs[i] = (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) ? (float)xi[yy * G.w + xx] * (1.f / 64.f) : 0.f;
+    }
+    __syncthreads();
+    for (int p = tid; p < PR * PC; p += kTcThreads) {
+        const int pr = p / PC, pc = p - pr * PC;
+        const int yy = iy0 + pr, xx = ix0 + pc;
+        uint32_t out[8];
+        if (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) {
+            float v[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = xs[(pr + k / 3) * XW + pc + k % 3];
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                float s0 = b1s[c], s1 = b1s[c + 1];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    s0 = __fmaf_rn(w1s[c * 9 + k], v[k], s0);
+                    s1 = __fmaf_rn(w1s[(c + 1) * 9 + k], v[k], s1);
+                }
+                out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) out[c] = 0u;
+        }
+        uint4 *d0 = reinterpret_cast<uint4 *>(Ps + (((pr * QPP + 0) * S + pc % S) * HC + pc / S) * 16);
+        uint4 *d1 = reinterpret_cast<uint4 *>(Ps + (((pr * QPP + 1) * S + pc % S) * HC + pc / S) * 16);
+        *d0 = make_uint4(out[0], out[1], out[2], out[3]);
+        *d1 = make_uint4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// Persistent: CTA c takes tiles c, c + gridDim.x, ...; the next tile's
+// operands are prepared (copied, or with FUSE1 computed) while the current
+// one is multiplied and written (2 stages).
+template <int CIN, int S, bool FUSE1>
 __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, ConvTcGeom G, const bf16 *wt,
-                                                                const float *bias, bf16 *y) {
+                                                                const float *bias, bf16 *y, Conv1Params C1) {
     constexpr int K = 9 * CIN, QPP = CIN / 8;
     constexpr int HC = Patch<S>::HC;
     constexpr int P_BYTES = (Patch<S>::PR * QPP * S * HC * 16 + 1023) / 1024 * 1024;
@@ -131,6 +187,8 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_s;
     __shared__ float bias_s[kTcN];
+    __shared__ float w1s[FUSE1 ? 144 : 1], b1s[FUSE1 ? 16 : 1];
+    __shared__ float xs[FUSE1 ? (Patch<S>::PR + 2) * (Patch<S>::PC + 2) : 1];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (G.ow + kTileW - 1) / kTileW;
     const int tiles_per_img = ((G.oh + kTileH - 1) / kTileH) * tiles_x;
@@ -149,7 +207,23 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
     if (tid < kTcN) bias_s[tid] = bias[tid];
 
     int tile = blockIdx.x;
-    if (tile < n_tiles) load_tile<CIN, S>(x, G, wt, tile, tiles_per_img, tiles_x, smem, smem + P_BYTES, true);
+    if (FUSE1) {
+        for (int i = tid; i < 144; i += kTcThreads) w1s[i] = __bfloat162float(C1.w1[i]);
+        if (tid < 16) b1s[tid] = C1.b1[tid];
+        // the weights of both stages, then the first tile's patch
+        constexpr int KC = K / 8;
+        for (int i = tid; i < 2 * kTcN * KC; i += kTcThreads) {
+            const int st2 = i / (kTcN * KC), j = i % (kTcN * KC), kc = j % KC, n = j / KC;
+            cp_async16(saddr(smem + st2 * STAGE + P_BYTES + ((kc * (kTcN / 8) + (n >> 3)) * 8 + (n & 7)) * 16),
+                       wt + (int64_t)n * K + kc * 8, 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (tile < n_tiles) compute_patch(C1, G, tile, tiles_per_img, tiles_x, smem, xs, w1s, b1s);
+    } else if (tile < n_tiles) {
+        load_tile<CIN, S>(x, G, wt, tile, tiles_per_img, tiles_x, smem, smem + P_BYTES, true);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -159,14 +233,16 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
         const int st = it & 1;
         uint8_t *Ps = smem + st * STAGE, *Bs = Ps + P_BYTES;
         const int next = tile + gridDim.x;
-        if (next < n_tiles) {
-            uint8_t *Pn = smem + (st ^ 1) * STAGE;
-            load_tile<CIN, S>(x, G, wt, next, tiles_per_img, tiles_x, Pn, Pn + P_BYTES, it == 0);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies are done
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!FUSE1) {
+            if (next < n_tiles) {
+                uint8_t *Pn = smem + (st ^ 1) * STAGE;
+                load_tile<CIN, S>(x, G, wt, next, tiles_per_img, tiles_x, Pn, Pn + P_BYTES, it == 0);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies are done
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // copies -> tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // smem writes -> tensor core (async proxy)
         __syncthreads();
         if (tid == 0) {
             const uint32_t p0 = saddr(Ps), b0 = saddr(Bs);
@@ -191,6 +267,9 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
                              saddr(&bar))
                          : "memory");
         }
+        // the next tile's fused first layer while the tensor core works on this one
+        if (FUSE1 && next < n_tiles)
+            compute_patch(C1, G, next, tiles_per_img, tiles_x, smem + (st ^ 1) * STAGE, xs, w1s, b1s);
         const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
         const bool all_done = __syncthreads_and(done ? 1 : 0) != 0;   // block-uniform
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -240,16 +319,16 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-template <int CIN, int S>
-cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const float *b, bf16 *y, cudaStream_t s) {
+template <int CIN, int S, bool FUSE1>
+cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const float *b, bf16 *y,
+                      const Conv1Params &C1, cudaStream_t s) {
     constexpr int QPP = CIN / 8;
     constexpr int P_BYTES = (Patch<S>::PR * QPP * S * Patch<S>::HC * 16 + 1023) / 1024 * 1024;
     constexpr int smem = 2 * (P_BYTES + kTcN * 9 * CIN * 2);
-    cudaError_t e =
-        cudaFuncSetAttribute(conv_fwd_tc_kernel<CIN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = conv_fwd_tc_kernel<CIN, S, FUSE1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)   // as much shared memory as possible: several CTAs per SM
-        e = cudaFuncSetAttribute(conv_fwd_tc_kernel<CIN, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, sm_smem = 0, reserved = 0;
     e = cudaGetDevice(&dev);
@@ -257,14 +336,14 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e != cudaSuccess) return e;
-    // CTAs per SM by shared memory (dynamic + 1 KB static + the per-block
-    // reservation), at most 512 / 32 by tensor memory
-    int per_sm = sm_smem / (smem + 1024 + reserved);
+    // CTAs per SM by shared memory (dynamic + up to 4 KB static + the
+    // per-block reservation), at most 512 / 32 by tensor memory
+    int per_sm = sm_smem / (smem + 4096 + reserved);
     if (per_sm < 1) per_sm = 1;
     if (per_sm * kTmemCols > 512) per_sm = 512 / kTmemCols;
     const int tiles = G.n * ((G.oh + kTileH - 1) / kTileH) * ((G.ow + kTileW - 1) / kTileW);
     const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
-    conv_fwd_tc_kernel<CIN, S><<<grid, kTcThreads, smem, s>>>(x, G, w, b, y);
+    kern<<<grid, kTcThreads, smem, s>>>(x, G, w, b, y, C1);
     return cudaGetLastError();
 }
 
@@ -272,14 +351,22 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
 
 cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, const void *w, const float *b, void *y,
                                cudaStream_t s) {
+    const Conv1Params none{nullptr, nullptr, nullptr};
     if (G.stride == 2) {
-        if (cin == 16) return launch_tc<16, 2>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, s);
-        if (cin == 32) return launch_tc<32, 2>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, s);
+        if (cin == 16) return launch_tc<16, 2, false>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, none, s);
+        if (cin == 32) return launch_tc<32, 2, false>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, none, s);
     } else if (G.stride == 1) {
-        if (cin == 16) return launch_tc<16, 1>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, s);
-        if (cin == 32) return launch_tc<32, 1>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, s);
+        if (cin == 16) return launch_tc<16, 1, false>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, none, s);
+        if (cin == 32) return launch_tc<32, 1, false>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, none, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const void *w1, const float *b1,
+                                   const void *w2, const float *b2, void *y2, cudaStream_t s) {
+    if (G.stride != 2) return cudaErrorInvalidValue;
+    const Conv1Params C1{x0, (const bf16 *)w1, b1};
+    return launch_tc<16, 2, true>((const bf16 *)w2, G, (const bf16 *)w2, b2, (bf16 *)y2, C1, s);
 }
 
 }  // namespace ld

@@ -182,6 +182,10 @@ struct ConvTcGeom {
 };
 cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, const void *w, const float *b, void *y,
                                cudaStream_t s);
+// Inference: conv1 (1->16, from the uint8 edge counts x0 [n][h][w]) fused into
+// conv2 (16->32, stride 2); G describes conv2 (input h x w = conv1's output).
+cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const void *w1, const float *b1,
+                                   const void *w2, const float *b2, void *y2, cudaStream_t s);
 
 // Proposal: band logits -> per-frame ascending active-pair lists, counts,
 // fallback flags, tile counts and the device prefix unit_begin [n + 1].

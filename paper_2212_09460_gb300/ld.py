@@ -103,6 +103,8 @@ _SIGS = {
     "ld_adam_step": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, ctypes.c_int32, _P, _P],
     "ld_conv_faults": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    "ld_proposal_logits": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_proposal_net),
+                           _P, _P],
     "ld_ctx_enable_timing": [_P, ctypes.c_int],
     "ld_ctx_stage_ms": [_P, ctypes.POINTER(ctypes.c_float * 3)],
 }
@@ -297,6 +299,10 @@ def ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream) -
     _check(load().ld_conv3x3_forward(d_x, n, h, w, cin, cout, stride, d_w, d_b, d_y, stream))
 
 
+def ld_proposal_logits(ctx, d_pool, n, ph, pw, net, d_logits, stream) -> None:
+    _check(load().ld_proposal_logits(ctx, d_pool, n, ph, pw, ctypes.byref(net), d_logits, stream))
+
+
 def ld_conv_faults(device: int = 0) -> int:
     """Tensor-core convolution faults recorded on `device` since the last call (read and cleared)."""
     v = ctypes.c_int32(0)
@@ -460,6 +466,17 @@ class Context:
         pk, npk, st, fb, act = out
         ld_detect_batch_proposal(self.handle, descs, p, net.c_struct(), q or proposal_params(), pk.data_ptr(),
                                  npk.data_ptr(), st.data_ptr(), fb.data_ptr(), act.data_ptr(), _stream_handle(stream))
+        return out
+
+    def proposal_logits(self, pool, net, out=None, stream=None):
+        """The proposal network's inference (fused first layer) on uint8 edge
+        counts [n][ph][pw] on the device: logits float32 [n][44]."""
+        torch = _torch()
+        n, ph, pw = pool.shape
+        if out is None:
+            out = torch.empty((n, 44), dtype=torch.float32, device=pool.device)
+        ld_proposal_logits(self.handle, pool.data_ptr(), n, ph, pw, net.c_struct(), out.data_ptr(),
+                           _stream_handle(stream))
         return out
 
     def edge_pool(self, frames, p: ld_params, widths=None, out=None, stream=None):

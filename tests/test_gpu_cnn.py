@@ -133,3 +133,19 @@ def test_tensor_core_conv_matches_oracle(ldlib, cin, stride, h, w):
     ref = torch.nn.functional.conv2d(x.double().permute(0, 3, 1, 2), wt.double().permute(0, 3, 1, 2),
                                      b.double(), stride=stride, padding=1).relu().permute(0, 2, 3, 1).numpy()
     assert _rel(y.float().cpu().numpy(), ref) < 1e-2
+
+
+@pytest.mark.parametrize("hw", [(135, 240), (70, 100)])
+def test_fused_inference_equals_layer_calls(ctx, ldlib, hw):
+    # ld_proposal_logits (conv1 fused into the tensor-core conv2) gives the
+    # same bits as the separate layer calls the trainer uses
+    params = _bf16_params(21)
+    rng = np.random.default_rng(hw[0])
+    x = (rng.integers(0, 40, size=(3,) + hw) * (rng.random((3,) + hw) < 0.4)).astype(np.uint8)
+    net = _net(ldlib, params)
+    xd = torch.from_numpy(x).cuda()
+    ref = net.forward(xd).logits
+    got = ctx.proposal_logits(xd, net)
+    torch.cuda.synchronize()
+    assert ldlib.ld_conv_faults(0) == 0
+    np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
