@@ -33,6 +33,8 @@ batch; a GPU test checks this on frames served in the mix.
 """
 from __future__ import annotations
 
+import ctypes
+import gc
 import os
 import time
 from collections import deque
@@ -201,6 +203,17 @@ class Scheduler:
         self.clock = clock or RealClock()
 
     def run(self, arrivals: list[Frame], keep_peaks: bool = False) -> ServeStats:
+        """Serve the arrivals (with Python's cyclic garbage collector paused,
+        so that no collection stalls the loop)."""
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(arrivals, keep_peaks)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _run(self, arrivals: list[Frame], keep_peaks: bool) -> ServeStats:
         adm, ex, clock = self.adm, self.ex, self.clock
         st = ServeStats()
         waiting = {s: deque() for s in adm.bufs}      # arrived, no slot yet
@@ -312,6 +325,16 @@ class GpuExecutor:
         self.style = synth.THROUGHPUT_1080P
         self.n_workers, self.max_batch = workers, max_batch
         self.loader = torch.cuda.Stream(self.dev)
+        # frame descriptors go to the device through a ring of pinned buffers
+        # allocated here, so that no load allocates pinned memory (which can
+        # stall the host for milliseconds)
+        max_load = sum(admission.slots(sz) for sz in admission.bufs)
+        desc_bytes = ctypes.sizeof(ld.ld_synth_frame) * max_load
+        self.desc_ring = 8
+        self.desc_host = torch.empty((self.desc_ring, desc_bytes), dtype=torch.uint8, pin_memory=True)
+        self.desc_dev = torch.empty((self.desc_ring, desc_bytes), dtype=torch.uint8, device=self.dev)
+        self.desc_ev = [None] * self.desc_ring
+        self.desc_next = 0
         max_px = max(w * h for w, h in sizes) * max_batch
         k = self.p.top_k
         self.w = []
@@ -356,12 +379,19 @@ class GpuExecutor:
         torch, ld = self.torch, self.ld
         specs = [(f.seed, f.w, f.h, self.style) for f in frames]
         arr = ld.synth_descriptors(specs, [f.buf for f in frames])
-        raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).pin_memory()
+        nbytes = ctypes.sizeof(arr)
+        k = self.desc_next
+        self.desc_next = (k + 1) % self.desc_ring
+        if self.desc_ev[k] is not None:
+            self.desc_ev[k].synchronize()   # the copy that last used this buffer (long done)
+        host, dev = self.desc_host[k], self.desc_dev[k]
+        ctypes.memmove(host.data_ptr(), ctypes.addressof(arr), nbytes)
         with torch.cuda.stream(self.loader):
-            d = raw.to(self.dev, non_blocking=True)
-            ld.ld_synth_frames(d.data_ptr(), len(frames), self.loader.cuda_stream)
+            dev[:nbytes].copy_(host[:nbytes], non_blocking=True)
+            ld.ld_synth_frames(dev.data_ptr(), len(frames), self.loader.cuda_stream)
             ev = torch.cuda.Event()
             ev.record(self.loader)
+        self.desc_ev[k] = ev
         for f in frames:
             f.ready = ev
 
