@@ -89,8 +89,8 @@ struct Patch {
     static constexpr int PR = (kTileH - 1) * S + 3, PC = (kTileW - 1) * S + 3, HC = (PC + S - 1) / S;
 };
 
-// Start the copies of tile `tile` (patch, and B when with_b) into one stage;
-// one commit group.
+// Start the copies of tile `tile`'s patch into one stage (and of the weights
+// B when with_b); one commit group.
 template <int CIN, int S>
 __device__ __forceinline__ void load_tile(const bf16 *x, const ConvTcGeom &G, const bf16 *wt, int tile,
                                           int tiles_per_img, int tiles_x, uint8_t *Ps, uint8_t *Bs, bool with_b) {
@@ -107,7 +107,7 @@ __device__ __forceinline__ void load_tile(const bf16 *x, const ConvTcGeom &G, co
         const bf16 *src = ok ? xi + ((int64_t)iy * G.w + ix) * CIN + q * 8 : x;
         cp_async16(saddr(Ps + (((pr * QPP + q) * S + pc % S) * HC + pc / S) * 16), src, ok ? 16 : 0);
     }
-    // B: chunk kc of output channel n (the same for every tile: loaded once per stage)
+    // B: chunk kc of output channel n (the same for every tile: loaded once)
     if (with_b)
         for (int i = tid; i < kTcN * KC; i += kTcThreads) {
             const int kc = i % KC, n = i / KC;
@@ -129,46 +129,66 @@ struct Conv1Params {
     const float *b1;  // [16]
 };
 
-__device__ __forceinline__ void compute_patch(const Conv1Params &C1, const ConvTcGeom &G, int tile,
-                                              int tiles_per_img, int tiles_x, uint8_t *Ps, float *xs,
-                                              const float *w1s, const float *b1s) {
-    constexpr int S = 2, QPP = 2, PR = Patch<2>::PR, PC = Patch<2>::PC, HC = Patch<2>::HC;
-    constexpr int XW = PC + 2, XN = (PR + 2) * (PC + 2);
-    const int tid = threadIdx.x;
+constexpr int kXsN = (Patch<2>::PR + 2) * (Patch<2>::PC + 2);   // staged counts per tile
+constexpr int kXsPer = (kXsN + kTcThreads - 1) / kTcThreads;       // per thread
+
+// Issue the loads of this thread's share of tile `tile`'s edge counts (/ 64,
+// zero outside the map) into registers; they land while other work runs.
+__device__ __forceinline__ void load_counts(const Conv1Params &C1, const ConvTcGeom &G, int tile, int tiles_per_img,
+                                            int tiles_x, float (&xr)[kXsPer]) {
+    constexpr int S = 2, XW = Patch<2>::PC + 2;
     const int img = tile / tiles_per_img, t = tile - img * tiles_per_img;
     const int iy0 = (t / tiles_x) * kTileH * S - 1, ix0 = (t % tiles_x) * kTileW * S - 1;
     const uint8_t *xi = C1.x0 + (int64_t)img * G.h * G.w;
-    for (int i = tid; i < XN; i += kTcThreads) {
+#pragma unroll
+    for (int j = 0; j < kXsPer; ++j) {
+        const int i = threadIdx.x + j * kTcThreads;
         const int yy = iy0 - 1 + i / XW, xx = ix0 - 1 + i % XW;
-        xs[i] = (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) ? (float)xi[yy * G.w + xx] * (1.f / 64.f) : 0.f;
+        xr[j] = (i < kXsN && yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) ? (float)__ldg(xi + yy * G.w + xx) * (1.f / 64.f)
+                                                                          : 0.f;
+    }
+}
+
+// Stage the counts and compute the tile's patch: conv1 for channels
+// 4w .. 4w+3 in warp w, of patch pixels lane, lane + 32, ...; 8 bytes into
+// chunk w / 2 at byte offset (w % 2) * 8.  All threads of the CTA call this.
+__device__ __forceinline__ void compute_patch(const ConvTcGeom &G, int tile, int tiles_per_img, int tiles_x,
+                                              uint8_t *Ps, float *xs, const float (&xr)[kXsPer],
+                                              const float (&w4)[36], const float (&b4)[4]) {
+    constexpr int S = 2, QPP = 2, PR = Patch<2>::PR, PC = Patch<2>::PC, HC = Patch<2>::HC;
+    constexpr int XW = PC + 2;
+    const int tid = threadIdx.x, lane = tid & 31, cg = tid >> 5;
+    const int img = tile / tiles_per_img, t = tile - img * tiles_per_img;
+    const int iy0 = (t / tiles_x) * kTileH * S - 1, ix0 = (t % tiles_x) * kTileW * S - 1;
+    (void)img;
+    __syncthreads();   // xs is free (the previous patch is written)
+#pragma unroll
+    for (int j = 0; j < kXsPer; ++j) {
+        const int i = tid + j * kTcThreads;
+        if (i < kXsN) xs[i] = xr[j];
     }
     __syncthreads();
-    for (int p = tid; p < PR * PC; p += kTcThreads) {
+    for (int p = lane; p < PR * PC; p += 32) {
         const int pr = p / PC, pc = p - pr * PC;
         const int yy = iy0 + pr, xx = ix0 + pc;
-        uint32_t out[8];
+        uint32_t o0 = 0u, o1 = 0u;
         if (yy >= 0 && yy < G.h && xx >= 0 && xx < G.w) {
             float v[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) v[k] = xs[(pr + k / 3) * XW + pc + k % 3];
+            float a[4];
 #pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                float s0 = b1s[c], s1 = b1s[c + 1];
+            for (int c = 0; c < 4; ++c) {
+                float acc = b4[c];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    s0 = __fmaf_rn(w1s[c * 9 + k], v[k], s0);
-                    s1 = __fmaf_rn(w1s[(c + 1) * 9 + k], v[k], s1);
-                }
-                out[c / 2] = to_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+                for (int k = 0; k < 9; ++k) acc = __fmaf_rn(w4[c * 9 + k], v[k], acc);
+                a[c] = fmaxf(acc, 0.f);
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) out[c] = 0u;
+            o0 = to_bf16x2(a[0], a[1]);
+            o1 = to_bf16x2(a[2], a[3]);
         }
-        uint4 *d0 = reinterpret_cast<uint4 *>(Ps + (((pr * QPP + 0) * S + pc % S) * HC + pc / S) * 16);
-        uint4 *d1 = reinterpret_cast<uint4 *>(Ps + (((pr * QPP + 1) * S + pc % S) * HC + pc / S) * 16);
-        *d0 = make_uint4(out[0], out[1], out[2], out[3]);
-        *d1 = make_uint4(out[4], out[5], out[6], out[7]);
+        *reinterpret_cast<uint2 *>(Ps + (((pr * QPP + (cg >> 1)) * S + pc % S) * HC + pc / S) * 16 + (cg & 1) * 8) =
+            make_uint2(o0, o1);
     }
 }
 
@@ -176,19 +196,21 @@ __device__ __forceinline__ void compute_patch(const Conv1Params &C1, const ConvT
 // operands are prepared (copied, or with FUSE1 computed) while the current
 // one is multiplied and written (2 stages).
 template <int CIN, int S, bool FUSE1>
-__global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, ConvTcGeom G, const bf16 *wt,
+__global__ void __launch_bounds__(kTcThreads, 4) conv_fwd_tc_kernel(const bf16 *x, ConvTcGeom G, const bf16 *wt,
                                                                 const float *bias, bf16 *y, Conv1Params C1) {
     constexpr int K = 9 * CIN, QPP = CIN / 8;
     constexpr int HC = Patch<S>::HC;
     constexpr int P_BYTES = (Patch<S>::PR * QPP * S * HC * 16 + 1023) / 1024 * 1024;
-    constexpr int B_BYTES = kTcN * K * 2, STAGE = P_BYTES + B_BYTES;
+    constexpr int B_BYTES = (kTcN * K * 2 + 1023) / 1024 * 1024, STAGE = P_BYTES;
     constexpr uint32_t ROW = QPP * S * HC * 16;   // bytes per patch row
-    extern __shared__ __align__(1024) uint8_t smem[];   // 2 stages of patch then B
+    extern __shared__ __align__(1024) uint8_t smem[];   // B (the weights), then 2 patch stages
+    uint8_t *const Bs = smem, *const stages = smem + B_BYTES;
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_s;
     __shared__ float bias_s[kTcN];
-    __shared__ float w1s[FUSE1 ? 144 : 1], b1s[FUSE1 ? 16 : 1];
-    __shared__ float xs[FUSE1 ? (Patch<S>::PR + 2) * (Patch<S>::PC + 2) : 1];
+    __shared__ float xs[FUSE1 ? kXsN : 1];
+    float w4[36], b4[4];   // FUSE1: conv1 weights and biases of this warp's 4 channels
+    float xr[kXsPer];      // FUSE1: the next tile's counts in flight
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = (G.ow + kTileW - 1) / kTileW;
     const int tiles_per_img = ((G.oh + kTileH - 1) / kTileH) * tiles_x;
@@ -208,21 +230,26 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
 
     int tile = blockIdx.x;
     if (FUSE1) {
-        for (int i = tid; i < 144; i += kTcThreads) w1s[i] = __bfloat162float(C1.w1[i]);
-        if (tid < 16) b1s[tid] = C1.b1[tid];
-        // the weights of both stages, then the first tile's patch
+#pragma unroll
+        for (int i = 0; i < 36; ++i) w4[i] = __bfloat162float(C1.w1[(warp * 4) * 9 + i]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b4[c] = C1.b1[warp * 4 + c];
+        // the weights, then the first tile's patch
         constexpr int KC = K / 8;
-        for (int i = tid; i < 2 * kTcN * KC; i += kTcThreads) {
-            const int st2 = i / (kTcN * KC), j = i % (kTcN * KC), kc = j % KC, n = j / KC;
-            cp_async16(saddr(smem + st2 * STAGE + P_BYTES + ((kc * (kTcN / 8) + (n >> 3)) * 8 + (n & 7)) * 16),
-                       wt + (int64_t)n * K + kc * 8, 16);
+        for (int i = tid; i < kTcN * KC; i += kTcThreads) {
+            const int kc = i % KC, n = i / KC;
+            cp_async16(saddr(Bs + ((kc * (kTcN / 8) + (n >> 3)) * 8 + (n & 7)) * 16), wt + (int64_t)n * K + kc * 8,
+                       16);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        if (tile < n_tiles) compute_patch(C1, G, tile, tiles_per_img, tiles_x, smem, xs, w1s, b1s);
+        if (tile < n_tiles) {
+            load_counts(C1, G, tile, tiles_per_img, tiles_x, xr);
+            compute_patch(G, tile, tiles_per_img, tiles_x, stages, xs, xr, w4, b4);
+        }
     } else if (tile < n_tiles) {
-        load_tile<CIN, S>(x, G, wt, tile, tiles_per_img, tiles_x, smem, smem + P_BYTES, true);
+        load_tile<CIN, S>(x, G, wt, tile, tiles_per_img, tiles_x, stages, Bs, true);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -231,12 +258,12 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
     bool fault = false;
     for (int it = 0; tile < n_tiles; ++it, tile += gridDim.x) {   // block-uniform
         const int st = it & 1;
-        uint8_t *Ps = smem + st * STAGE, *Bs = Ps + P_BYTES;
+        uint8_t *Ps = stages + st * STAGE;
         const int next = tile + gridDim.x;
         if (!FUSE1) {
             if (next < n_tiles) {
-                uint8_t *Pn = smem + (st ^ 1) * STAGE;
-                load_tile<CIN, S>(x, G, wt, next, tiles_per_img, tiles_x, Pn, Pn + P_BYTES, it == 0);
+                uint8_t *Pn = stages + (st ^ 1) * STAGE;
+                load_tile<CIN, S>(x, G, wt, next, tiles_per_img, tiles_x, Pn, Bs, false);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies are done
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -267,9 +294,9 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
                              saddr(&bar))
                          : "memory");
         }
-        // the next tile's fused first layer while the tensor core works on this one
-        if (FUSE1 && next < n_tiles)
-            compute_patch(C1, G, next, tiles_per_img, tiles_x, smem + (st ^ 1) * STAGE, xs, w1s, b1s);
+        // the next tile's counts are fetched while the tensor core works on
+        // this one (its patch is computed after the epilogue)
+        if (FUSE1 && next < n_tiles) load_counts(C1, G, next, tiles_per_img, tiles_x, xr);
         const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
         const bool all_done = __syncthreads_and(done ? 1 : 0) != 0;   // block-uniform
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -303,6 +330,8 @@ __global__ void __launch_bounds__(kTcThreads) conv_fwd_tc_kernel(const bf16 *x, 
             dst[2] = make_uint4(o[8], o[9], o[10], o[11]);
             dst[3] = make_uint4(o[12], o[13], o[14], o[15]);
         }
+        if (FUSE1 && next < n_tiles)   // block-uniform
+            compute_patch(G, next, tiles_per_img, tiles_x, stages + (st ^ 1) * STAGE, xs, xr, w4, b4);
         // the accumulator is read and this stage's operands are used before
         // the next MMA or the next copies into this stage
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -324,7 +353,7 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
                       const Conv1Params &C1, cudaStream_t s) {
     constexpr int QPP = CIN / 8;
     constexpr int P_BYTES = (Patch<S>::PR * QPP * S * Patch<S>::HC * 16 + 1023) / 1024 * 1024;
-    constexpr int smem = 2 * (P_BYTES + kTcN * 9 * CIN * 2);
+    constexpr int smem = (kTcN * 9 * CIN * 2 + 1023) / 1024 * 1024 + 2 * P_BYTES;
     auto kern = conv_fwd_tc_kernel<CIN, S, FUSE1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)   // as much shared memory as possible: several CTAs per SM
@@ -336,9 +365,14 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e != cudaSuccess) return e;
-    // CTAs per SM by shared memory (dynamic + up to 4 KB static + the
-    // per-block reservation), at most 512 / 32 by tensor memory
-    int per_sm = sm_smem / (smem + 4096 + reserved);
+    // CTAs per SM by shared memory (dynamic + static + the per-block
+    // reservation) and by registers, at most 512 / 32 by tensor memory
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int per_sm = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
+    const int per_sm_regs = 65536 / (kTcThreads * ((fa.numRegs + 7) / 8 * 8));
+    if (per_sm_regs < per_sm) per_sm = per_sm_regs;
     if (per_sm < 1) per_sm = 1;
     if (per_sm * kTmemCols > 512) per_sm = 512 / kTmemCols;
     const int tiles = G.n * ((G.oh + kTileH - 1) / kTileH) * ((G.ow + kTileW - 1) / kTileW);
