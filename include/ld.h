@@ -272,7 +272,9 @@ LD_API ld_status ld_conv3x3_forward(const void *d_x, int32_t n, int32_t h, int32
 LD_API ld_status ld_conv_faults(int32_t device, int32_t *flags);
 /* From dy (bf16, w.r.t. the ReLU output y): dw += dL/dw, db += dL/db (fp32,
  * accumulated: zero them first) and, if d_dx != NULL, dx = dL/dx (bf16).  The
- * 1-channel layer takes d_dx = NULL. */
+ * 1-channel layer takes d_dx = NULL.  Partial sums are reduced in a fixed
+ * order (a stream-ordered workspace), so the results are bitwise
+ * reproducible. */
 LD_API ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w,
                                      int32_t cin, int32_t cout, int32_t stride,
                                      const void *d_w, const void *d_y, const void *d_dy,

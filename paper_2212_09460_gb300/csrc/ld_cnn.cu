@@ -89,10 +89,11 @@ __global__ void __launch_bounds__(256) conv1_fwd_kernel(const uint8_t *x, int h,
     dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
 }
 
-// dw1[co][tap] += sum_p dy_pre[p][co] * x[pix(p, tap)],  db1[co] += sum_p dy_pre[p][co].
-// Block: 16 channels x 16 pixel lanes.
+// Partial sums of dw1[co][tap] = sum_p dy_pre[p][co] * x[pix(p, tap)] and
+// db1[co] = sum_p dy_pre[p][co] over this block's pixels: part[block][co * 10
+// + tap] (tap 9 = bias).  Block: 16 channels x 16 pixel lanes.
 __global__ void __launch_bounds__(256) conv1_wgrad_kernel(const uint8_t *x, const bf16 *y, const bf16 *dy, int n,
-                                                         int h, int w, float *dw, float *db) {
+                                                         int h, int w, float *part) {
     const int co = threadIdx.x & 15, lane = threadIdx.x >> 4;
     float acc[10];
 #pragma unroll
@@ -120,8 +121,7 @@ __global__ void __launch_bounds__(256) conv1_wgrad_kernel(const uint8_t *x, cons
         const int c = threadIdx.x / 10, t = threadIdx.x % 10;
         float s = 0.f;
         for (int l = 0; l < 16; ++l) s += red[l][c][t];
-        if (t < 9) atomicAdd(dw + c * 9 + t, s);
-        else atomicAdd(db + c, s);
+        part[(int64_t)blockIdx.x * 160 + c * 10 + t] = s;
     }
 }
 
@@ -211,13 +211,14 @@ __global__ void __launch_bounds__(128) conv_dgrad_kernel(const bf16 *y, const bf
     }
 }
 
-// Weight gradient: dw[co][tap][ci] += sum_p dy_pre[p][co] * x[pix(p, tap)][ci]
-// over this CTA's chunk of output pixels (M = COUT, N = 9*CIN, K = pixels).
-// Warp w takes n-tiles w, w+4, ...; the chunk's partial sums go to dw by fp32
-// atomics.  db[co] gets the bias gradient the same way.
+// Weight gradient: the partial sums dw[co][tap][ci] = sum_p dy_pre[p][co] *
+// x[pix(p, tap)][ci] over this CTA's chunk of output pixels (M = COUT,
+// N = 9*CIN, K = pixels) go to part[cta][co * 9 * CIN + (tap, ci)], and the
+// bias partials to part_b[cta][co]; reduce_parts sums them in CTA order, so
+// gradients are bitwise reproducible.  Warp w takes n-tiles w, w+4, ...
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf16 *y, const bf16 *dy, ConvGeom G,
-                                                        int chunk, float *dw, float *db) {
+                                                        int chunk, float *part, float *part_b) {
     constexpr int NT = 9 * CIN / 8;            // n8 tiles over (tap, ci)
     constexpr int NTW = (NT + 3) / 4;          // tiles per warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -301,13 +302,31 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf
             const int ncol = nt * 8 + 2 * t;
             const int co0 = mt * 16 + g;
             // column ncol = tap * CIN + ci maps to dw[co][tap][ci] = dw[co * 9 * CIN + ncol]
-            atomicAdd(dw + (int64_t)co0 * 9 * CIN + ncol, acc[mt][j][0]);
-            atomicAdd(dw + (int64_t)co0 * 9 * CIN + ncol + 1, acc[mt][j][1]);
-            atomicAdd(dw + (int64_t)(co0 + 8) * 9 * CIN + ncol, acc[mt][j][2]);
-            atomicAdd(dw + (int64_t)(co0 + 8) * 9 * CIN + ncol + 1, acc[mt][j][3]);
+            float *pc = part + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * (COUT * 9 * CIN);
+            pc[co0 * 9 * CIN + ncol] = acc[mt][j][0];
+            pc[co0 * 9 * CIN + ncol + 1] = acc[mt][j][1];
+            pc[(co0 + 8) * 9 * CIN + ncol] = acc[mt][j][2];
+            pc[(co0 + 8) * 9 * CIN + ncol + 1] = acc[mt][j][3];
         }
     }
-    if (warp == 0 && lane < COUT) atomicAdd(db + lane, bacc);
+    if (warp == 0 && lane < COUT) part_b[(int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * COUT + lane] = bacc;
+}
+
+// out[i] += sum over r < rows of part[r][i], in order (one thread per i).
+__global__ void __launch_bounds__(256) reduce_parts(const float *part, int rows, int cols, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += part[(int64_t)r * cols + i];
+    out[i] += s;
+}
+// out[c * 9 + t] += ..., outb[c] += ... from conv1's [rows][16 * 10] partials.
+__global__ void __launch_bounds__(160) reduce_parts1(const float *part, int rows, float *dw, float *db) {
+    const int i = threadIdx.x, c = i / 10, t = i % 10;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += part[(int64_t)r * 160 + i];
+    if (t < 9) dw[c * 9 + t] += s;
+    else db[c] += s;
 }
 
 // ------------------------------------------------------------------ pool + head
@@ -410,7 +429,7 @@ __global__ void __launch_bounds__(256) bce_kernel(const float *z, const float *t
     if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        atomicAdd(loss, s / (float)nk);
+        *loss = s / (float)nk;   // one block: the sum is in a fixed order
     }
 }
 
@@ -501,19 +520,33 @@ ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, 
     cudaStream_t s = (cudaStream_t)stream;
     if (cin == 1) {
         if (stride != 1 || d_dx) return bad("ld_conv3x3_backward: the 1-channel layer: stride 1, no dx");
-        conv1_wgrad_kernel<<<blocks_for((int64_t)n * h * w, 16 * 64, 1024), 256, 0, s>>>(
-            (const uint8_t *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy, n, h, w, d_dw, d_db);
+        const int blocks = blocks_for((int64_t)n * h * w, 16 * 64, 1024);
+        float *part = nullptr;
+        if (cudaMallocAsync((void **)&part, (size_t)blocks * 160 * sizeof(float), s) != cudaSuccess)
+            return launch_status("conv1_wgrad workspace");
+        conv1_wgrad_kernel<<<blocks, 256, 0, s>>>((const uint8_t *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy, n,
+                                                 h, w, part);
+        reduce_parts1<<<1, 160, 0, s>>>(part, blocks, d_dw, d_db);
+        cudaFreeAsync(part, s);
         return launch_status("conv1_wgrad");
     }
     const ConvGeom G = geom(n, h, w, stride);
     const int chunk = 2048;
     const dim3 wgrid((G.oh * G.ow + chunk - 1) / chunk, n);
+    const int ctas = (int)(wgrid.x * wgrid.y), nw = cout * 9 * cin;
+    float *part = nullptr;   // per-CTA partial sums (weights, then biases), stream-ordered
+    if (cudaMallocAsync((void **)&part, (size_t)ctas * (nw + cout) * sizeof(float), s) != cudaSuccess)
+        return launch_status("conv_wgrad workspace");
+    float *part_b = part + (size_t)ctas * nw;
     if (cin == 16)
         conv_wgrad_kernel<16, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
-                                                        G, chunk, d_dw, d_db);
+                                                        G, chunk, part, part_b);
     else
         conv_wgrad_kernel<32, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
-                                                        G, chunk, d_dw, d_db);
+                                                        G, chunk, part, part_b);
+    reduce_parts<<<(nw + 255) / 256, 256, 0, s>>>(part, ctas, nw, d_dw);
+    reduce_parts<<<1, 256, 0, s>>>(part_b, ctas, cout, d_db);
+    cudaFreeAsync(part, s);
     ld_status st = launch_status("conv_wgrad");
     if (st != LD_OK || !d_dx) return st;
     const dim3 dgrid((h * w + 63) / 64, n);
@@ -554,7 +587,7 @@ ld_status ld_bce_loss(const float *d_logits, const float *d_target, int32_t n, i
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_loss, 0, sizeof(float), s);
     if (e != cudaSuccess) return launch_status("ld_bce_loss memset");
-    bce_kernel<<<blocks_for(nk, 256, 256), 256, 0, s>>>(d_logits, d_target, nk, d_loss, d_dlogits);
+    bce_kernel<<<1, 256, 0, s>>>(d_logits, d_target, nk, d_loss, d_dlogits);
     return launch_status("bce");
 }
 

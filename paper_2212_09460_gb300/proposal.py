@@ -67,17 +67,28 @@ class ProposalNet:
     def state_numpy(self) -> dict:
         return {k: v.detach().cpu().numpy() for k, v in self.p.items()}
 
-    def save(self, path: str) -> None:
+    def save(self, path: str, with_optimizer: bool = False) -> None:
+        """Weights and the step count; with_optimizer also stores Adam's moments,
+        so that training resumed from the file continues bit for bit."""
         buf = io.BytesIO()
-        np.savez(buf, step=np.array(self.step_count), **self.state_numpy())
+        extra = {}
+        if with_optimizer:
+            for k in self.p:
+                extra["adam_m_" + k] = self.m[k].detach().cpu().numpy()
+                extra["adam_v_" + k] = self.v[k].detach().cpu().numpy()
+        np.savez(buf, step=np.array(self.step_count), **self.state_numpy(), **extra)
         with open(path, "wb") as f:
             f.write(buf.getvalue())
 
     @classmethod
     def load(cls, path: str, device=0) -> "ProposalNet":
         z = np.load(path)
-        net = cls({k: z[k] for k in z.files if k != "step"}, device)
+        net = cls({k: z[k] for k in z.files if k != "step" and not k.startswith("adam_")}, device)
         net.step_count = int(z["step"])
+        for k in net.p:
+            if "adam_m_" + k in z.files:
+                net.m[k].copy_(net.torch.from_numpy(z["adam_m_" + k]))
+                net.v[k].copy_(net.torch.from_numpy(z["adam_v_" + k]))
         return net
 
     def c_struct(self) -> "ld.ld_proposal_net":

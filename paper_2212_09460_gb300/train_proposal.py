@@ -62,16 +62,21 @@ def labelled_batch(torch, ctx, src, seeds, p):
     return frames, pool, tgt
 
 
-def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every: int = 100):
+def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every: int = 100,
+          checkpoint_every: int = 0, resume: str | None = None):
+    """Train for `steps` steps of `batch` device-generated frames (step k uses
+    frames TRAIN_SEED0 + k*batch ...).  Every checkpoint_every steps the
+    network and Adam's state go to out + ".ckpt.npz"; resume continues from
+    such a file at its step, reproducing the uninterrupted run bit for bit."""
     import torch
     dev = torch.device("cuda", 0)
     p = ld.params(n_theta=N_THETA, top_k=TOP_K, border=ld.LD_BORDER_CLEAR)
-    net = ProposalNet(device=0, seed=seed)
+    net = ProposalNet.load(resume, 0) if resume else ProposalNet(device=0, seed=seed)
     src = FrameSource(torch, dev, batch)
     log = []
     t0 = time.time()
     with ld.Context(0) as ctx:
-        for step in range(steps):
+        for step in range(net.step_count, steps):
             seeds = TRAIN_SEED0 + step * batch + np.arange(batch)
             _, pool, tgt = labelled_batch(torch, ctx, src, seeds, p)
             cur_lr = lr * 0.5 * (1 + math.cos(math.pi * step / steps))      # cosine decay
@@ -80,6 +85,8 @@ def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every:
                 log.append((step, float(loss.item())))
                 print(json.dumps({"step": step, "loss": log[-1][1], "lr": cur_lr,
                                   "elapsed_s": round(time.time() - t0, 1)}), flush=True)
+            if checkpoint_every and (step + 1) % checkpoint_every == 0:
+                net.save(out + ".ckpt.npz", with_optimizer=True)
     net.save(out)
     return net, log
 
@@ -139,13 +146,15 @@ def main():
     ap.add_argument("--p-band", type=float, default=0.05)
     ap.add_argument("--p-fallback", type=float, default=0.5)
     ap.add_argument("--margin", type=int, default=2)
+    ap.add_argument("--checkpoint-every", type=int, default=0, help="steps between resumable checkpoints")
+    ap.add_argument("--resume", default=None, help="checkpoint (network + Adam state) to continue from")
     a = ap.parse_args()
     from . import build
     build.build()
     if a.eval:
         print(json.dumps(evaluate(a.eval, a.frames, a.batch, a.p_band, a.p_fallback, a.margin)))
     else:
-        train(a.steps, a.batch, a.lr, a.out)
+        train(a.steps, a.batch, a.lr, a.out, checkpoint_every=a.checkpoint_every, resume=a.resume)
 
 
 if __name__ == "__main__":

@@ -149,3 +149,34 @@ def test_fused_inference_equals_layer_calls(ctx, ldlib, hw):
     torch.cuda.synchronize()
     assert ldlib.ld_conv_faults(0) == 0
     np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_training_is_reproducible_and_resumes_exactly(ldlib, tmp_path):
+    # gradients are reduced in a fixed order, so two runs give the same bits,
+    # and a checkpoint with Adam's moments resumes the same trajectory
+    params = _bf16_params(15)
+    x = [torch.from_numpy(_counts(30 + i, 4)).cuda() for i in range(4)]
+    tg = [torch.from_numpy((np.random.default_rng(40 + i).random((4, 44)) < 0.2).astype(np.float32)).cuda()
+          for i in range(4)]
+
+    def run(net, steps):
+        return [float(net.train_step(x[i], tg[i], lr=2e-3).item()) for i in steps]
+
+    a = _net(ldlib, params)
+    la = run(a, range(4))
+    b = _net(ldlib, params)
+    lb = run(b, range(4))
+    assert la == lb
+    for k in a.p:
+        assert torch.equal(a.p[k], b.p[k]), k
+    c = _net(ldlib, params)
+    lc = run(c, range(2))
+    ck = str(tmp_path / "ck.npz")
+    c.save(ck, with_optimizer=True)
+    from paper_2212_09460_gb300.proposal import ProposalNet
+    d = ProposalNet.load(ck, 0)
+    assert d.step_count == 2
+    lc += run(d, range(2, 4))
+    assert lc == la
+    for k in a.p:
+        assert torch.equal(a.p[k], d.p[k]) and torch.equal(a.m[k], d.m[k]) and torch.equal(a.v[k], d.v[k]), k
