@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) pool_head_bwd_kernel(const float *dlogits
                                                            bf16 *dy4) {
     __shared__ float df[kFeat], dl[kOut];
     const int s = blockIdx.x;
-    if (threadIdx.x < kOut) dl[threadIdx.x] = dlogits[(int64_t)s * kOut + threadIdx.x];
+    for (int o = threadIdx.x; o < kOut; o += blockDim.x) dl[o] = dlogits[(int64_t)s * kOut + o];
     __syncthreads();
     for (int q = threadIdx.x; q < kFeat; q += blockDim.x) {
         float acc = 0.f;

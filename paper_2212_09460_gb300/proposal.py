@@ -56,6 +56,10 @@ class ProposalNet:
         self.torch = torch
         self.device = torch.device("cuda", device) if isinstance(device, int) else device
         src = params if params is not None else init_numpy(seed)
+        ref = init_numpy(0)   # the shapes the kernels read (a wrong head size would be read out of bounds)
+        if set(src) != set(ref) or any(np.shape(src[k]) != ref[k].shape for k in ref):
+            raise ValueError("proposal network parameters do not have the expected names and shapes "
+                             f"(head {N_OUT} x {N_FEAT})")
         self.p = {k: torch.tensor(np.asarray(v, np.float32), device=self.device).contiguous() for k, v in src.items()}
         self.g = {k: torch.zeros_like(v) for k, v in self.p.items()}
         self.m = {k: torch.zeros_like(v) for k, v in self.p.items()}
