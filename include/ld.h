@@ -319,8 +319,9 @@ typedef struct {
 } ld_proposal_net;
 
 typedef struct {
-    float p_band;           /* vote a band if sigmoid(logit) >= p_band              [0.05] */
-    float p_fallback;       /* full vote if every band's probability < p_fallback  [0.5]  */
+    float p_band;           /* vote a band if sigmoid(logit) >= p_band              [0.2]  */
+    float p_fallback;       /* full vote if every band's probability < p_fallback  [0.5]
+                               (or < p_band: a frame always votes some pair)           */
     int32_t margin;         /* extra theta bins voted on each side of a kept band  [2]   */
     int32_t reserved;       /* must be 0 */
 } ld_proposal_params;

@@ -906,7 +906,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     ld_status st = check_params(&p);
     if (st != LD_OK) return st;
     if (p.n_theta % 36 != 0) return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: n_theta must be a multiple of 36");
-    ld_proposal_params q = prp ? *prp : ld_proposal_params{0.05f, 0.5f, 2, 0};
+    ld_proposal_params q = prp ? *prp : ld_proposal_params{0.2f, 0.5f, 2, 0};
     if (q.reserved != 0 || q.margin < 0 || !(q.p_band >= 0.f && q.p_band <= 1.f) ||
         !(q.p_fallback >= 0.f && q.p_fallback <= 1.f))
         return fail(LD_ERR_INVALID, "ld_detect_batch_proposal: bad proposal parameters");
@@ -943,7 +943,10 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     const int64_t epf = ((int64_t)w * h + 3) / 4 * 4;
     if (!ctx->edges.ensure((size_t)(n * epf) * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
     if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
-    if (!ctx->cand.ensure((size_t)n * hp.n_tiles * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    // restricted-vote tiles per frame: up to twice the full vote's, so that
+    // units can shrink to fill the persistent launch's last wave
+    const int tile_cap = std::min(n_pairs, 2 * hp.n_tiles);
+    if (!ctx->cand.ensure((size_t)n * tile_cap * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
     // proposal scratch, carved in 256-byte aligned pieces
     size_t off = 0;
     auto carve = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
@@ -1002,8 +1005,8 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     st = net_infer(pool, n, hs, ws, net, y[2], y[3], y[4], feat, logits, s);
     if (st != LD_OK) return st;
     // bands -> active pairs -> work units
-    e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, plist, pcnt, fb, tiles,
-                            ub, s);
+    e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, tile_cap,
+                            ctx->num_sms, plist, pcnt, fb, tiles, ub, s);
     if (e != cudaSuccess) return cuda_fail(e, "band selection");
     // Steps 3-4 on the kept pairs
     HoughLaunch HL;
@@ -1024,7 +1027,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         HF.edges = edges + i * epf;
         HF.count = sm.counts + i;
         HF.cap = (int64_t)w * h;
-        HF.cand = cand + (size_t)i * hp.n_tiles * M;
+        HF.cand = cand + (size_t)i * tile_cap * M;
         HF.flags = sm.flags + i;
         HF.done = sm.done + i;
         HF.peaks = d_peaks + (size_t)i * p.top_k;
@@ -1038,9 +1041,9 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         HF.n_rho = hp.n_rho;
         HF.n_splits = 1;
         HF.pairs_per_tile = hp.pairs;
-        HF.n_tiles = hp.n_tiles;
+        HF.n_tiles = tile_cap;   // unused: the device prefix ub gives each frame's tiles
     }
-    const int max_units = n * hp.n_tiles;
+    const int max_units = n * tile_cap;
     e = launch_hough(HL, max_units < ctx->num_sms ? max_units : ctx->num_sms, hp.pairs,
                      (int64_t)hp.pairs * hp.n_rho, s);
     if (e != cudaSuccess) return cuda_fail(e, "hough launch");

@@ -188,10 +188,12 @@ cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const
                                    const void *w2, const float *b2, void *y2, cudaStream_t s);
 
 // Proposal: band logits -> per-frame ascending active-pair lists, counts,
-// fallback flags, tile counts and the device prefix unit_begin [n + 1].
+// fallback flags, tile counts (at most pmax pairs and tile_cap tiles a frame,
+// sized to fill waves of `slots` persistent CTAs) and the device prefix
+// unit_begin [n + 1].  1 <= n <= kMaxLaunchFrames.
 cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p_band, float p_fallback, int margin,
-                                int pairs_per_tile, int32_t *pair_list, int32_t *pair_count, int32_t *fallback,
-                                int32_t *tiles, int32_t *unit_begin, cudaStream_t s);
+                                int pmax, int tile_cap, int slots, int32_t *pair_list, int32_t *pair_count,
+                                int32_t *fallback, int32_t *tiles, int32_t *unit_begin, cudaStream_t s);
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);

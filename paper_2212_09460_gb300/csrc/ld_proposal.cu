@@ -12,13 +12,13 @@ constexpr int kBands = 36, kRowBands = 8, kOut = kBands + kRowBands;
 
 // One CTA per frame.  Band b is kept if sigmoid(logit_b) >= p_band; the kept
 // bands' theta bins, widened by `margin` bins on each side, are voted.  If no
-// band reaches p_fallback the frame votes every bin (full-vote fallback).
-// Pair j covers bins {j, n - j} (j = 0: {0, n/2}); the frame's list holds the
-// pairs with an active bin, ascending; tiles[f] = ceil(count / pairs_per_tile).
+// band reaches p_fallback, or none reaches p_band (possible when p_band >
+// p_fallback), the frame votes every bin (full-vote fallback), so every
+// frame votes at least one pair.  Pair j covers bins {j, n - j} (j = 0:
+// {0, n/2}); the frame's list holds the pairs with an active bin, ascending.
 __global__ void __launch_bounds__(256) select_bands_kernel(const float *logits, int n_theta, float p_band,
-                                                          float p_fallback, int margin, int pairs_per_tile,
-                                                          int32_t *pair_list, int32_t *pair_count,
-                                                          int32_t *fallback, int32_t *tiles) {
+                                                          float p_fallback, int margin, int32_t *pair_list,
+                                                          int32_t *pair_count, int32_t *fallback) {
     __shared__ float prob[kBands];
     __shared__ uint8_t bin_on[kMaxTheta];
     __shared__ int warp_cnt[8];
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) select_bands_kernel(const float *logits, 
     if (tid == 0) {
         float mx = 0.f;
         for (int b = 0; b < kBands; ++b) mx = fmaxf(mx, prob[b]);
-        fb_s = mx < p_fallback ? 1 : 0;
+        fb_s = (mx < p_fallback || mx < p_band) ? 1 : 0;
     }
     __syncthreads();
     const int bpb = n_theta / kBands;
@@ -64,20 +64,67 @@ __global__ void __launch_bounds__(256) select_bands_kernel(const float *logits, 
     if (tid == 0) {
         pair_count[f] = base;
         fallback[f] = fb_s;
-        tiles[f] = (base + pairs_per_tile - 1) / pairs_per_tile;
     }
 }
 
-// unit_begin[0] = 0, unit_begin[f + 1] = unit_begin[f] + tiles[f].
-__global__ void prefix_kernel(const int32_t *tiles, int n, int32_t *unit_begin) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int s = 0;
-        unit_begin[0] = 0;
-        for (int f = 0; f < n; ++f) {
-            s += tiles[f];
-            unit_begin[f + 1] = s;
-        }
+constexpr int kPlanThreads = kMaxLaunchFrames;   // one thread per frame
+
+__device__ __forceinline__ int tiles_at(int c, int r, int tile_cap) {
+    const int r_min = (c + tile_cap - 1) / tile_cap;   // at most tile_cap tiles per frame
+    const int rr = r > r_min ? r : r_min;
+    return (c + rr - 1) / rr;
+}
+
+// Work units of the restricted vote (one CTA).  Frame f's c_f active pairs
+// are split evenly over T_f tiles.  The persistent vote runs `slots` CTAs, so
+// U = sum T_f units take ceil(U / slots) waves, each as long as its largest
+// unit.  With the largest tile pmax the batch needs at least
+// k = ceil(sum ceil(c_f / pmax) / slots) waves; the plan keeps k and takes the
+// smallest pairs per tile r whose units still fit k * slots: T_f =
+// ceil(c_f / r) (never more than tile_cap tiles), so the last wave is full
+// and every unit is as short as the wave count allows.  Writes tiles[f] and
+// the prefix unit_begin [n + 1].
+__global__ void __launch_bounds__(kPlanThreads) plan_units_kernel(const int32_t *pair_count, int n, int pmax,
+                                                                  int tile_cap, int slots, int32_t *tiles,
+                                                                  int32_t *unit_begin) {
+    __shared__ int warp_sum[kPlanThreads / 32];
+    __shared__ int r_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = tid < n ? pair_count[tid] : 0;
+    auto block_sum = [&](int v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        __syncthreads();
+        if (lane == 0) warp_sum[warp] = v;
+        __syncthreads();
+        int t = 0;
+        for (int i = 0; i < kPlanThreads / 32; ++i) t += warp_sum[i];
+        return t;
+    };
+    const int u_min = block_sum(tid < n ? tiles_at(c, pmax, tile_cap) : 0);
+    const int budget = (u_min + slots - 1) / slots * slots;
+    if (tid == 0) r_s = pmax;
+    for (int r = pmax - 1; r >= 1; --r) {   // block-uniform loop; U(r) grows as r falls
+        const int u = block_sum(tid < n ? tiles_at(c, r, tile_cap) : 0);
+        if (u > budget) break;
+        if (tid == 0) r_s = r;
     }
+    __syncthreads();
+    const int t = tid < n ? tiles_at(c, r_s, tile_cap) : 0;
+    // inclusive prefix over the frames (n <= kPlanThreads)
+    int v = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += y;
+    }
+    __syncthreads();
+    if (lane == 31) warp_sum[warp] = v;
+    __syncthreads();
+    for (int i = 0; i < warp; ++i) v += warp_sum[i];
+    if (tid < n) {
+        tiles[tid] = t;
+        unit_begin[tid + 1] = v;
+    }
+    if (tid == 0) unit_begin[0] = 0;
 }
 
 // Training targets from a frame's peaks (one CTA per frame).  A peak counts
@@ -119,13 +166,14 @@ __global__ void __launch_bounds__(256) targets_kernel(const ld_peak *peaks, cons
 }  // namespace
 
 cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p_band, float p_fallback, int margin,
-                                int pairs_per_tile, int32_t *pair_list, int32_t *pair_count, int32_t *fallback,
-                                int32_t *tiles, int32_t *unit_begin, cudaStream_t s) {
-    select_bands_kernel<<<n, 256, 0, s>>>(logits, n_theta, p_band, p_fallback, margin, pairs_per_tile, pair_list,
-                                          pair_count, fallback, tiles);
+                                int pmax, int tile_cap, int slots, int32_t *pair_list, int32_t *pair_count,
+                                int32_t *fallback, int32_t *tiles, int32_t *unit_begin, cudaStream_t s) {
+    if (n < 1 || n > kPlanThreads || pmax < 1 || tile_cap < 1 || slots < 1) return cudaErrorInvalidValue;
+    select_bands_kernel<<<n, 256, 0, s>>>(logits, n_theta, p_band, p_fallback, margin, pair_list, pair_count,
+                                          fallback);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    prefix_kernel<<<1, 32, 0, s>>>(tiles, n, unit_begin);
+    plan_units_kernel<<<1, kPlanThreads, 0, s>>>(pair_count, n, pmax, tile_cap, slots, tiles, unit_begin);
     return cudaGetLastError();
 }
 

@@ -282,7 +282,7 @@ def ld_proposal_targets(d_peaks, d_n_peaks, n, top_k, w, h, n_theta, always_k, r
                                       stream))
 
 
-def proposal_params(p_band=0.05, p_fallback=0.5, margin=2) -> ld_proposal_params:
+def proposal_params(p_band=0.2, p_fallback=0.5, margin=2) -> ld_proposal_params:
     q = ld_proposal_params()
     q.p_band, q.p_fallback, q.margin, q.reserved = p_band, p_fallback, margin, 0
     return q
@@ -480,7 +480,7 @@ class Context:
         return out
 
     def edge_pool(self, frames, p: ld_params, widths=None, out=None, stream=None):
-        """8x8 OR-pooled edge maps of equal-size frames: uint8 [n][ceil(h/8)][ceil(w/8)]."""
+        """Edge pixels per 8x8 block (0..64) of equal-size frames: uint8 [n][ceil(h/8)][ceil(w/8)]."""
         torch = _torch()
         descs = self._descs(frames, widths)
         w, h = descs[0][1], descs[0][2]

@@ -12,11 +12,12 @@ predictable from the image; restricted voting is exact for any superset).  Input
 (generation, Sobel, voting, targets, network forward/backward, Adam) runs in
 libld.so's kernels.
 
-  python -m paper_2212_09460_gb300.train_proposal --steps 3125 --batch 64 \
-      --out paper_2212_09460_gb300/weights/proposal_1080p.npz
+  python -m paper_2212_09460_gb300.train_proposal --steps 25000 --batch 64 \
+      --lr 3e-3 --out paper_2212_09460_gb300/weights/proposal_1080p.npz
   python -m paper_2212_09460_gb300.train_proposal --eval FILE --frames 10000
 
-Training seeds: 1_000_000 + i; held-out evaluation seeds: 9_000_000 + i.
+Training seeds: 1_000_000 + (i mod 200_000) (25000 steps of 64 = 8 epochs over
+the 200k training frames); held-out evaluation seeds: 9_000_000 + i.
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ from .proposal import ProposalNet
 W, H, N_THETA, TOP_K = 1920, 1080, 360, 4
 LABEL_TOP_K, LABEL_ALWAYS, LABEL_REL = 16, 4, 0.4
 TRAIN_SEED0, EVAL_SEED0 = 1_000_000, 9_000_000
+TRAIN_FRAMES = 200_000
 
 
 class FrameSource:
@@ -63,11 +65,13 @@ def labelled_batch(torch, ctx, src, seeds, p):
 
 
 def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every: int = 100,
-          checkpoint_every: int = 0, resume: str | None = None):
-    """Train for `steps` steps of `batch` device-generated frames (step k uses
-    frames TRAIN_SEED0 + k*batch ...).  Every checkpoint_every steps the
-    network and Adam's state go to out + ".ckpt.npz"; resume continues from
-    such a file at its step, reproducing the uninterrupted run bit for bit."""
+          checkpoint_every: int = 0, resume: str | None = None, train_frames: int = TRAIN_FRAMES):
+    """Train for `steps` steps of `batch` device-generated frames drawn from the
+    train_frames training frames in order (step k uses frames
+    TRAIN_SEED0 + (k*batch mod train_frames) ..., so more steps are more
+    epochs over the same frames).  Every checkpoint_every steps the network
+    and Adam's state go to out + ".ckpt.npz"; resume continues from such a
+    file at its step, reproducing the uninterrupted run bit for bit."""
     import torch
     dev = torch.device("cuda", 0)
     p = ld.params(n_theta=N_THETA, top_k=TOP_K, border=ld.LD_BORDER_CLEAR)
@@ -77,7 +81,7 @@ def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every:
     t0 = time.time()
     with ld.Context(0) as ctx:
         for step in range(net.step_count, steps):
-            seeds = TRAIN_SEED0 + step * batch + np.arange(batch)
+            seeds = TRAIN_SEED0 + (step * batch + np.arange(batch)) % train_frames
             _, pool, tgt = labelled_batch(torch, ctx, src, seeds, p)
             cur_lr = lr * 0.5 * (1 + math.cos(math.pi * step / steps))      # cosine decay
             loss = net.train_step(pool, tgt, cur_lr)
@@ -91,7 +95,7 @@ def train(steps: int, batch: int, lr: float, out: str, seed: int = 0, log_every:
     return net, log
 
 
-def evaluate(weights: str, frames: int, batch: int = 64, p_band=0.05, p_fallback=0.5, margin=2):
+def evaluate(weights: str, frames: int, batch: int = 64, p_band=0.2, p_fallback=0.5, margin=2):
     """Proposal vs plain on held-out frames: peak agreement, fallback rate,
     voted fraction, and device time of both paths (frames resident)."""
     import torch
@@ -137,13 +141,13 @@ def evaluate(weights: str, frames: int, batch: int = 64, p_band=0.05, p_fallback
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=3125)
+    ap.add_argument("--steps", type=int, default=25000)
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--out", default="proposal_1080p.npz")
     ap.add_argument("--eval", default=None, help="weights file to evaluate instead of training")
     ap.add_argument("--frames", type=int, default=10000)
-    ap.add_argument("--p-band", type=float, default=0.05)
+    ap.add_argument("--p-band", type=float, default=0.2)
     ap.add_argument("--p-fallback", type=float, default=0.5)
     ap.add_argument("--margin", type=int, default=2)
     ap.add_argument("--checkpoint-every", type=int, default=0, help="steps between resumable checkpoints")

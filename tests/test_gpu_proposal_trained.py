@@ -1,9 +1,12 @@
 """What the trained proposal network gains over the plain method.
 
-With the committed weights (trained on 200k synthetic 1080p frames labelled by
-the plain path), on held-out frames the proposal path must return the same
-peaks as the full vote on almost every frame while voting only part of the
-theta range, and must take less device time than the plain path."""
+With the committed weights (8 epochs over 200k synthetic 1080p frames labelled
+by the plain path with the frame border cleared), on held-out frames in the
+same setting and with the default band thresholds, the proposal path must
+return the same peaks as the full vote on at least 99% of 256 frames (the
+10k-frame rate is 99.9%, so more than 2 misses in 256 is a regression) while
+voting under 35% of the theta range, and must take less device time than the
+plain path."""
 import os
 
 import numpy as np
@@ -20,7 +23,7 @@ def test_trained_proposal_matches_plain_and_saves_work(ctx, ldlib):
     from paper_2212_09460_gb300 import train_proposal as tp
     from paper_2212_09460_gb300.proposal import ProposalNet
     net = ProposalNet.load(WEIGHTS, 0)
-    p = ldlib.params(n_theta=360, top_k=4, border=1)
+    p = ldlib.params(n_theta=360, top_k=4, border=ldlib.LD_BORDER_CLEAR)
     src = tp.FrameSource(torch, torch.device("cuda", 0), 64)
     agree = total = 0
     voted = []
@@ -47,6 +50,6 @@ def test_trained_proposal_matches_plain_and_saves_work(ctx, ldlib):
             total += 1
             agree += int(pn[i] == qn[i] and np.array_equal(ppk[i, : pn[i]], qpk[i, : qn[i]]))
         voted.extend(qact / 180.0)
-    assert agree / total >= 0.98, (agree, total)
-    assert np.mean(voted) < 0.6
+    assert agree / total >= 0.99, (agree, total)
+    assert np.mean(voted) < 0.35
     assert t_prop < t_plain
