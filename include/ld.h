@@ -208,7 +208,8 @@ LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
  * h_frames (device images, as in ld_detect_batch), it times ld_detect_batch
  * on the frames of that size, `iters` calls per candidate: first the voting
  * stage for each candidate voting tile size (theta pairs per CTA: the
- * compiled sizes from 1/8 of the largest that fits shared memory up to it),
+ * compiled sizes from 1/8 of the largest that fits shared memory up to it,
+ * and the interleaved-column kernel where it fits and min_votes >= 1),
  * then the Sobel stage for each run length (1, 2 or 4 groups of 8 rows per
  * warp), and keeps the fastest of each in the context; later ld_detect_batch
  * calls on frames of that size and n_theta use them.  Results do not depend
@@ -221,7 +222,9 @@ LD_API ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
 
 /* The voting tile size (theta pairs per CTA) and the Sobel run length (in
  * groups of 8 rows per warp) that ld_detect_batch uses for w x h frames with
- * p->n_theta (tuned or default). */
+ * p->n_theta (tuned or default).  *pairs_per_tile is negative (minus the
+ * pairs per tile) when the interleaved-column voting kernel votes (tiles of
+ * up to 16 pairs; a launch group uses it only if every frame's plan does). */
 LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *p,
                              int32_t *pairs_per_tile, int32_t *sobel_rows);
 

@@ -83,12 +83,16 @@ struct ld_ctx {
     std::map<int, std::vector<int32_t>> trig_host;
     DevBuf edges, small, cand;            // detect_batch / hough_peaks scratch
     DevBuf prop;                          // proposal path: edge-count maps, activations, pair lists
+    DevBuf part;                          // interleaved voting: split tiles' partial accumulators + counters
     std::vector<cudaEvent_t> ev;   // 3 events per timed call, reused in order
     int timed_calls = 0;           // timed calls since the last ld_ctx_stage_ms
     bool timing = false;
-    // autotuned plans: (w, h, n_theta) -> (theta pairs per tile, Sobel rows per warp)
+    // autotuned plans: (w, h, n_theta) -> (theta pairs per tile, Sobel rows per
+    // warp); pairs -1 selects the interleaved-column voting kernel
     std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     int force_pairs = 0, force_rows = 0;   // set while the autotuner times candidates
+    // (w, h, n_theta) -> rows of the interleaved-column accumulator
+    mutable std::map<std::tuple<int, int, int>, int> col_rows;
     std::mutex mu;
 };
 
@@ -223,8 +227,18 @@ Small small_of(void *p) {
     return {b, b + kMaxLaunchFrames, b + 2 * kMaxLaunchFrames, b + 3 * kMaxLaunchFrames};
 }
 
+// Split tiles of the interleaved voting kernel: at most num_sms pieces in a
+// launch; scratch = the pieces' arrival counters (one per tile, 256-byte
+// padded) then their partial accumulators.
+constexpr int kMaxSplits = 8;
+size_t split_scratch_bytes(int pieces, int rows) {
+    return ((size_t)pieces * 4 + 255) / 256 * 256 + (size_t)pieces * rows * kHoughColPairs * 4;
+}
+
 struct HoughPlan {
     int n_rho, D, pairs, n_tiles;
+    bool cols = false;   // interleaved-column kernel (tiles of <= kHoughColPairs pairs)
+    int rows = 0;        // its accumulator rows
 };
 
 HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
@@ -293,10 +307,62 @@ HoughPlan plan_hough(int w, int h, int n_theta) {
     return hp;
 }
 
-HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta) {
-    if (ctx->force_pairs > 0) return plan_with_pairs(w, h, n_theta, ctx->force_pairs);
-    auto it = ctx->tuned.find(std::make_tuple(w, h, n_theta));
-    if (it != ctx->tuned.end()) return plan_with_pairs(w, h, n_theta, it->second.first);
+// Rows of the interleaved-column accumulator for w x h frames: the widest
+// theta window, max - min + 1 over the image corners of
+// floor((x c + y s + 32768) / 65536), over the thetas the kernel votes
+// ((c_k, s_k) for k <= n/2 from the table, (-c_k, s_k) for n/2 < n - k < n).
+int interleaved_rows(const ld_ctx *ctx, int w, int h, int n_theta) {
+    const auto key = std::make_tuple(w, h, n_theta);
+    auto it = ctx->col_rows.find(key);
+    if (it != ctx->col_rows.end()) return it->second;
+    const std::vector<int32_t> t = make_trig(n_theta);
+    const int half = n_theta / 2;
+    auto fl = [](int64_t v) { return v >= 0 ? v / 65536 : -((-v + 65535) / 65536); };
+    int64_t rows = 1;
+    for (int k = 0; k < n_theta; ++k) {
+        const int kk = k <= half ? k : n_theta - k;
+        const int64_t c = k <= half ? t[2 * kk] : -t[2 * kk];
+        const int64_t s = t[2 * kk + 1];
+        const int64_t xlo = c < 0 ? (w - 1) * c : 0, xhi = c < 0 ? 0 : (w - 1) * c;
+        const int64_t ylo = s < 0 ? (h - 1) * s : 0, yhi = s < 0 ? 0 : (h - 1) * s;
+        rows = std::max(rows, fl(xhi + yhi + 32768) - fl(xlo + ylo + 32768) + 1);
+    }
+    const int r = (int)std::min<int64_t>(rows, 1 << 30);
+    ctx->col_rows[key] = r;
+    return r;
+}
+
+// The interleaved-column plan (tiles of at most kHoughColPairs pairs, split
+// evenly), or a plan with cols == false if its accumulator does not fit.
+HoughPlan plan_cols(const ld_ctx *ctx, int w, int h, int n_theta) {
+    HoughPlan hp;
+    hp.D = (int)rho_max_of(w, h);
+    hp.n_rho = 2 * hp.D + 1;
+    const int n_pairs = n_theta / 2;
+    hp.n_tiles = (n_pairs + kHoughColPairs - 1) / kHoughColPairs;
+    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
+    hp.rows = interleaved_rows(ctx, w, h, n_theta);
+    hp.cols = hp.rows <= hough_cols_max_rows();
+    return hp;
+}
+
+// The voting plan of w x h frames.  allow_cols: the launch may use the
+// interleaved-column kernel (full vote in candidate mode with min_votes >= 1,
+// where cells outside a theta's window, which it does not hold, cannot be
+// candidates).  Forced (autotuner), else tuned, else the interleaved kernel
+// when it fits and its tiles hold at least 12 pairs on average (a lane per
+// pair: emptier tiles leave lanes idle), else the packed-pair plan.
+HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta, bool allow_cols) {
+    int pairs = ctx->force_pairs;
+    if (pairs == 0) {
+        auto it = ctx->tuned.find(std::make_tuple(w, h, n_theta));
+        if (it != ctx->tuned.end()) pairs = it->second.first;
+    }
+    if (pairs > 0) return plan_with_pairs(w, h, n_theta, pairs);
+    if (allow_cols) {
+        const HoughPlan hc = plan_cols(ctx, w, h, n_theta);
+        if (hc.cols && (pairs == -1 || n_theta >= 24 * hc.n_tiles)) return hc;
+    }
     return plan_hough(w, h, n_theta);
 }
 
@@ -361,6 +427,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->small.release();
         ctx->cand.release();
         ctx->prop.release();
+        ctx->part.release();
     }
     delete ctx;
     return LD_OK;
@@ -404,6 +471,8 @@ ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames, in
     int64_t nc = groups_frames * per_frame;
     if (acc_chunks * cand_m(p) > nc) nc = acc_chunks * cand_m(p);
     if (!ctx->cand.ensure((size_t)nc * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    if (max_frames > 0 && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hough_cols_max_rows())))
+        return fail(LD_ERR_NOMEM, "scratch partial accumulators");
     return LD_OK;
 }
 
@@ -632,8 +701,9 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         int64_t ed = 0, ca = 0;
         for (int i = g0; i < g1; ++i) {
             ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
-            const int T0 = plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles;
-            ca += (int64_t)std::min(p.n_theta / 2, T0 + (T0 + 3) / 4) * M;   // room for balance_tiles
+            const int T0 = plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta, false).n_tiles;
+            const int Tc = (p.n_theta / 2 + kHoughColPairs - 1) / kHoughColPairs;
+            ca += (int64_t)std::max(Tc, std::min(p.n_theta / 2, T0 + (T0 + 3) / 4)) * M;   // room for balance_tiles
         }
         if (ed > max_edges) max_edges = ed;
         if (ca > max_cand) max_cand = ca;
@@ -667,11 +737,21 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         coffs.assign(gn, 0);
         plans.resize(gn);
         int64_t eoff = 0, coff = 0;
-        for (int k = 0; k < gn; ++k) {
+        // one voting kernel per launch: the interleaved-column one only if
+        // every frame of the group gets an interleaved plan
+        bool cols = p.min_votes >= 1;
+        for (int k = 0; k < gn && cols; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
-            plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta);
+            plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, true);
+            cols = plans[k].cols;
         }
-        balance_tiles(plans, p.n_theta / 2, ctx->num_sms);
+        if (!cols) {
+            for (int k = 0; k < gn; ++k) {
+                const ld_frame &fr = h_frames[g0 + k];
+                plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
+            }
+            balance_tiles(plans, p.n_theta / 2, ctx->num_sms);
+        }
         for (int k = 0; k < gn; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
             eoffs[k] = eoff;
@@ -706,6 +786,40 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             const int64_t cb = (int64_t)h_frames[g0 + b].w * h_frames[g0 + b].h * plans[b].pairs;
             return ca > cb;
         });
+        // Interleaved kernel: when the launch's last wave would be at most half
+        // full, split each tile of the last frames in queue order (together
+        // at least as many tiles as that wave holds) into ns edge ranges
+        // (pieces, at most num_sms in all), which spread over the wave.
+        int split_from = gn, ns_split = 1, split_tiles = 0, rows_max = 1;
+        if (cols) {
+            int U0 = 0;
+            for (int k = 0; k < gn; ++k) {
+                U0 += plans[k].n_tiles;
+                rows_max = std::max(rows_max, plans[k].rows);
+            }
+            const int S = ctx->num_sms, tail = U0 % S;
+            if (U0 > S && tail > 0 && 2 * tail <= S) {
+                int q = gn, units = 0;
+                while (q > 0 && units < tail) units += plans[order[--q]].n_tiles;
+                const int ns = std::min(kMaxSplits, S / units);
+                if (ns >= 2) {
+                    split_from = q;
+                    ns_split = ns;
+                    split_tiles = units;
+                }
+            }
+            HLn.col_chunk = hough_cols_chunk(rows_max);
+            HLn.part_stride = rows_max * kHoughColPairs;
+            if (split_tiles > 0) {
+                const size_t cnt_bytes = ((size_t)split_tiles * 4 + 255) / 256 * 256;
+                if (!ctx->part.ensure(split_scratch_bytes(split_tiles * ns_split, rows_max)))
+                    return fail(LD_ERR_NOMEM, "scratch partial accumulators");
+                HLn.tile_cnt = (int32_t *)ctx->part.p;
+                HLn.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
+                e = cudaMemsetAsync(ctx->part.p, 0, (size_t)split_tiles * 4, s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(split counters)");
+            }
+        }
         HLn.n = gn;
         HLn.n_theta = p.n_theta;
         HLn.mode = kHoughCandidates;
@@ -716,7 +830,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         HLn.nms_rho = p.nms_rho;
         HLn.trig = dt;
         HLn.queue = sm.queue;
-        int units = 0, pmax = 1;
+        int units = 0, pmax = 1, split_base = 0;
         int64_t words_max = 0;
         for (int q = 0; q < gn; ++q) {
             const int k = order[q];
@@ -738,10 +852,13 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             HF.D = hp.D;
             HF.n_rho = hp.n_rho;
             HF.unit_begin = units;
-            HF.n_splits = 1;
+            HF.n_splits = q >= split_from ? ns_split : 1;
+            HF.split_base = HF.n_splits > 1 ? split_base : 0;
+            if (HF.n_splits > 1) split_base += hp.n_tiles;
             HF.pairs_per_tile = hp.pairs;
             HF.n_tiles = hp.n_tiles;
-            units += hp.n_tiles;
+            HF.rows = hp.rows;
+            units += hp.n_tiles * HF.n_splits;
             if (hp.pairs > pmax) pmax = hp.pairs;
             const int64_t wds = (int64_t)hp.pairs * hp.n_rho;
             if (wds > words_max) words_max = wds;
@@ -765,7 +882,8 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         e = launch_sobel(SLn, sob_ctas, s);
         if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
         if (tev) cudaEventRecord(tev[1], s);
-        e = launch_hough(HLn, hough_ctas, pmax, words_max, s);
+        e = cols ? launch_hough_cols(HLn, hough_ctas, rows_max, s)
+                 : launch_hough(HLn, hough_ctas, pmax, words_max, s);
         if (e != cudaSuccess) return cuda_fail(e, "hough launch");
         if (tev) cudaEventRecord(tev[2], s);
     }
@@ -938,7 +1056,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
             return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
     }
     const int M = cand_m(p);
-    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta);
+    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta, false);   // restricted vote: packed-pair kernel
     const int n_pairs = p.n_theta / 2;
     const int64_t epf = ((int64_t)w * h + 3) / 4 * 4;
     if (!ctx->edges.ensure((size_t)(n * epf) * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
@@ -1063,8 +1181,8 @@ ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *pp, in
     st = check_size(w, h, p, nullptr);
     if (st != LD_OK) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta);
-    if (pairs_per_tile) *pairs_per_tile = hp.pairs;
+    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta, p.min_votes >= 1);
+    if (pairs_per_tile) *pairs_per_tile = hp.cols ? -hp.pairs : hp.pairs;
     if (sobel_rows) {
         const ld_frame f = {nullptr, w, h, w, 0};
         *sobel_rows = rows_for(ctx, &f, 0, 1, p.n_theta);
@@ -1107,6 +1225,7 @@ ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         LD_HOUGH_PAIR_SIZES(LD_CAND)
 #undef LD_CAND
         if (pair_cands.empty()) pair_cands.push_back(std::max(1, pmax));
+        if (p.min_votes >= 1 && plan_cols(ctx, w, h, p.n_theta).cols) pair_cands.push_back(-1);   // interleaved
         // the voting tile size by the voting stage's time, then the Sobel run
         // length by the Sobel stage's time (the two stages are independent)
         auto time_stage = [&](int P, int R, int stage, float *out) -> ld_status {

@@ -63,6 +63,10 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void red_add_shared(uint32_t *addr, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(addr)), "r"(v) : "memory");
 }
+// The same at a 32-bit shared-window address.
+__device__ __forceinline__ void red_add_shared_at(uint32_t saddr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -96,6 +100,211 @@ __device__ __forceinline__ void ordered_col(int q, int np, bool has0, int &slot,
     half = 1;
     if (has0) slot = (q2 == 0) ? 0 : np - q2;
     else slot = np - 1 - q2;
+}
+
+// Accumulator layouts of a tile, for the candidate selection.  A tile holds
+// np theta pairs (slots); each 32-bit word packs two 16-bit counts, the low
+// half for theta_lo(slot) and the high half for theta_hi(slot).
+//
+// PairRowLayout: slot p's words are p * n_rho + rho (rho index of both halves).
+struct PairRowLayout {
+    int n_rho;
+    // word i -> its slot and the rho index of its low / high count
+    __device__ __forceinline__ void cells(int i, int &slot, int &rho_lo, int &rho_hi) const {
+        slot = i / n_rho;
+        rho_lo = rho_hi = i - slot * n_rho;
+    }
+    __device__ __forceinline__ int col_len() const { return n_rho; }   // rows of one theta column
+    __device__ __forceinline__ int word(int slot, int row) const { return slot * n_rho + row; }
+    __device__ __forceinline__ int rho(int slot, int half, int row) const { return row; }
+};
+
+// InterleavedLayout: word row * kCols + slot; row r of slot p holds the count
+// of theta_lo(p) at rho index r + lo[p] and of theta_hi(p) at r + hi[p] (each
+// theta's rho window starts at its own minimum over the image).
+constexpr int kCols = kHoughColPairs;
+struct InterleavedLayout {
+    const int *lo, *hi;   // shared memory: rho index of row 0 per slot and half
+    int rows;
+    __device__ __forceinline__ void cells(int i, int &slot, int &rho_lo, int &rho_hi) const {
+        slot = i % kCols;
+        const int row = i / kCols;
+        rho_lo = row + lo[slot];
+        rho_hi = row + hi[slot];
+    }
+    __device__ __forceinline__ int col_len() const { return rows; }
+    __device__ __forceinline__ int word(int slot, int row) const { return row * kCols + slot; }
+    __device__ __forceinline__ int rho(int slot, int half, int row) const { return row + (half ? hi[slot] : lo[slot]); }
+};
+
+// Exact local top-M (order: votes desc, theta asc, rho asc) of a tile's
+// `words` accumulator words, written as keys to out[0..M) (unused slots 0).
+// Every cell of a theta column that the layout does not hold must have 0 votes
+// and min_votes >= 1, or be held.  The edge ring is free and serves as scratch
+// (at least 4 * blockDim.x + 8 * 2048 bytes).  Every thread calls it.
+template <class Lay>
+__device__ void select_tile(const HoughLaunch &L, uint64_t *out, const uint32_t *acc, int words, int np, bool has0,
+                            const int *tj, const Lay &lay, SelectSmem &S, uint32_t *ring) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    const int n_theta = L.n_theta;
+    const int M = L.cand_m;
+    const int32_t mv = L.min_votes;
+
+    // pass 0: included count, per-thread maximum, overall maximum
+    int cnt = 0;
+    int tmax = -1;
+    for (int i = tid; i < words; i += nthr) {
+        const uint32_t wv = acc[i];
+        const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+        if (a >= mv) { ++cnt; tmax = max(tmax, a); }
+        if (b >= mv) { ++cnt; tmax = max(tmax, b); }
+    }
+    const int total = block_sum(cnt, S);
+    uint32_t vmax = tmax < 0 ? 0u : (uint32_t)tmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+    if (lane == 0) S.red[warp] = vmax;
+    __syncthreads();
+    uint32_t gmax = 0;
+    for (int w = 0; w < nwarps; ++w) gmax = max(gmax, S.red[w]);
+    __syncthreads();
+
+    // Fast path.  L = the M-th largest of the per-thread maxima: M distinct
+    // cells have votes >= L, so every top-M cell does too.  The cells with
+    // votes >= L ("survivors", usually a few hundred) are compacted as keys,
+    // which are unique and ordered like the peaks, and the first M keys of
+    // their descending sort are exactly the tile's top-M.  Too many
+    // survivors: the general path.
+    constexpr int kMaxSurv = 2048;
+    if (total > M && M <= nthr) {
+        int *tm = reinterpret_cast<int *>(ring);
+        uint64_t *keys = reinterpret_cast<uint64_t *>(ring + nthr);
+        tm[tid] = tmax;
+        if (tid == 0) S.surv = 0;
+        __syncthreads();
+        block_sort_desc(tm, nthr);
+        const int Lth = tm[M - 1];
+        if (Lth >= 0) {   // block-uniform
+            for (int i = tid; i < words; i += nthr) {
+                const uint32_t wv = acc[i];
+                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+                if (a >= Lth || b >= Lth) {
+                    int p, ra, rb;
+                    lay.cells(i, p, ra, rb);
+                    if (a >= Lth) {
+                        const int slot = atomicAdd(&S.surv, 1);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(a, theta_lo(tj, p), ra);
+                    }
+                    if (b >= Lth) {
+                        const int slot = atomicAdd(&S.surv, 1);
+                        if (slot < kMaxSurv) keys[slot] = peak_key(b, theta_hi(tj, p, n_theta), rb);
+                    }
+                }
+            }
+            __syncthreads();
+            const int ns_ = S.surv;
+            if (ns_ <= kMaxSurv) {   // block-uniform
+                int n2 = 1;
+                while (n2 < ns_) n2 <<= 1;
+                for (int i = ns_ + tid; i < n2; i += nthr) keys[i] = 0ull;
+                __syncthreads();
+                block_sort_desc(keys, n2);
+                for (int i = tid; i < M; i += nthr) out[i] = keys[i];
+                return;
+            }
+        }
+        __syncthreads();
+    }
+
+    const bool all_in = total <= M;
+    if (tid == 0) {
+        S.prefix = 0x80000000u;
+        S.pmask = 0xFFFF0000u;
+        S.rank = M;
+        S.out_n = 0;
+    }
+    __syncthreads();
+    if (!all_in) {
+        int top_shift = 0;   // highest nibble holding a set bit of the max count
+        for (int s = 12; s > 0; s -= 4)
+            if (gmax >> s) { top_shift = s; break; }
+        for (int shift = top_shift; shift >= 0; shift -= 4) {
+            uint32_t wh[16];
+#pragma unroll
+            for (int d = 0; d < 16; ++d) wh[d] = 0;
+            const uint32_t prefix = S.prefix, pmask = S.pmask;
+            for (int base = 0; base < words; base += nthr) {
+                const int i = base + tid;
+                const uint32_t wv = (i < words) ? acc[i] : 0u;
+                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+                const uint32_t ua = (uint32_t)a ^ 0x80000000u, ub = (uint32_t)b ^ 0x80000000u;
+                ballot_digits(wh, i < words && a >= mv && (ua & pmask) == prefix, (ua >> shift) & 15u);
+                ballot_digits(wh, i < words && b >= mv && (ub & pmask) == prefix, (ub >> shift) & 15u);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int d = 0; d < 16; ++d) S.hist[warp][d] = wh[d];
+            }
+            select_digit(S, shift);
+        }
+    }
+    const uint32_t ustar = S.prefix;
+    const int need = all_in ? 0 : S.rank;   // cells equal to u* to take, in order
+    __syncthreads();
+
+    // ordered emission over per-thread contiguous ranges of the ordered cells
+    // (theta columns ascending, rho ascending inside a column)
+    const int clen = lay.col_len();
+    const int64_t ncell = 2 * (int64_t)np * clen;
+    const int64_t r0 = ncell * tid / nthr, r1 = ncell * (tid + 1) / nthr;
+    auto cell_at = [&](int64_t li, int &theta, int &rho) -> int32_t {
+        const int q = (int)(li / clen);
+        const int row = (int)(li - (int64_t)q * clen);
+        int slot, half;
+        ordered_col(q, np, has0, slot, half);
+        theta = half ? theta_hi(tj, slot, n_theta) : theta_lo(tj, slot);
+        rho = lay.rho(slot, half, row);
+        const uint32_t wv = acc[lay.word(slot, row)];
+        return (int32_t)(half ? (wv >> 16) : (wv & 0xFFFFu));
+    };
+    int ties = 0;
+    if (!all_in) {
+        for (int64_t li = r0; li < r1; ++li) {
+            int th, rh;
+            const int32_t v = cell_at(li, th, rh);
+            ties += (v >= mv && ((uint32_t)v ^ 0x80000000u) == ustar);
+        }
+    }
+    // exclusive block scan of the tie counts
+    int incl = ties;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) S.red[warp] = (uint32_t)incl;
+    __syncthreads();
+    int woff = 0;
+    for (int w = 0; w < warp; ++w) woff += (int)S.red[w];
+    int trank = woff + incl - ties;
+    for (int64_t li = r0; li < r1; ++li) {
+        int th, rh;
+        const int32_t v = cell_at(li, th, rh);
+        if (v < mv) continue;
+        const uint32_t u = (uint32_t)v ^ 0x80000000u;
+        if (all_in || u > ustar) {
+            const int slot = atomicAdd(&S.out_n, 1);
+            if (slot < M) out[slot] = peak_key(v, th, rh);
+        } else if (u == ustar) {
+            if (trank < need) out[(M - need) + trank] = peak_key(v, th, rh);
+            ++trank;
+        }
+    }
+    __syncthreads();
+    // unused slots (fewer included cells than M) are empty keys
+    const int filled = all_in ? min(S.out_n, M) : M;
+    for (int i = filled + tid; i < M; i += nthr) out[i] = 0ull;
 }
 
 // Votes of one edge pixel (x, y) into the tile's packed accumulator.  For
@@ -278,160 +487,7 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
     }
 
     // ---- candidate mode: exact local top-M of this tile (see ld_select.cuh)
-    const int M = L.cand_m;
-    const int32_t mv = L.min_votes;
-    uint64_t *out = F.cand + (size_t)tile * M;
-
-    // pass 0: included count, per-thread maximum, overall maximum
-    int cnt = 0;
-    int tmax = -1;
-    for (int i = tid; i < words; i += kHoughThreads) {
-        const uint32_t wv = acc[i];
-        const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-        if (a >= mv) { ++cnt; tmax = max(tmax, a); }
-        if (b >= mv) { ++cnt; tmax = max(tmax, b); }
-    }
-    const int total = block_sum(cnt, S);
-    uint32_t vmax = tmax < 0 ? 0u : (uint32_t)tmax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
-    if (lane == 0) S.red[warp] = vmax;
-    __syncthreads();
-    uint32_t gmax = 0;
-    for (int w = 0; w < kHoughWarps; ++w) gmax = max(gmax, S.red[w]);
-    __syncthreads();
-
-    // Fast path.  L = the M-th largest of the per-thread maxima: M distinct
-    // cells have votes >= L, so every top-M cell does too.  The cells with
-    // votes >= L ("survivors", usually a few hundred) are compacted as keys,
-    // which are unique and ordered like the peaks, and the first M keys of
-    // their descending sort are exactly the tile's top-M.  The edge ring is
-    // free now and holds the scratch.  Too many survivors: the general path.
-    constexpr int kMaxSurv = 2048;
-    if (total > M && M <= kHoughThreads) {
-        int *tm = reinterpret_cast<int *>(ring);
-        uint64_t *keys = reinterpret_cast<uint64_t *>(ring + kHoughThreads);
-        tm[tid] = tmax;
-        if (tid == 0) S.surv = 0;
-        __syncthreads();
-        block_sort_desc(tm, kHoughThreads);
-        const int Lth = tm[M - 1];
-        if (Lth >= 0) {   // block-uniform
-            for (int i = tid; i < words; i += kHoughThreads) {
-                const uint32_t wv = acc[i];
-                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-                if (a >= Lth || b >= Lth) {
-                    const int p = i / n_rho, r = i - p * n_rho;
-                    if (a >= Lth) {
-                        const int slot = atomicAdd(&S.surv, 1);
-                        if (slot < kMaxSurv) keys[slot] = peak_key(a, theta_lo(tj, p), r);
-                    }
-                    if (b >= Lth) {
-                        const int slot = atomicAdd(&S.surv, 1);
-                        if (slot < kMaxSurv) keys[slot] = peak_key(b, theta_hi(tj, p, n_theta), r);
-                    }
-                }
-            }
-            __syncthreads();
-            const int ns_ = S.surv;
-            if (ns_ <= kMaxSurv) {   // block-uniform
-                int n2 = 1;
-                while (n2 < ns_) n2 <<= 1;
-                for (int i = ns_ + tid; i < n2; i += kHoughThreads) keys[i] = 0ull;
-                __syncthreads();
-                block_sort_desc(keys, n2);
-                for (int i = tid; i < M; i += kHoughThreads) out[i] = keys[i];
-                return true;
-            }
-        }
-        __syncthreads();
-    }
-
-    const bool all_in = total <= M;
-    if (tid == 0) {
-        S.prefix = 0x80000000u;
-        S.pmask = 0xFFFF0000u;
-        S.rank = M;
-        S.out_n = 0;
-    }
-    __syncthreads();
-    if (!all_in) {
-        int top_shift = 0;   // highest nibble holding a set bit of the max count
-        for (int s = 12; s > 0; s -= 4)
-            if (gmax >> s) { top_shift = s; break; }
-        for (int shift = top_shift; shift >= 0; shift -= 4) {
-            uint32_t wh[16];
-#pragma unroll
-            for (int d = 0; d < 16; ++d) wh[d] = 0;
-            const uint32_t prefix = S.prefix, pmask = S.pmask;
-            for (int base = 0; base < words; base += kHoughThreads) {
-                const int i = base + tid;
-                const uint32_t wv = (i < words) ? acc[i] : 0u;
-                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-                const uint32_t ua = (uint32_t)a ^ 0x80000000u, ub = (uint32_t)b ^ 0x80000000u;
-                ballot_digits(wh, i < words && a >= mv && (ua & pmask) == prefix, (ua >> shift) & 15u);
-                ballot_digits(wh, i < words && b >= mv && (ub & pmask) == prefix, (ub >> shift) & 15u);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int d = 0; d < 16; ++d) S.hist[warp][d] = wh[d];
-            }
-            select_digit(S, shift);
-        }
-    }
-    const uint32_t ustar = S.prefix;
-    const int need = all_in ? 0 : S.rank;   // cells equal to u* to take, in order
-    __syncthreads();
-
-    // ordered emission over per-thread contiguous ranges of the ordered cells
-    const int64_t ncell = 2 * (int64_t)words;
-    const int64_t r0 = ncell * tid / kHoughThreads, r1 = ncell * (tid + 1) / kHoughThreads;
-    auto cell_at = [&](int64_t li, int &theta, int &rho) -> int32_t {
-        const int q = (int)(li / n_rho);
-        rho = (int)(li - (int64_t)q * n_rho);
-        int slot, half;
-        ordered_col(q, np, has0, slot, half);
-        theta = half ? theta_hi(tj, slot, n_theta) : theta_lo(tj, slot);
-        const uint32_t wv = acc[slot * n_rho + rho];
-        return (int32_t)(half ? (wv >> 16) : (wv & 0xFFFFu));
-    };
-    int ties = 0;
-    if (!all_in) {
-        for (int64_t li = r0; li < r1; ++li) {
-            int th, rh;
-            const int32_t v = cell_at(li, th, rh);
-            ties += (v >= mv && ((uint32_t)v ^ 0x80000000u) == ustar);
-        }
-    }
-    // exclusive block scan of the tie counts
-    int incl = ties;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) S.red[warp] = (uint32_t)incl;
-    __syncthreads();
-    int woff = 0;
-    for (int w = 0; w < warp; ++w) woff += (int)S.red[w];
-    int trank = woff + incl - ties;
-    for (int64_t li = r0; li < r1; ++li) {
-        int th, rh;
-        const int32_t v = cell_at(li, th, rh);
-        if (v < mv) continue;
-        const uint32_t u = (uint32_t)v ^ 0x80000000u;
-        if (all_in || u > ustar) {
-            const int slot = atomicAdd(&S.out_n, 1);
-            if (slot < M) out[slot] = peak_key(v, th, rh);
-        } else if (u == ustar) {
-            if (trank < need) out[(M - need) + trank] = peak_key(v, th, rh);
-            ++trank;
-        }
-    }
-    __syncthreads();
-    // unused slots (fewer included cells than M) are empty keys
-    const int filled = all_in ? min(S.out_n, M) : M;
-    for (int i = filled + tid; i < M; i += kHoughThreads) out[i] = 0ull;
+    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, has0, tj, PairRowLayout{n_rho}, S, ring);
     return true;
 }
 
@@ -490,6 +546,308 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
     }
 }
 
+
+// ---------------------------------------------------------------- interleaved columns
+//
+// Second voting kernel for the full-vote detection path.  Each 32-lane
+// red.shared of the kernel above hits 32 random words, and 32 random words
+// fall on about 3.5 distinct-bank wavefronts.  Here lane l of a warp owns
+// slot l % 16 of a tile of up to 16 theta pairs, and the tile's words are
+// interleaved (word = row * 16 + slot), so slot l lives in banks l and l + 16
+// only.  The two half-warps vote two different edges into the same 16 slots,
+// so one red.shared costs at most 2 wavefronts (2 when any slot's two rows
+// agree in parity, i.e. almost always), against about 3.5 for 32 random
+// words.  Each theta's rho window starts at its own
+// minimum over the image corners, so a column needs only the frame's widest
+// window (at most D + 1 rows) instead of 2D + 1: 16 pairs of a 1080p frame
+// take 141 KB.  Each lane holds the (cos, sin) of both thetas of its pair, so
+// the pair {0, n/2} needs no special case.  Edge lists are read as 16-byte
+// groups of 4 edges, one group per half-warp and loop step (a broadcast
+// load); the first half of each streamed chunk goes to half-warp 0 and the
+// second to half-warp 1, so that the two edges voted together lie far apart
+// in the row-major list (far-apart edges seldom share a cell).  The edge
+// ring has 2 stages of 8192 edges (4096 when the accumulator leaves less
+// room): fewer, larger chunks measured faster.  A launch whose last wave would
+// be poorly filled splits the tiles of its last frames into edge ranges
+// (pieces), which fill that wave.  The vote has
+// no per-edge branch (the kernel is issue-bound without the bank conflicts):
+// addresses are 32-bit shared-window offsets, the lanes of unused slots vote
+// into their own spare columns, which are cleared before the selection, and
+// coordinates are clamped into the image.  The clamp is a memory guard only:
+// this kernel votes edge lists written by the Sobel kernel, whose entries are
+// always inside the image.
+constexpr int kColThreads = 1024;
+constexpr int kColWarps = kColThreads / 32;
+constexpr int kColStages = 2;                 // edge ring stages of L.col_chunk edges
+constexpr int kColChunkMin = 4096, kColChunkMax = 8192;
+constexpr int kColRingMin = kColStages * kColChunkMin * 4;   // 32 KB
+static_assert(kColRingMin >= 4 * kColThreads + 8 * 2048, "ring too small for the selection scratch");
+
+// floor(v / 65536) of a signed value
+__device__ __forceinline__ int32_t floor_q16(int64_t v) {
+    return (int32_t)(v >= 0 ? v / 65536 : -((-v + 65535) / 65536));
+}
+// Smallest floor((x c + y s + 32768) / 65536) over the image (a corner).
+__device__ __forceinline__ int32_t window_min(int32_t c, int32_t s, int W, int H) {
+    const int64_t xm = c < 0 ? (int64_t)(W - 1) * c : 0;
+    const int64_t ym = s < 0 ? (int64_t)(H - 1) * s : 0;
+    return floor_q16(xm + ym + 32768);
+}
+// The same, also giving up once *abort is set (by another warp that gave up).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && *abort) return false;
+    }
+    return false;
+}
+
+// Ring state of a CTA of the interleaved kernel (shared memory).
+struct ColRing {
+    uint64_t bars[kColStages];   // full barriers (bytes landed)
+    uint32_t rel[kColStages];    // warps done with a stage, counted over the kernel
+    int issued_hi;               // chunks [0, issued_hi) of the current unit were issued
+};
+
+enum ColResult { kColAbort = -1, kColPiece = 0, kColTile = 1 };
+
+// One work unit of frame F: tile `tile`, edge range `split` of n_splits
+// (chunk-aligned).  A split tile's pieces store their partial accumulators in
+// L.part; the last piece to finish adds the others' and selects.  Returns
+// kColTile if this unit finished its tile (candidates written), kColPiece if
+// another piece will, kColAbort if a bounded wait gave up (the frame is
+// flagged; the CTA must stop).
+__device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame &F, int tile, int split,
+                                         uint32_t &seq, uint8_t *smem_raw, ColRing &R, SelectSmem &S,
+                                         int &abort_flag, int &last_s, int *tj, int *wlo, int *whi) {
+    const int n_theta = L.n_theta, n_tiles = F.n_tiles, ns = F.n_splits, chunk = L.col_chunk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_pairs = n_theta / 2;
+    const int base = n_pairs / n_tiles, extra = n_pairs % n_tiles;
+    const int np = base + (tile < extra ? 1 : 0);   // <= kCols (host plan)
+    const int j0 = tile * base + min(tile, extra);
+    const int W = F.w, H = F.h, D = F.D, rows = F.rows;
+
+    // per-lane constants: (c, s) and Q16 offset of both thetas of the lane's pair
+    const int slot = lane % kCols, half = lane / kCols;
+    const int j = slot < np ? j0 + slot : 0;   // unused slots: a spare column
+    const int32_t cl = L.trig[2 * j], sl = L.trig[2 * j + 1];
+    const int32_t ch = j == 0 ? L.trig[2 * (n_theta / 2)] : -cl;
+    const int32_t sh = j == 0 ? L.trig[2 * (n_theta / 2) + 1] : sl;
+    const int32_t ml = window_min(cl, sl, W, H), mh = window_min(ch, sh, W, H);
+    // v = x c + y s + kq; v >> 16 = floor((x c + y s + 32768) / 65536) - m, the row
+    const uint32_t kql = 32768u - (uint32_t)ml * 65536u, kqh = 32768u - (uint32_t)mh * 65536u;
+    // e = y * 65536 + x, so e c + y (s - 65536 c) = x c + y s (mod 2^32)
+    const uint32_t sl2 = (uint32_t)sl - ((uint32_t)cl << 16), sh2 = (uint32_t)sh - ((uint32_t)ch << 16);
+    const uint32_t lim = ((uint32_t)(H - 1) << 16) | (uint32_t)(W - 1);   // clamp of (y, x)
+    if (warp == 0 && half == 0) {
+        tj[slot] = j;
+        wlo[slot] = ml + D;   // rho index of row 0
+        whi[slot] = mh + D;
+    }
+
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem_raw + (size_t)kColStages * chunk * 4);
+    const int words = rows * kCols;
+    const uint32_t acc_slot = smem_u32(acc) + (uint32_t)slot * 4u;
+
+    // ---- zero the accumulator
+    {
+        uint4 *a4 = reinterpret_cast<uint4 *>(acc);
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < words / 4; i += kColThreads) a4[i] = z;   // words is a multiple of 16
+    }
+    __syncthreads();
+
+    // ---- this unit's chunks: split `split` of the frame's chunks
+    int64_t E = (int64_t)*F.count;
+    if (E > F.cap) E = F.cap;
+    if (E < 0) E = 0;
+    const int chunks_all = (int)((E + chunk - 1) / chunk);
+    const int c0 = (int)((int64_t)chunks_all * split / ns), c1 = (int)((int64_t)chunks_all * (split + 1) / ns);
+    const int n_chunks = c1 - c0;
+
+    auto issue = [&](int c) {   // local chunk c (frame chunk c0 + c)
+        const int st = (int)((seq + (uint32_t)c) % kColStages);
+        const int64_t start = (int64_t)(c0 + c) * chunk;
+        const int n_c = (int)((E - start) < chunk ? (E - start) : chunk);
+        const int n4 = n_c & ~3;
+        if (n4 > 0) {
+            mbar_arrive_expect_tx(&R.bars[st], (uint32_t)n4 * 4u);
+            bulk_g2s(ring + st * chunk, F.edges + start, (uint32_t)n4 * 4u, &R.bars[st]);
+        } else {
+            mbar_arrive(&R.bars[st]);
+        }
+    };
+    if (tid == 0) {
+        fence_proxy_async();   // the ring was last written by generic stores
+        const int k0 = n_chunks < kColStages ? n_chunks : kColStages;
+        for (int c = 0; c < k0; ++c) issue(c);
+        R.issued_hi = k0;
+    }
+
+    auto vote = [&](uint32_t e) {
+        uint32_t ec;
+        asm("min.u16x2 %0, %1, %2;" : "=r"(ec) : "r"(e), "r"(lim));
+        const uint32_t y = ec >> 16;
+        const uint32_t v1 = ec * (uint32_t)cl + y * sl2 + kql;   // = x c + y s + kq
+        const uint32_t v2 = ec * (uint32_t)ch + y * sh2 + kqh;
+        red_add_shared_at(acc_slot + (v1 >> 16) * (kCols * 4), 1u);         // theta_lo
+        red_add_shared_at(acc_slot + (v2 >> 16) * (kCols * 4), 0x10000u);   // theta_hi
+    };
+
+    // Warps stream the chunks without block barriers: lane 0 of each warp waits
+    // for a chunk's bytes, and the last warp to finish with a ring stage (its
+    // release count reaching a multiple of kColWarps; the counts only grow)
+    // issues the copy of the chunk kColStages ahead into it.  Copies are issued
+    // in chunk order, so the chunks issued so far are [0, R.issued_hi).
+    int c = 0;
+    for (; c < n_chunks; ++c) {
+        const uint32_t g = seq + (uint32_t)c;
+        const int st = (int)(g % kColStages);
+        uint32_t ok = 1u;
+        if (lane == 0) ok = mbar_wait_or_abort(&R.bars[st], (g / kColStages) & 1u, &abort_flag) ? 1u : 0u;
+        ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        __syncwarp();   // lane 0's wait orders the chunk's bytes for the whole warp
+        if (!ok) {
+            if (lane == 0) atomicExch(&abort_flag, 1);
+            break;
+        }
+        const int64_t start = (int64_t)(c0 + c) * chunk;
+        const int n_c = (int)((E - start) < chunk ? (E - start) : chunk);
+        const int n4 = n_c & ~3;
+        const int G = n4 >> 2, Gh = (G + 1) >> 1;
+        const int g_lo = half ? Gh : 0, g_hi = half ? G : Gh;
+        const uint4 *buf4 = reinterpret_cast<const uint4 *>(ring + st * chunk);
+        for (int k = warp; k < Gh; k += kColWarps) {
+            const int gi = g_lo + k;
+            if (gi < g_hi) {
+                const uint4 q = buf4[gi];   // the half-warp's 4 edges (broadcast)
+                vote(q.x);
+                vote(q.y);
+                vote(q.z);
+                vote(q.w);
+            }
+        }
+        if (warp == kColWarps - 1 && half == 0)   // the chunk's last n_c % 4 edges
+            for (int i = n4; i < n_c; ++i) vote(F.edges[start + i]);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();   // this warp's reads of the stage come first
+            const uint32_t last = (g / kColStages + 1u) * kColWarps - 1u;
+            if (atomicAdd(&R.rel[st], 1u) == last && c + kColStages < n_chunks) {
+                __threadfence_block();
+                fence_proxy_async();
+                issue(c + kColStages);
+                atomicMax(&R.issued_hi, c + kColStages + 1);
+            }
+        }
+    }
+    __syncthreads();
+
+    if (abort_flag) {
+        // drain this CTA's copies that may still be in flight (bounded), flag the frame
+        if (tid == 0) {
+            const int hi = R.issued_hi;
+            for (int k = hi - kColStages < 0 ? 0 : hi - kColStages; k < hi; ++k) {
+                const uint32_t g = seq + (uint32_t)k;
+                (void)mbar_wait_bounded(&R.bars[g % kColStages], (g / kColStages) & 1u);
+            }
+            if (F.flags) atomicOr(F.flags, kFlagTimeout);
+        }
+        return kColAbort;
+    }
+    seq += (uint32_t)n_chunks;
+    if (np < kCols) {   // clear the spare columns (votes of the unused slots' lanes)
+        for (int i = tid; i < words; i += kColThreads)
+            if (i % kCols >= np) acc[i] = 0u;
+        __syncthreads();
+    }
+
+    if (ns > 1) {
+        // a piece of a split tile: publish the partial accumulator; the last
+        // piece adds the others' (each cell's total fits its 16 bits, so the
+        // halves add without carries) and selects
+        const size_t tile_ix = (size_t)F.split_base + tile;
+        uint4 *mine = reinterpret_cast<uint4 *>(L.part + (tile_ix * ns + split) * L.part_stride);
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(acc);
+        for (int i = tid; i < words / 4; i += kColThreads) mine[i] = a4[i];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last_s = (atomicAdd(L.tile_cnt + tile_ix, 1) == ns - 1) ? 1 : 0;
+        __syncthreads();
+        if (!last_s) return kColPiece;   // block-uniform
+        __threadfence();
+        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+        for (int o = 0; o < ns; ++o) {
+            if (o == split) continue;
+            const uint4 *other = reinterpret_cast<const uint4 *>(L.part + (tile_ix * ns + o) * L.part_stride);
+            for (int i = tid; i < words / 4; i += kColThreads) {
+                const uint4 b = __ldcg(other + i);
+                uint4 a = acc4[i];
+                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                acc4[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+
+    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, j0 == 0, tj,
+                InterleavedLayout{wlo, whi, rows}, S, ring);
+    return kColTile;
+}
+
+__global__ void __launch_bounds__(kColThreads, 1) hough_cols_kernel(const __grid_constant__ HoughLaunch L) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ ColRing R;
+    __shared__ SelectSmem S;
+    __shared__ MergeSmem MS;
+    __shared__ int abort_flag, unit_s, last_s, piece_s;
+    __shared__ int tile_j[kCols], win_lo[kCols], win_hi[kCols];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < kColStages; ++s) {
+            mbar_init(&R.bars[s], 1);
+            R.rel[s] = 0u;
+        }
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    uint32_t seq = 0;
+    for (;;) {
+        if (tid == 0) unit_s = atomicAdd(L.queue, 1);
+        __syncthreads();
+        const int u = unit_s;
+        if (u >= L.total_units) break;   // block-uniform
+        int lo = 0, hi = L.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.f[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const HoughFrame &F = L.f[lo];
+        const int local = u - F.unit_begin;
+        const int r = cols_unit(L, F, local / F.n_splits, local % F.n_splits, seq, smem_raw, R, S, abort_flag,
+                                piece_s, tile_j, win_lo, win_hi);
+        if (r == kColAbort) break;
+        if (r == kColTile) {
+            __syncthreads();   // this tile's candidates are written
+            if (tid == 0) {
+                __threadfence();
+                last_s = (atomicAdd(F.done, 1) == F.n_tiles - 1) ? 1 : 0;
+            }
+            __syncthreads();
+            if (last_s) {   // block-uniform
+                __threadfence();
+                const int32_t fl = F.flags ? __ldcg(F.flags) : 0;
+                block_merge(F.cand, (int64_t)F.n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
+                            F.n_peaks, F.status, fl, MS);
+            }
+        }
+        __syncthreads();   // before unit_s and the tile's shared arrays are overwritten
+    }
+}
+
 template <int PMAX>
 cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t s) {
     static uint64_t attr_set = 0;   // devices 0..63 whose attribute is set
@@ -524,6 +882,36 @@ cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_
 #undef LD_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+int hough_cols_max_rows() {
+    const int avail = kSmemLimit - kStaticSmemReserve - kColRingMin;
+    return avail / (kCols * 4);
+}
+
+int hough_cols_chunk(int rows_max) {
+    const int avail = kSmemLimit - kStaticSmemReserve - rows_max * kCols * 4;
+    return avail >= kColStages * kColChunkMax * 4 ? kColChunkMax : kColChunkMin;
+}
+
+cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int rows_max, cudaStream_t s) {
+    if (n_ctas <= 0) return cudaSuccess;
+    if (rows_max < 1 || rows_max > hough_cols_max_rows() || (L.col_chunk != kColChunkMin && L.col_chunk != kColChunkMax))
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kColStages * L.col_chunk * 4 + (size_t)rows_max * kCols * 4;
+    if (smem > (size_t)(kSmemLimit - kStaticSmemReserve)) return cudaErrorInvalidValue;
+    static uint64_t attr_set = 0;   // devices 0..63 whose attribute is set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(attr_set >> dev & 1u)) {
+        e = cudaFuncSetAttribute(hough_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit - kStaticSmemReserve);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_set |= uint64_t(1) << dev;
+    }
+    hough_cols_kernel<<<n_ctas, kColThreads, smem, s>>>(L);
+    return cudaGetLastError();
 }
 
 int hough_template_pairs(int pairs) {

@@ -92,6 +92,9 @@ struct HoughFrame {
     int32_t n_splits;      // units sharing one theta tile (edge ranges)
     int32_t pairs_per_tile;
     int32_t n_tiles;
+    int32_t rows;          // interleaved-column kernel: rows of the tile accumulator
+    int32_t split_base;    // interleaved-column kernel, n_splits > 1: the frame's first tile
+                           // in the launch's split-tile arrays (tile_cnt, part)
 };
 
 struct HoughLaunch {
@@ -102,7 +105,11 @@ struct HoughLaunch {
     int32_t min_votes;
     int32_t total_units;   // work units over all frames
     int32_t top_k, nms_theta, nms_rho;   // candidate mode: the merge
+    int32_t col_chunk;     // interleaved-column kernel: edges per streamed chunk
+    int32_t part_stride;   // interleaved-column kernel: words per partial accumulator
     int32_t pad_;
+    uint32_t *part;        // interleaved-column kernel: partial accumulators of split tiles
+    int32_t *tile_cnt;     // interleaved-column kernel: finished pieces per split tile (zeroed)
     int32_t *queue;        // work-queue head (zeroed before the launch)
     const int32_t *unit_begin_dev;   // nullable: device [n + 1] unit offsets (restricted vote)
     const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
@@ -168,6 +175,19 @@ cudaError_t launch_merge(const MergeLaunch &L, cudaStream_t s);
 
 // Largest pairs-per-tile whose packed accumulator fits shared memory.
 int hough_max_pairs(int n_rho);
+
+// Interleaved-column voting kernel (candidate mode, min_votes >= 1, full
+// pair ranges): tiles of up to kHoughColPairs theta pairs, one per lane of a
+// half-warp; the accumulator holds `rows` rows of kHoughColPairs words.  A
+// frame's tiles may be split into n_splits edge ranges whose partial
+// accumulators meet in L.part.
+constexpr int kHoughColPairs = 16;
+// Largest `rows` that fits shared memory (with the smallest edge ring).
+int hough_cols_max_rows();
+// Edges per streamed chunk for an accumulator of rows_max rows (the largest
+// ring that fits).
+int hough_cols_chunk(int rows_max);
+cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int rows_max, cudaStream_t s);
 
 // Compiled tile sizes (theta pairs per CTA) of the voting kernel; a tile of
 // exactly one of these sizes runs without per-pair predicates.

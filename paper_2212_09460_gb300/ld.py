@@ -443,7 +443,8 @@ class Context:
         ld_autotune(self.handle, self._descs(frames, widths), p, iters, _stream_handle(stream))
 
     def plan(self, w: int, h: int, p: ld_params) -> tuple[int, int]:
-        """(theta pairs per voting tile, Sobel rows per warp) used for w x h frames."""
+        """(theta pairs per voting tile, Sobel rows per warp) used for w x h
+        frames; pairs < 0: the interleaved-column voting kernel, -pairs per tile."""
         return ld_ctx_plan(self.handle, w, h, p)
 
     def prepare(self, frames, widths=None) -> "PreparedBatch":

@@ -102,7 +102,7 @@ def test_autotune_keeps_results_and_sets_plans(ldlib, ora):
         c.autotune(dev, p, iters=2)
         after = [c.plan(w, h, p) for w, h in sizes]
         for pairs, rows in after:
-            assert 1 <= pairs <= 30 and rows in (1, 2, 4)
+            assert 1 <= abs(pairs) <= 30 and rows in (1, 2, 4)
         pk, n, st = c.detect_batch(dev, p)
         torch.cuda.synchronize()
         pk, n, st = pk.cpu().numpy(), n.cpu().numpy(), st.cpu().numpy()
@@ -113,3 +113,60 @@ def test_autotune_keeps_results_and_sets_plans(ldlib, ora):
         assert len(before) == len(after)
     finally:
         c.close()
+
+
+# Both voting kernels against the oracle.  The interleaved-column kernel votes
+# when min_votes >= 1 and the frame fits (plan pairs < 0); min_votes <= 0
+# takes the packed-pair kernel.  Cases: one full 16-pair tile (32 theta), a
+# cut of M > 1024 candidates per tile (the radix select instead of the
+# survivor sort), a checkerboard frame whose accumulator is full of equal
+# counts (the ordered emission of ties), 1440p (the largest common size that
+# fits the interleaved accumulator), and min_votes 0 and 2.
+KERNEL_CASES = [
+    dict(n_theta=32, top_k=16, min_votes=3),
+    dict(n_theta=180, top_k=16, nms_theta=63, nms_rho=3),
+    dict(n_theta=360, top_k=8, nms_theta=1, nms_rho=1, min_votes=0),
+    dict(n_theta=360, top_k=16, nms_theta=1, nms_rho=1, min_votes=2),
+]
+
+
+def _checker(w, h, cell):
+    yy, xx = np.mgrid[0:h, 0:w]
+    return ((((xx // cell) + (yy // cell)) & 1) * 255).astype(np.uint8)
+
+
+@pytest.mark.parametrize("kw", KERNEL_CASES)
+def test_detect_voting_kernels(ctx, ldlib, ora, kw):
+    sizes = [(640, 480), (2560, 1440), (37, 23)]
+    raw = [synth.road_frame(5000 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    raw.append(_checker(1280, 720, 7))
+    sizes.append((1280, 720))
+    p = ldlib.params(**kw)
+    for w, h in sizes:
+        pairs, _ = ctx.plan(w, h, p)
+        assert (pairs < 0) == (kw.get("min_votes", 1) >= 1), (w, h, pairs)
+    frames = [synth.pitched(r, seed=i) for i, r in enumerate(raw)]
+    pk, n, st = _detect(ctx, ldlib, frames, [w for w, h in sizes], **kw)
+    _check(ora, raw, pk, n, st, **kw)
+
+
+def test_benchmark_config_uses_interleaved_kernel(ctx, ldlib):
+    p = ldlib.params(n_theta=360, top_k=4)
+    pairs, rows = ctx.plan(1920, 1080, p)
+    assert pairs == -15 and rows in (1, 2, 4)
+    pairs4k, _ = ctx.plan(3840, 2160, p)
+    assert pairs4k > 0   # 4K does not fit the interleaved accumulator
+
+
+# Split tiles: when a launch's last wave would be at most half full, the tiles
+# of its last frames are voted in edge-range pieces that meet in a partial
+# accumulator.  13 x 1080p at 360 theta: 156 tiles on 152 SMs, the last frame
+# split 8 ways; 60 x 640x480 at 90 theta: 180 tiles, the last 10 frames split
+# 5 ways (pieces of a frame with only a few edge chunks get none).  Every frame
+# against the oracle.
+@pytest.mark.parametrize("n,w,h,n_theta", [(13, 1920, 1080, 360), (60, 640, 480, 90)])
+def test_detect_split_tiles(ctx, ldlib, ora, n, w, h, n_theta):
+    raw = [synth.road_frame(6000 + i, w, h, synth.THROUGHPUT_1080P) for i in range(n)]
+    kw = dict(n_theta=n_theta, top_k=4)
+    pk, cnt, st = _detect(ctx, ldlib, raw, [w] * n, **kw)
+    _check(ora, raw, pk, cnt, st, **kw)
