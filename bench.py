@@ -43,9 +43,9 @@ METRIC = "1080p frames/s end-to-end, % of HBM roofline; proposal vs plain at equ
 # valid only while the kernel's sources hash to the recorded value (else null).
 MEASURED_TRAFFIC = {
     "hough": {"sources": ["ld_hough.cu", "ld_select.cuh", "ld_internal.cuh"],
-              "sha1": "03c2b0796c373bb9c2be85c4e94a7e846c7534ec", "bytes_per_frame": (41170944 + 905984) / 64},
+              "sha1": "15c957c3f96685bbdd35af420fb5c9c14c4c7640", "bytes_per_frame": (41158144 + 1550080) / 64},
     "sobel": {"sources": ["ld_sobel.cu", "ld_internal.cuh"],
-              "sha1": "144711ba03fd953e316a5a2b73c62105df459942", "bytes_per_frame": (132765696 + 22340352) / 64},
+              "sha1": "4660fda7051478ceaf4078d540cecd610d64ebf2", "bytes_per_frame": (132778240 + 22275584) / 64},
 }
 
 
@@ -490,7 +490,8 @@ def main():
         sobel_s = stage_ms[0] / 1000.0
         sobel_bytes = nf * W * H * 1 + e_sum * 4
         atom_peak = n_sms * 32 * sm_max_mhz * 1e6 / 1e9          # Gvote/s: 32 banks/clk/SM
-        roof = {"bound": "alu", "kernel": "hough_kernel (Step 3 voting + per-tile top-M)",
+        roof = {"bound": "alu", "kernel": "hough_cols_kernel (Step 3 interleaved-column voting + per-tile top-M "
+                                          "+ the frame's peak merge)",
                 "achieved": votes / hough_s / 1e9, "peak": atom_peak, "unit": "Gvote/s",
                 "frac": votes / hough_s / 1e9 / atom_peak, "traffic": measured_traffic("hough", nf),
                 "peak_basis": f"{n_sms} SMs x 32 shared-memory banks/clk x {sm_max_mhz:.0f} MHz "
