@@ -187,6 +187,8 @@ class ServeStats:
     max_waiting: int = 0
     max_slots_in_use: int = 0
     wall_s: float = 0.0
+    batch_device_ms: list = field(default_factory=list)   # (device ms, batch class, frames) per batch
+    max_loop_gap_ms: float = 0.0   # longest time between two scheduler iterations
 
 
 class Scheduler:
@@ -196,7 +198,8 @@ class Scheduler:
     putting admitted frames in their slots); submit(worker, frames, seq)
     (launch one batch); poll(worker) -> None while the worker's batch runs,
     else (frames, peaks[n][k][3], n_peaks[n], status[n], fallback[n]) with
-    fallback -1 on plain launches; busy(worker)."""
+    fallback -1 on plain launches; busy(worker); optionally device_ms(worker)
+    -> (device ms, batch class) of the batch poll just returned."""
 
     def __init__(self, admission: Admission, executor, max_batch: int = 64, clock=None):
         self.adm, self.ex, self.max_batch = admission, executor, max_batch
@@ -220,8 +223,12 @@ class Scheduler:
         admitted = {}                                  # batch class -> deque of loaded frames
         total, ai, done, seq = len(arrivals), 0, 0, 0
         t_start = clock.now()
+        t_prev = t_start
+        dev_ms = getattr(ex, "device_ms", None)
         while done < total:
             now = clock.now()
+            st.max_loop_gap_ms = max(st.max_loop_gap_ms, (now - t_prev) * 1e3)
+            t_prev = now
             progressed = False
             while ai < total and arrivals[ai].t_arrival <= now:
                 f = arrivals[ai]
@@ -251,6 +258,9 @@ class Scheduler:
                     inflight += 1
                     continue
                 frames, pk, npk, status, fb = res
+                if dev_ms is not None:
+                    ms, cls = dev_ms(wi)
+                    st.batch_device_ms.append((ms, cls, len(frames)))
                 t_done = clock.now()
                 for k, f in enumerate(frames):
                     f.t_done = t_done
@@ -307,7 +317,20 @@ def summarize(st: ServeStats) -> dict:
             "max_batch_seen": int(max(st.batch_sizes)), "max_inflight_batches": st.max_inflight,
             "max_waiting_for_slot": st.max_waiting, "max_slots_in_use": st.max_slots_in_use,
             "proposal_fallback_rate": float(np.mean(fb)) if fb else None,
-            "status_nonzero": int(sum(1 for f in fr if f.status != 0))}
+            "status_nonzero": int(sum(1 for f in fr if f.status != 0)),
+            "max_loop_gap_ms": st.max_loop_gap_ms,
+            **_device_summary(st.batch_device_ms)}
+
+
+def _device_summary(bd: list) -> dict:
+    """Device time per batch (launch to results on the host side of the
+    stream): p50, p99 and the slowest batch."""
+    if not bd:
+        return {}
+    ms = np.array([b[0] for b in bd])
+    worst = max(bd, key=lambda b: b[0])
+    return {"batch_device_ms_p50": float(np.percentile(ms, 50)), "batch_device_ms_p99": float(np.percentile(ms, 99)),
+            "batch_device_ms_max": float(worst[0]), "slowest_batch": {"class": str(worst[1]), "frames": worst[2]}}
 
 
 class GpuExecutor:
@@ -409,7 +432,10 @@ class GpuExecutor:
                 s.wait_event(f.ready)
                 waited.add(id(f.ready))
         out = tuple(t[:n] for t in w["dev"])
-        proposal = self.batch_class(frames[0]) == "proposal"
+        cls = self.batch_class(frames[0])
+        proposal = cls == "proposal"
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev0.record(s)
         bufs, widths = [f.buf for f in frames], [f.w for f in frames]
         if proposal:
             w["ctx"].detect_batch_proposal(bufs, self.p, self.net, self.q, widths=widths, out=out, stream=s)
@@ -418,9 +444,10 @@ class GpuExecutor:
         with torch.cuda.stream(s):
             for h_t, d_t in zip(w["host"], out[:4]):
                 h_t[:n].copy_(d_t, non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
         w["frames"], w["event"], w["proposal"] = frames, ev, proposal
+        w["ev0"], w["class"] = ev0, cls + " " + "+".join(sorted({f"{f.w}x{f.h}" for f in frames}))
 
     def poll(self, wi: int):
         w = self.w[wi]
@@ -431,6 +458,11 @@ class GpuExecutor:
         pk, npk, st, fb = (t[:n].numpy() for t in w["host"])
         fb = fb.copy() if w["proposal"] else np.full(n, -1, np.int32)
         return frames, pk.copy(), npk.copy(), st.copy(), fb
+
+    def device_ms(self, wi: int):
+        """(device ms, batch class) of the worker's last completed batch."""
+        w = self.w[wi]
+        return w["ev0"].elapsed_time(w["event"]), w["class"]
 
 
 class Server:
