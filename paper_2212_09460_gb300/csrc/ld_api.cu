@@ -1056,15 +1056,21 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
             return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
     }
     const int M = cand_m(p);
-    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta, false);   // restricted vote: packed-pair kernel
+    const HoughPlan hp = plan_for(ctx, w, h, p.n_theta, false);   // packed-pair plan
+    // the interleaved-column kernel votes the kept pairs when the frame fits it
+    // and min_votes >= 1 (its windows leave unvoted cells out); device plan
+    const HoughPlan hc = plan_cols(ctx, w, h, p.n_theta);
+    const bool cols = p.min_votes >= 1 && hc.cols;
     const int n_pairs = p.n_theta / 2;
     const int64_t epf = ((int64_t)w * h + 3) / 4 * 4;
     if (!ctx->edges.ensure((size_t)(n * epf) * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
     if (!ctx->small.ensure(kSmallInts * 4)) return fail(LD_ERR_NOMEM, "scratch counts");
     // restricted-vote tiles per frame: up to twice the full vote's, so that
     // units can shrink to fill the persistent launch's last wave
-    const int tile_cap = std::min(n_pairs, 2 * hp.n_tiles);
+    const int tile_cap = cols ? hc.n_tiles : std::min(n_pairs, 2 * hp.n_tiles);
     if (!ctx->cand.ensure((size_t)n * tile_cap * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+    if (cols && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hc.rows)))
+        return fail(LD_ERR_NOMEM, "scratch partial accumulators");
     // proposal scratch, carved in 256-byte aligned pieces
     size_t off = 0;
     auto carve = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
@@ -1079,6 +1085,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     const size_t o_fb = carve((size_t)n * 4);
     const size_t o_tiles = carve((size_t)n * 4);
     const size_t o_ub = carve((size_t)(n + 1) * 4);
+    const size_t o_cplan = carve((size_t)n * 3 * 4);
     if (!ctx->prop.ensure(off)) return fail(LD_ERR_NOMEM, "scratch proposal");
     uint8_t *pb = (uint8_t *)ctx->prop.p;
     uint8_t *pool = pb + o_pool;
@@ -1087,6 +1094,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     int32_t *plist = (int32_t *)(pb + o_list), *pcnt = (int32_t *)(pb + o_cnt);
     int32_t *fb = d_fallback ? d_fallback : (int32_t *)(pb + o_fb);
     int32_t *tiles = (int32_t *)(pb + o_tiles), *ub = (int32_t *)(pb + o_ub);
+    int32_t *cplan = (int32_t *)(pb + o_cplan);
     uint32_t *edges = (uint32_t *)ctx->edges.p;
     const Small sm = small_of(ctx->small.p);
     uint64_t *cand = (uint64_t *)ctx->cand.p;
@@ -1123,8 +1131,14 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     st = net_infer(pool, n, hs, ws, net, y[2], y[3], y[4], feat, logits, s);
     if (st != LD_OK) return st;
     // bands -> active pairs -> work units
-    e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, tile_cap,
-                            ctx->num_sms, plist, pcnt, fb, tiles, ub, s);
+    const size_t cnt_bytes = ((size_t)ctx->num_sms * 4 + 255) / 256 * 256;
+    int32_t *tile_cnt = cols ? (int32_t *)ctx->part.p : nullptr;
+    if (cols)
+        e = launch_select_bands_cols(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, ctx->num_sms, plist, pcnt,
+                                     fb, cplan, ub, tile_cnt, s);
+    else
+        e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, tile_cap,
+                                ctx->num_sms, plist, pcnt, fb, tiles, ub, s);
     if (e != cudaSuccess) return cuda_fail(e, "band selection");
     // Steps 3-4 on the kept pairs
     HoughLaunch HL;
@@ -1140,6 +1154,13 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     HL.trig = dt;
     HL.queue = sm.queue;
     HL.unit_begin_dev = ub;
+    if (cols) {
+        HL.col_plan = cplan;
+        HL.col_chunk = hough_cols_chunk(hc.rows);
+        HL.part_stride = hc.rows * kHoughColPairs;
+        HL.tile_cnt = tile_cnt;
+        HL.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
+    }
     for (int i = 0; i < n; ++i) {
         HoughFrame &HF = HL.f[i];
         HF.edges = edges + i * epf;
@@ -1159,11 +1180,13 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         HF.n_rho = hp.n_rho;
         HF.n_splits = 1;
         HF.pairs_per_tile = hp.pairs;
-        HF.n_tiles = tile_cap;   // unused: the device prefix ub gives each frame's tiles
+        HF.n_tiles = tile_cap;   // unused: the device plan gives each frame's tiles
+        HF.rows = hc.rows;
     }
-    const int max_units = n * tile_cap;
-    e = launch_hough(HL, max_units < ctx->num_sms ? max_units : ctx->num_sms, hp.pairs,
-                     (int64_t)hp.pairs * hp.n_rho, s);
+    const int max_units = n * tile_cap * (cols ? kMaxSplits : 1);
+    const int ctas = max_units < ctx->num_sms ? max_units : ctx->num_sms;
+    e = cols ? launch_hough_cols(HL, ctas, hc.rows, s)
+             : launch_hough(HL, ctas, hp.pairs, (int64_t)hp.pairs * hp.n_rho, s);
     if (e != cudaSuccess) return cuda_fail(e, "hough launch");
     if (d_active_pairs) {
         e = cudaMemcpyAsync(d_active_pairs, pcnt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);

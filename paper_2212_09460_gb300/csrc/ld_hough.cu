@@ -611,26 +611,30 @@ struct ColRing {
 
 enum ColResult { kColAbort = -1, kColPiece = 0, kColTile = 1 };
 
-// One work unit of frame F: tile `tile`, edge range `split` of n_splits
-// (chunk-aligned).  A split tile's pieces store their partial accumulators in
-// L.part; the last piece to finish adds the others' and selects.  Returns
-// kColTile if this unit finished its tile (candidates written), kColPiece if
-// another piece will, kColAbort if a bounded wait gave up (the frame is
-// flagged; the CTA must stop).
+// One work unit of frame F: tile `tile` of n_tiles, edge range `split` of
+// ns (chunk-aligned).  The frame's pairs are all n_theta/2, or its ascending
+// active-pair list (restricted vote), split evenly over its tiles (at most
+// kCols pairs each).  A split tile's pieces store their partial accumulators
+// in L.part (tile index split_base + tile); the last piece to finish adds
+// the others' and selects.  Returns kColTile if this unit finished its tile
+// (candidates written), kColPiece if another piece will, kColAbort if a
+// bounded wait gave up (the frame is flagged; the CTA must stop).
 __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame &F, int tile, int split,
-                                         uint32_t &seq, uint8_t *smem_raw, ColRing &R, SelectSmem &S,
-                                         int &abort_flag, int &last_s, int *tj, int *wlo, int *whi) {
-    const int n_theta = L.n_theta, n_tiles = F.n_tiles, ns = F.n_splits, chunk = L.col_chunk;
+                                         int n_tiles, int ns, int split_base, uint32_t &seq, uint8_t *smem_raw,
+                                         ColRing &R, SelectSmem &S, int &abort_flag, int &last_s, int *tj,
+                                         int *wlo, int *whi) {
+    const int n_theta = L.n_theta, chunk = L.col_chunk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_pairs = n_theta / 2;
-    const int base = n_pairs / n_tiles, extra = n_pairs % n_tiles;
-    const int np = base + (tile < extra ? 1 : 0);   // <= kCols (host plan)
+    const int n_avail = F.pair_list ? *F.pair_count : n_theta / 2;
+    const int base = n_avail / n_tiles, extra = n_avail % n_tiles;
+    const int np = base + (tile < extra ? 1 : 0);   // <= kCols (plan)
     const int j0 = tile * base + min(tile, extra);
+    const bool has0 = (F.pair_list ? F.pair_list[j0] : j0) == 0;
     const int W = F.w, H = F.h, D = F.D, rows = F.rows;
 
     // per-lane constants: (c, s) and Q16 offset of both thetas of the lane's pair
     const int slot = lane % kCols, half = lane / kCols;
-    const int j = slot < np ? j0 + slot : 0;   // unused slots: a spare column
+    const int j = slot < np ? (F.pair_list ? F.pair_list[j0 + slot] : j0 + slot) : 0;   // unused: a spare column
     const int32_t cl = L.trig[2 * j], sl = L.trig[2 * j + 1];
     const int32_t ch = j == 0 ? L.trig[2 * (n_theta / 2)] : -cl;
     const int32_t sh = j == 0 ? L.trig[2 * (n_theta / 2) + 1] : sl;
@@ -768,7 +772,7 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         // a piece of a split tile: publish the partial accumulator; the last
         // piece adds the others' (each cell's total fits its 16 bits, so the
         // halves add without carries) and selects
-        const size_t tile_ix = (size_t)F.split_base + tile;
+        const size_t tile_ix = (size_t)split_base + tile;
         uint4 *mine = reinterpret_cast<uint4 *>(L.part + (tile_ix * ns + split) * L.part_stride);
         const uint4 *a4 = reinterpret_cast<const uint4 *>(acc);
         for (int i = tid; i < words / 4; i += kColThreads) mine[i] = a4[i];
@@ -792,8 +796,8 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         __syncthreads();
     }
 
-    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, j0 == 0, tj,
-                InterleavedLayout{wlo, whi, rows}, S, ring);
+    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, has0, tj, InterleavedLayout{wlo, whi, rows},
+                S, ring);
     return kColTile;
 }
 
@@ -815,32 +819,37 @@ __global__ void __launch_bounds__(kColThreads, 1) hough_cols_kernel(const __grid
     }
     __syncthreads();
     uint32_t seq = 0;
+    const int32_t *ub = L.unit_begin_dev;   // restricted vote: device plan
+    const int total_units = ub ? ub[L.n] : L.total_units;
     for (;;) {
         if (tid == 0) unit_s = atomicAdd(L.queue, 1);
         __syncthreads();
         const int u = unit_s;
-        if (u >= L.total_units) break;   // block-uniform
+        if (u >= total_units) break;   // block-uniform
         int lo = 0, hi = L.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (L.f[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+            if ((ub ? ub[mid] : L.f[mid].unit_begin) <= u) lo = mid; else hi = mid - 1;
         }
         const HoughFrame &F = L.f[lo];
-        const int local = u - F.unit_begin;
-        const int r = cols_unit(L, F, local / F.n_splits, local % F.n_splits, seq, smem_raw, R, S, abort_flag,
+        const int local = u - (ub ? ub[lo] : F.unit_begin);
+        const int n_tiles = ub ? L.col_plan[3 * lo] : F.n_tiles;
+        const int ns = ub ? L.col_plan[3 * lo + 1] : F.n_splits;
+        const int sb = ub ? L.col_plan[3 * lo + 2] : F.split_base;
+        const int r = cols_unit(L, F, local / ns, local % ns, n_tiles, ns, sb, seq, smem_raw, R, S, abort_flag,
                                 piece_s, tile_j, win_lo, win_hi);
         if (r == kColAbort) break;
         if (r == kColTile) {
             __syncthreads();   // this tile's candidates are written
             if (tid == 0) {
                 __threadfence();
-                last_s = (atomicAdd(F.done, 1) == F.n_tiles - 1) ? 1 : 0;
+                last_s = (atomicAdd(F.done, 1) == n_tiles - 1) ? 1 : 0;
             }
             __syncthreads();
             if (last_s) {   // block-uniform
                 __threadfence();
                 const int32_t fl = F.flags ? __ldcg(F.flags) : 0;
-                block_merge(F.cand, (int64_t)F.n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
+                block_merge(F.cand, (int64_t)n_tiles * L.cand_m, L.top_k, L.nms_theta, L.nms_rho, F.peaks,
                             F.n_peaks, F.status, fl, MS);
             }
         }

@@ -112,6 +112,8 @@ struct HoughLaunch {
     int32_t *tile_cnt;     // interleaved-column kernel: finished pieces per split tile (zeroed)
     int32_t *queue;        // work-queue head (zeroed before the launch)
     const int32_t *unit_begin_dev;   // nullable: device [n + 1] unit offsets (restricted vote)
+    const int32_t *col_plan;         // interleaved kernel with unit_begin_dev: device [n][3]
+                                     // (tiles, n_splits, split_base) per frame
     const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
     HoughFrame f[kMaxLaunchFrames];
 };
@@ -214,6 +216,16 @@ cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const
 cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p_band, float p_fallback, int margin,
                                 int pmax, int tile_cap, int slots, int32_t *pair_list, int32_t *pair_count,
                                 int32_t *fallback, int32_t *tiles, int32_t *unit_begin, cudaStream_t s);
+// The same band selection, planned for the interleaved-column kernel: tiles
+// of at most kHoughColPairs pairs, and when the launch's last wave (of
+// `slots` CTAs) would be at most half full, the tiles of the last frames split
+// into edge-range pieces (at most `slots` pieces).  Writes col_plan [n][3]
+// (tiles, n_splits, split_base), unit_begin [n + 1], and zeroes the split
+// tiles' counters tile_cnt [slots].
+cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, float p_band, float p_fallback,
+                                     int margin, int slots, int32_t *pair_list, int32_t *pair_count,
+                                     int32_t *fallback, int32_t *col_plan, int32_t *unit_begin, int32_t *tile_cnt,
+                                     cudaStream_t s);
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);

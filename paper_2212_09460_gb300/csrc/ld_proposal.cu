@@ -127,6 +127,52 @@ __global__ void __launch_bounds__(kPlanThreads) plan_units_kernel(const int32_t 
     if (tid == 0) unit_begin[0] = 0;
 }
 
+// Work units of the restricted vote on the interleaved-column kernel (one
+// CTA; thread f plans frame f).  Frame f votes c_f pairs in T_f =
+// ceil(c_f / kHoughColPairs) tiles; a unit costs about the frame's edge count
+// whatever its pairs, so tiles are as few as possible.  When the U = sum T_f
+// units leave the persistent launch's last wave at most half full, the tiles
+// of the last frames (together at least that wave's units) are split into
+// ns = min(8, slots / their tiles) edge-range pieces, which fill it.
+__global__ void __launch_bounds__(kPlanThreads) plan_cols_units_kernel(const int32_t *pair_count, int n, int slots,
+                                                                       int32_t *col_plan, int32_t *unit_begin,
+                                                                       int32_t *tile_cnt) {
+    __shared__ int tiles_s[kPlanThreads];
+    const int tid = threadIdx.x;
+    if (tid < n) {
+        const int c = pair_count[tid] > 0 ? pair_count[tid] : 1;
+        tiles_s[tid] = (c + kHoughColPairs - 1) / kHoughColPairs;
+    }
+    for (int i = tid; i < slots; i += blockDim.x) tile_cnt[i] = 0;
+    __syncthreads();
+    if (tid == 0) {
+        int u0 = 0;
+        for (int f = 0; f < n; ++f) u0 += tiles_s[f];
+        int split_from = n, ns = 1;
+        const int tail = u0 % slots;
+        if (u0 > slots && tail > 0 && 2 * tail <= slots) {
+            int q = n, units = 0;
+            while (q > 0 && units < tail) units += tiles_s[--q];
+            const int k = slots / units < 8 ? slots / units : 8;
+            if (k >= 2) {
+                split_from = q;
+                ns = k;
+            }
+        }
+        int ub = 0, sb = 0;
+        for (int f = 0; f < n; ++f) {
+            const int t = tiles_s[f], k = f >= split_from ? ns : 1;
+            col_plan[3 * f] = t;
+            col_plan[3 * f + 1] = k;
+            col_plan[3 * f + 2] = k > 1 ? sb : 0;
+            if (k > 1) sb += t;
+            unit_begin[f] = ub;
+            ub += t * k;
+        }
+        unit_begin[n] = ub;
+    }
+}
+
 // Training targets from a frame's peaks (one CTA per frame).  A peak counts
 // if it is among the first `always_k` or has >= rel_votes times the first
 // peak's votes.  Targets: the theta band of each counted peak, and every
@@ -174,6 +220,19 @@ cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     plan_units_kernel<<<1, kPlanThreads, 0, s>>>(pair_count, n, pmax, tile_cap, slots, tiles, unit_begin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, float p_band, float p_fallback,
+                                     int margin, int slots, int32_t *pair_list, int32_t *pair_count,
+                                     int32_t *fallback, int32_t *col_plan, int32_t *unit_begin, int32_t *tile_cnt,
+                                     cudaStream_t s) {
+    if (n < 1 || n > kPlanThreads || slots < 1) return cudaErrorInvalidValue;
+    select_bands_kernel<<<n, 256, 0, s>>>(logits, n_theta, p_band, p_fallback, margin, pair_list, pair_count,
+                                          fallback);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    plan_cols_units_kernel<<<1, kPlanThreads, 0, s>>>(pair_count, n, slots, col_plan, unit_begin, tile_cnt);
     return cudaGetLastError();
 }
 

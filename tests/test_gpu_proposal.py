@@ -52,10 +52,14 @@ def _voted_rows(bands, margin, n_theta=NT):
     return rows, len(pairs)
 
 
-@pytest.mark.parametrize("bands,margin", [([27, 10], 2), ([0, 18, 35], 0), ([5], 4)])
-def test_restricted_vote_matches_masked_oracle(ctx, ldlib, ora, bands, margin):
+# min_votes 1: the interleaved-column kernel votes the kept pairs; min_votes 0:
+# the packed-pair kernel (the frames have far more than top_k voted cells, so
+# the peaks are the same either way)
+@pytest.mark.parametrize("bands,margin,mv", [([27, 10], 2, 1), ([0, 18, 35], 0, 1), ([5], 4, 1), ([27, 10], 2, 0),
+                                             ([0, 18, 35], 0, 0)])
+def test_restricted_vote_matches_masked_oracle(ctx, ldlib, ora, bands, margin, mv):
     raw, dev = _frames([4000, 4001, 4002])
-    p = ldlib.params(n_theta=NT, top_k=4, border=1)
+    p = ldlib.params(n_theta=NT, top_k=4, border=1, min_votes=mv)
     net = _forced_net(bands)
     q = ldlib.proposal_params(0.5, 0.9, margin)
     pk, npk, st, fb, act = (t.cpu().numpy() for t in ctx.detect_batch_proposal(dev, p, net, q))
@@ -64,7 +68,7 @@ def test_restricted_vote_matches_masked_oracle(ctx, ldlib, ora, bands, margin):
         e = ora.edge_list(ora.binarize(ora.sobel_mag(r, border=1), 128))
         acc = ora.hough(e, W, H, NT)
         acc[~rows] = 0
-        ref = ora.peaks(acc, 4)
+        ref = ora.peaks(acc, 4, min_votes=mv)
         assert st[i] == 0 and fb[i] == 0 and act[i] == n_pairs
         assert npk[i] == len(ref)
         np.testing.assert_array_equal(pk[i, : npk[i]], ref)
