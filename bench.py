@@ -285,8 +285,48 @@ def serving_run(seconds: float, rate_scale: float, workers: int = 3):
     return {"seconds": seconds, "offered_frames_per_s": 8 * 30 * rate_scale, **serving.summarize(st)}
 
 
+def _oracle_detect(frame: np.ndarray) -> int:
+    import oracle
+    return len(oracle.detect(frame, N_THETA, TOP_K))
+
+
+def oracle_stages(reps_by_px=((400_000, 5), (1_000_000, 3), (2_100_000, 3), (10**9, 1))):
+    """Per-stage oracle times (ms, median of up to 5 runs after a warm-up, one
+    thread) on one frame of each workload: the 640x480 latency frame (180
+    theta, top-2) and the four resolutions of the mixed batch (360 theta,
+    top-4; 1920x1080 is the throughput frame)."""
+    import oracle
+    from paper_2212_09460_gb300 import synth
+    cases = [("640x480 latency, 180 theta", 640, 480, 0, synth.LATENCY_640x480, 180, 2)]
+    cases += [(f"{w}x{h}, 360 theta", w, h, 2000 + i, synth.THROUGHPUT_1080P, 360, 4)
+              for i, (w, h) in enumerate(MIXED_SIZES)]
+    out = {}
+    for name, w, h, seed, style, nt, k in cases:
+        img = synth.road_frame(seed, w, h, style)
+        reps = next(r for px, r in reps_by_px if w * h <= px)
+        t = {"sobel": [], "binarize": [], "edge_list": [], "hough": [], "peaks": []}
+        for it in range(reps + 1):
+            t0 = time.perf_counter(); mag = oracle.sobel_mag(img)
+            t1 = time.perf_counter(); b = oracle.binarize(mag, 128)
+            t2 = time.perf_counter(); e = oracle.edge_list(b)
+            t3 = time.perf_counter(); acc = oracle.hough(e, w, h, nt)
+            t4 = time.perf_counter(); oracle.peaks(acc, k)
+            t5 = time.perf_counter()
+            if it == 0:
+                continue   # warm-up
+            for key, a, z in (("sobel", t0, t1), ("binarize", t1, t2), ("edge_list", t2, t3), ("hough", t3, t4),
+                              ("peaks", t4, t5)):
+                t[key].append((z - a) * 1e3)
+        med = {key: statistics.median(v) for key, v in t.items()}
+        out[name] = {**med, "total": sum(med.values()), "frames_per_s": 1e3 / sum(med.values()),
+                     "edges": int(len(e)), "runs": reps}
+    return out
+
+
 def cpu_baseline(frames: np.ndarray, budget_s: float = 12.0):
-    """The oracle as it stands, single-threaded, on as many frames as fit the budget."""
+    """The oracle as it stands: single-threaded on as many 1080p frames as fit
+    the budget (the reported value); the same over all host cores (one
+    process per core, frames shared out); per-stage times per workload."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
@@ -297,9 +337,18 @@ def cpu_baseline(frames: np.ndarray, budget_s: float = 12.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_detect, list(frames[:cores]))   # warm the workers
+        t1 = time.perf_counter()
+        pool.map(_oracle_detect, list(frames), chunksize=1)
+        dt_mc = time.perf_counter() - t1
     return {"value": done / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} of the {len(frames)} 1920x1080 frames, full Steps 1-4 (oracle.detect), "
-                      f"{dt:.1f} s, one thread"}
+                      f"{dt:.1f} s, one thread",
+            "multi_core": {"value": len(frames) / dt_mc, "unit": "frames/s", "cores": cores,
+                           "sample": f"all {len(frames)} 1920x1080 frames, one process per core, {dt_mc:.1f} s"},
+            "stages_ms": oracle_stages()}
 
 
 def run_reference(args):
