@@ -355,28 +355,41 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
     constexpr int P_BYTES = (Patch<S>::PR * QPP * S * Patch<S>::HC * 16 + 1023) / 1024 * 1024;
     constexpr int smem = (kTcN * 9 * CIN * 2 + 1023) / 1024 * 1024 + 2 * P_BYTES;
     auto kern = conv_fwd_tc_kernel<CIN, S, FUSE1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)   // as much shared memory as possible: several CTAs per SM
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    // once per device: the attributes, and the grid limit (SMs x CTAs per SM)
+    static std::atomic<uint64_t> done{0};
+    static std::atomic<int> grid_max[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, sm_smem = 0, reserved = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    int limit = dev < 64 ? grid_max[dev].load(std::memory_order_acquire) : 0;
+    e = once_per_device(done, [&](int d) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (r == cudaSuccess)   // as much shared memory as possible: several CTAs per SM
+            r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        int sms = 0, sm_smem = 0, reserved = 0;
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, d);
+        // CTAs per SM by shared memory (dynamic + static + the per-block
+        // reservation) and by registers, at most 512 / 32 by tensor memory
+        cudaFuncAttributes fa;
+        if (r == cudaSuccess) r = cudaFuncGetAttributes(&fa, kern);
+        if (r != cudaSuccess) return r;
+        int per_sm = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
+        const int per_sm_regs = 65536 / (kTcThreads * ((fa.numRegs + 7) / 8 * 8));
+        if (per_sm_regs < per_sm) per_sm = per_sm_regs;
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm * kTmemCols > 512) per_sm = 512 / kTmemCols;
+        limit = sms * per_sm;
+        if (d < 64) grid_max[d].store(limit, std::memory_order_release);
+        return cudaSuccess;
+    });
     if (e != cudaSuccess) return e;
-    // CTAs per SM by shared memory (dynamic + static + the per-block
-    // reservation) and by registers, at most 512 / 32 by tensor memory
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, kern);
-    if (e != cudaSuccess) return e;
-    int per_sm = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
-    const int per_sm_regs = 65536 / (kTcThreads * ((fa.numRegs + 7) / 8 * 8));
-    if (per_sm_regs < per_sm) per_sm = per_sm_regs;
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm * kTmemCols > 512) per_sm = 512 / kTmemCols;
+    if (limit <= 0 && dev < 64) limit = grid_max[dev].load(std::memory_order_acquire);
+    if (limit <= 0) return cudaErrorInvalidValue;
     const int tiles = G.n * ((G.oh + kTileH - 1) / kTileH) * ((G.ow + kTileW - 1) / kTileW);
-    const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
+    const int grid = tiles < limit ? tiles : limit;
     kern<<<grid, kTcThreads, smem, s>>>(x, G, w, b, y, C1);
     return cudaGetLastError();
 }

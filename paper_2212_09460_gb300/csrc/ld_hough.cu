@@ -859,16 +859,12 @@ __global__ void __launch_bounds__(kColThreads, 1) hough_cols_kernel(const __grid
 
 template <int PMAX>
 cudaError_t launch_p(const HoughLaunch &L, int n_ctas, size_t smem, cudaStream_t s) {
-    static uint64_t attr_set = 0;   // devices 0..63 whose attribute is set
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static std::atomic<uint64_t> attr_done{0};
+    const cudaError_t e = once_per_device(attr_done, [](int) {
+        return cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kSmemLimit - kStaticSmemReserve);
+    });
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(attr_set >> dev & 1u)) {
-        e = cudaFuncSetAttribute(hough_kernel<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemLimit - kStaticSmemReserve);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set |= uint64_t(1) << dev;
-    }
     hough_kernel<PMAX><<<n_ctas, kHoughThreads, smem, s>>>(L);
     return cudaGetLastError();
 }
@@ -909,16 +905,12 @@ cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int rows_max, cu
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)kColStages * L.col_chunk * 4 + (size_t)rows_max * kCols * 4;
     if (smem > (size_t)(kSmemLimit - kStaticSmemReserve)) return cudaErrorInvalidValue;
-    static uint64_t attr_set = 0;   // devices 0..63 whose attribute is set
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static std::atomic<uint64_t> attr_done{0};
+    const cudaError_t e = once_per_device(attr_done, [](int) {
+        return cudaFuncSetAttribute(hough_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kSmemLimit - kStaticSmemReserve);
+    });
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(attr_set >> dev & 1u)) {
-        e = cudaFuncSetAttribute(hough_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemLimit - kStaticSmemReserve);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set |= uint64_t(1) << dev;
-    }
     hough_cols_kernel<<<n_ctas, kColThreads, smem, s>>>(L);
     return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 // is part of the public C ABI, which lives in include/ld.h.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -229,5 +230,21 @@ cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, fl
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);
+
+// One-time per-device setup of a kernel (function attributes): `done` holds
+// one bit per device 0..63, set after `setup(device)` succeeded; later calls
+// on that device skip it (devices >= 64 run it every time).  Launch paths
+// call this instead of setting attributes on every launch, which costs driver
+// calls and can wait on driver locks that other host threads hold.
+template <class F>
+cudaError_t once_per_device(std::atomic<uint64_t> &done, F &&setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1u)) return cudaSuccess;
+    e = setup(dev);
+    if (e == cudaSuccess && dev < 64) done.fetch_or(uint64_t(1) << dev, std::memory_order_acq_rel);
+    return e;
+}
 
 }  // namespace ld

@@ -343,7 +343,10 @@ cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s) {
         if ((L.f[i].bin != nullptr) != bin || (L.f[i].pool != nullptr) != pool) return cudaErrorInvalidValue;
     auto kern = bin ? (pool ? sobel_bin_edges_kernel<true, true> : sobel_bin_edges_kernel<true, false>)
                     : (pool ? sobel_bin_edges_kernel<false, true> : sobel_bin_edges_kernel<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSobelSmem);
+    static std::atomic<uint64_t> attr_done[4];   // per template instance, one bit per device
+    cudaError_t e = once_per_device(attr_done[(bin ? 2 : 0) + (pool ? 1 : 0)], [&](int) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSobelSmem);
+    });
     if (e != cudaSuccess) return e;
     kern<<<n_ctas, kSobelThreads, kSobelSmem, s>>>(L);
     return cudaGetLastError();
