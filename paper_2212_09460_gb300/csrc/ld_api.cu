@@ -231,6 +231,10 @@ Small small_of(void *p) {
 // launch; scratch = the pieces' arrival counters (one per tile, 256-byte
 // padded) then their partial accumulators.
 constexpr int kMaxSplits = 8;
+// A launch with fewer tiles than SMs splits every tile (to fill the GPU)
+// only when its frames have at least this many pixels: below it a tile's edge
+// stream is too short to pay for a piece's partial store and merge.
+constexpr int64_t kSplitFillPixels = 1 << 19;
 size_t split_scratch_bytes(int pieces, int rows) {
     return ((size_t)pieces * 4 + 255) / 256 * 256 + (size_t)pieces * rows * kHoughColPairs * 4;
 }
@@ -789,16 +793,27 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         // Interleaved kernel: when the launch's last wave would be at most half
         // full, split each tile of the last frames in queue order (together
         // at least as many tiles as that wave holds) into ns edge ranges
-        // (pieces, at most num_sms in all), which spread over the wave.
+        // (pieces, at most num_sms in all), which spread over the wave.  A
+        // launch with fewer tiles than SMs (small batches: latency) splits
+        // every tile, if its frames are large enough.
         int split_from = gn, ns_split = 1, split_tiles = 0, rows_max = 1;
         if (cols) {
             int U0 = 0;
+            int64_t px_min = INT64_MAX;
             for (int k = 0; k < gn; ++k) {
                 U0 += plans[k].n_tiles;
                 rows_max = std::max(rows_max, plans[k].rows);
+                px_min = std::min(px_min, (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h);
             }
             const int S = ctx->num_sms, tail = U0 % S;
-            if (U0 > S && tail > 0 && 2 * tail <= S) {
+            if (U0 < S && px_min >= kSplitFillPixels) {
+                const int ns = std::min(kMaxSplits, S / U0);
+                if (ns >= 2) {
+                    split_from = 0;
+                    ns_split = ns;
+                    split_tiles = U0;
+                }
+            } else if (U0 > S && tail > 0 && 2 * tail <= S) {
                 int q = gn, units = 0;
                 while (q > 0 && units < tail) units += plans[order[--q]].n_tiles;
                 const int ns = std::min(kMaxSplits, S / units);
@@ -1134,8 +1149,8 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     const size_t cnt_bytes = ((size_t)ctx->num_sms * 4 + 255) / 256 * 256;
     int32_t *tile_cnt = cols ? (int32_t *)ctx->part.p : nullptr;
     if (cols)
-        e = launch_select_bands_cols(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, ctx->num_sms, plist, pcnt,
-                                     fb, cplan, ub, tile_cnt, s);
+        e = launch_select_bands_cols(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, ctx->num_sms,
+                                     (int64_t)w * h >= kSplitFillPixels, plist, pcnt, fb, cplan, ub, tile_cnt, s);
     else
         e = launch_select_bands(logits, n, p.n_theta, q.p_band, q.p_fallback, q.margin, hp.pairs, tile_cap,
                                 ctx->num_sms, plist, pcnt, fb, tiles, ub, s);

@@ -220,11 +220,12 @@ cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p
 // The same band selection, planned for the interleaved-column kernel: tiles
 // of at most kHoughColPairs pairs, and when the launch's last wave (of
 // `slots` CTAs) would be at most half full, the tiles of the last frames split
-// into edge-range pieces (at most `slots` pieces).  Writes col_plan [n][3]
-// (tiles, n_splits, split_base), unit_begin [n + 1], and zeroes the split
-// tiles' counters tile_cnt [slots].
+// into edge-range pieces (at most `slots` pieces); with fewer tiles than
+// slots and `fill`, every tile splits.  Writes col_plan [n][3] (tiles,
+// n_splits, split_base), unit_begin [n + 1], and zeroes the split tiles'
+// counters tile_cnt [slots].
 cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, float p_band, float p_fallback,
-                                     int margin, int slots, int32_t *pair_list, int32_t *pair_count,
+                                     int margin, int slots, bool fill, int32_t *pair_list, int32_t *pair_count,
                                      int32_t *fallback, int32_t *col_plan, int32_t *unit_begin, int32_t *tile_cnt,
                                      cudaStream_t s);
 

@@ -133,10 +133,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_units_kernel(const int32_t 
 // whatever its pairs, so tiles are as few as possible.  When the U = sum T_f
 // units leave the persistent launch's last wave at most half full, the tiles
 // of the last frames (together at least that wave's units) are split into
-// ns = min(8, slots / their tiles) edge-range pieces, which fill it.
+// ns = min(8, slots / their tiles) edge-range pieces, which fill it.  With
+// fewer units than slots and `fill` (frames large enough), every tile splits
+// into min(8, slots / U) pieces (latency of small batches).
 __global__ void __launch_bounds__(kPlanThreads) plan_cols_units_kernel(const int32_t *pair_count, int n, int slots,
-                                                                       int32_t *col_plan, int32_t *unit_begin,
-                                                                       int32_t *tile_cnt) {
+                                                                       int fill, int32_t *col_plan,
+                                                                       int32_t *unit_begin, int32_t *tile_cnt) {
     __shared__ int tiles_s[kPlanThreads];
     const int tid = threadIdx.x;
     if (tid < n) {
@@ -150,7 +152,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_cols_units_kernel(const int
         for (int f = 0; f < n; ++f) u0 += tiles_s[f];
         int split_from = n, ns = 1;
         const int tail = u0 % slots;
-        if (u0 > slots && tail > 0 && 2 * tail <= slots) {
+        if (u0 < slots && fill) {
+            const int k = slots / u0 < 8 ? slots / u0 : 8;
+            if (k >= 2) {
+                split_from = 0;
+                ns = k;
+            }
+        } else if (u0 > slots && tail > 0 && 2 * tail <= slots) {
             int q = n, units = 0;
             while (q > 0 && units < tail) units += tiles_s[--q];
             const int k = slots / units < 8 ? slots / units : 8;
@@ -224,7 +232,7 @@ cudaError_t launch_select_bands(const float *logits, int n, int n_theta, float p
 }
 
 cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, float p_band, float p_fallback,
-                                     int margin, int slots, int32_t *pair_list, int32_t *pair_count,
+                                     int margin, int slots, bool fill, int32_t *pair_list, int32_t *pair_count,
                                      int32_t *fallback, int32_t *col_plan, int32_t *unit_begin, int32_t *tile_cnt,
                                      cudaStream_t s) {
     if (n < 1 || n > kPlanThreads || slots < 1) return cudaErrorInvalidValue;
@@ -232,7 +240,8 @@ cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, fl
                                           fallback);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    plan_cols_units_kernel<<<1, kPlanThreads, 0, s>>>(pair_count, n, slots, col_plan, unit_begin, tile_cnt);
+    plan_cols_units_kernel<<<1, kPlanThreads, 0, s>>>(pair_count, n, slots, fill ? 1 : 0, col_plan, unit_begin,
+                                                      tile_cnt);
     return cudaGetLastError();
 }
 

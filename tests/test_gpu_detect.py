@@ -162,9 +162,12 @@ def test_benchmark_config_uses_interleaved_kernel(ctx, ldlib):
 # of its last frames are voted in edge-range pieces that meet in a partial
 # accumulator.  13 x 1080p at 360 theta: 156 tiles on 152 SMs, the last frame
 # split 8 ways; 60 x 640x480 at 90 theta: 180 tiles, the last 10 frames split
-# 5 ways (pieces of a frame with only a few edge chunks get none).  Every frame
-# against the oracle.
-@pytest.mark.parametrize("n,w,h,n_theta", [(13, 1920, 1080, 360), (60, 640, 480, 90)])
+# 5 ways (pieces of a frame with only a few edge chunks get none).  Small
+# batches of large frames split every tile to fill the GPU: 1 x 1080p (12
+# tiles, 8 pieces each), 3 x 720p (36 tiles, 4 each).  Every frame against
+# the oracle.
+@pytest.mark.parametrize("n,w,h,n_theta", [(13, 1920, 1080, 360), (60, 640, 480, 90), (1, 1920, 1080, 360),
+                                           (3, 1280, 720, 360)])
 def test_detect_split_tiles(ctx, ldlib, ora, n, w, h, n_theta):
     raw = [synth.road_frame(6000 + i, w, h, synth.THROUGHPUT_1080P) for i in range(n)]
     kw = dict(n_theta=n_theta, top_k=4)
