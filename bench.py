@@ -323,6 +323,31 @@ def oracle_stages(reps_by_px=((400_000, 5), (1_000_000, 3), (2_100_000, 3), (10*
     return out
 
 
+def smem_red_rates(torch, ld, dev, n_sms: int) -> dict:
+    """Measured 32-bit shared-memory reduction rate of this GPU (Gred/s):
+    conflict-free (lanes on distinct banks: the ceiling of a vote) and random
+    words; 2 CTAs of 1024 threads per SM, best of 10 timed launches."""
+    stream = torch.cuda.current_stream(dev)
+    n_ctas = 2 * n_sms
+    sink = torch.zeros(n_ctas, dtype=torch.int32, device=dev)
+    out = {}
+    for pattern, name, iters in ((0, "conflict_free", 4096), (1, "random_words", 1024)):
+        for _ in range(3):
+            ld.ld_probe_smem_red(n_ctas, iters, pattern, sink.data_ptr(), stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(10):
+            e0.record(stream)
+            ld.ld_probe_smem_red(n_ctas, iters, pattern, sink.data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        if not bool((sink == 1024 * iters).all()):
+            raise RuntimeError("shared-memory reduction probe: wrong sums")
+        out[name] = n_ctas * 1024 * iters / (best / 1e3) / 1e9
+    return out
+
+
 def cpu_baseline(frames: np.ndarray, budget_s: float = 12.0):
     """The oracle as it stands: single-threaded on as many 1080p frames as fit
     the budget (the reported value); the same over all host cores (one
@@ -440,6 +465,7 @@ def main():
     views = ctx.prepare(frame_list)
     views_e2e = [ctx.prepare([fb[i] for i in range(nf)]) for fb in frames_e2e]
     stream = torch.cuda.current_stream(dev)
+    red_rates = smem_red_rates(torch, ld, dev, torch.cuda.get_device_properties(dev).multi_processor_count)
     ld.ld_ctx_enable_timing(ctx.handle, True)   # after the autotuner
 
     def step(vs):
@@ -538,13 +564,16 @@ def main():
         hough_s = stage_ms[1] / 1000.0
         sobel_s = stage_ms[0] / 1000.0
         sobel_bytes = nf * W * H * 1 + e_sum * 4
-        atom_peak = n_sms * 32 * sm_max_mhz * 1e6 / 1e9          # Gvote/s: 32 banks/clk/SM
+        atom_nominal = n_sms * 32 * sm_max_mhz * 1e6 / 1e9       # Gvote/s: 32 banks/clk/SM
+        atom_peak = red_rates["conflict_free"]
         roof = {"bound": "alu", "kernel": "hough_cols_kernel (Step 3 interleaved-column voting + per-tile top-M "
                                           "+ the frame's peak merge)",
                 "achieved": votes / hough_s / 1e9, "peak": atom_peak, "unit": "Gvote/s",
                 "frac": votes / hough_s / 1e9 / atom_peak, "traffic": measured_traffic("hough", nf),
-                "peak_basis": f"{n_sms} SMs x 32 shared-memory banks/clk x {sm_max_mhz:.0f} MHz "
-                              f"(one conflict-free 4-byte atomic per bank per clock)",
+                "peak_basis": "measured: conflict-free 32-lane red.shared.add.u32 rate of this GPU "
+                              f"(ld_probe_smem_red); nominal {n_sms} SMs x 32 banks x {sm_max_mhz:.0f} MHz = "
+                              f"{atom_nominal:.0f}",
+                "random_words_rate": red_rates["random_words"], "frac_of_nominal": votes / hough_s / 1e9 / atom_nominal,
                 "avg_launch_ms": stage_ms[1]}
         roof_sobel = {"bound": "hbm", "kernel": "sobel_bin_edges_kernel (Steps 1-2 + compaction)",
                       "achieved": sobel_bytes / sobel_s / 1e9, "peak": hbm_peak, "unit": "GB/s",

@@ -390,6 +390,17 @@ typedef struct {
 /* Generate n frames; d_frames is a DEVICE array of n descriptors. */
 LD_API ld_status ld_synth_frames(const ld_synth_frame *d_frames, int32_t n, void *stream);
 
+/* Measurement probe (not part of the path): n_ctas CTAs of 1024 threads each
+ * perform `iters` 32-bit shared-memory reductions per thread (red.shared.add)
+ * into a 16 KB shared array: pattern 0 puts the 32 lanes of every
+ * instruction on 32 distinct banks (the conflict-free rate that bounds Step
+ * 3's voting, Sec. 4.3), pattern 1 on pseudo-random words (32 unrelated
+ * votes).  Each CTA writes its array's sum (n_ctas * 1024 * iters in all) to
+ * d_sink[blockIdx] (device, n_ctas uint32).  The caller times the call on
+ * `stream`.  iters: a positive multiple of 8. */
+LD_API ld_status ld_probe_smem_red(int32_t n_ctas, int32_t iters, int32_t pattern, uint32_t *d_sink,
+                                   void *stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 LD_API const char *ld_last_error(void);
 

@@ -87,6 +87,7 @@ _SIGS = {
     "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
                     ctypes.POINTER(ctypes.c_int32)],
     "ld_synth_frames": [_P, ctypes.c_int32, _P],
+    "ld_probe_smem_red": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P],
     "ld_proposal_targets": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                             ctypes.c_int32, ctypes.c_float, _P, _P],
     "ld_detect_batch_proposal": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
@@ -238,6 +239,10 @@ def ld_ctx_stage_ms(ctx: int) -> tuple[float, float, int]:
 
 def ld_synth_frames(d_descs, n, stream) -> None:
     _check(load().ld_synth_frames(d_descs, n, stream))
+
+
+def ld_probe_smem_red(n_ctas, iters, pattern, d_sink, stream) -> None:
+    _check(load().ld_probe_smem_red(n_ctas, iters, pattern, d_sink, stream))
 
 
 def synth_descriptors(specs, bufs):

@@ -173,3 +173,14 @@ def test_detect_split_tiles(ctx, ldlib, ora, n, w, h, n_theta):
     kw = dict(n_theta=n_theta, top_k=4)
     pk, cnt, st = _detect(ctx, ldlib, raw, [w] * n, **kw)
     _check(ora, raw, pk, cnt, st, **kw)
+
+
+def test_shared_memory_reduction_probe(ldlib):
+    # the measurement probe of the voting ceiling: every reduction lands (sums exact)
+    sink = torch.zeros(8, dtype=torch.int32, device="cuda")
+    for pattern in (0, 1):
+        ldlib.ld_probe_smem_red(8, 64, pattern, sink.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert (sink.cpu().numpy() == 1024 * 64).all()
+    with pytest.raises(ldlib.LdError):
+        ldlib.ld_probe_smem_red(8, 12, 0, sink.data_ptr(), 0)   # iters not a multiple of 8
