@@ -763,8 +763,8 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
     }
     seq += (uint32_t)n_chunks;
     if (np < kCols) {   // clear the spare columns (votes of the unused slots' lanes)
-        for (int i = tid; i < words; i += kColThreads)
-            if (i % kCols >= np) acc[i] = 0u;
+        const int spare = kCols - np;
+        for (int i = tid; i < rows * spare; i += kColThreads) acc[(i / spare) * kCols + np + i % spare] = 0u;
         __syncthreads();
     }
 
