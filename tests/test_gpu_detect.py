@@ -184,3 +184,30 @@ def test_shared_memory_reduction_probe(ldlib):
         assert (sink.cpu().numpy() == 1024 * 64).all()
     with pytest.raises(ldlib.LdError):
         ldlib.ld_probe_smem_red(8, 12, 0, sink.data_ptr(), 0)   # iters not a multiple of 8
+
+
+def test_detect_split_tiles_mixed_sizes(ctx, ldlib, ora):
+    # 12 x 1080p + 1 x 720p at 360 theta: 156 tiles; the 720p frame is last in
+    # queue order (fewest pixels), so its tiles are the ones split, and its
+    # partial accumulators are smaller than the launch's stride (sized for
+    # 1080p rows).  Every frame against the oracle.
+    sizes = [(1920, 1080)] * 12 + [(1280, 720)]
+    raw = [synth.road_frame(6500 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    kw = dict(n_theta=360, top_k=4)
+    pk, cnt, st = _detect(ctx, ldlib, raw, [w for w, h in sizes], **kw)
+    _check(ora, raw, pk, cnt, st, **kw)
+
+
+@pytest.mark.parametrize("n_theta,top_k,nms_theta,nms_rho", [(4096, 16, 7, 3), (1000, 8, 5, 5)])
+def test_detect_many_theta_bins(ctx, ldlib, ora, n_theta, top_k, nms_theta, nms_rho):
+    # the interleaved-column kernel with many tiles a frame (4096 theta: 128
+    # tiles of 16 pairs; 1000 theta: 500 pairs in tiles of 16 and 15)
+    sizes = [(97, 61), (640, 480)]
+    raw = [synth.road_frame(6800 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    kw = dict(n_theta=n_theta, top_k=top_k, nms_theta=nms_theta, nms_rho=nms_rho)
+    p = ldlib.params(**kw)
+    for w, h in sizes:
+        assert ctx.plan(w, h, p)[0] < 0
+    frames = [synth.pitched(r, seed=i) for i, r in enumerate(raw)]
+    pk, cnt, st = _detect(ctx, ldlib, frames, [w for w, h in sizes], **kw)
+    _check(ora, raw, pk, cnt, st, **kw)
