@@ -269,6 +269,7 @@ double wave_fill(int64_t units, int num_sms) {
 // the persistent launch best; more tiles only when that gains > 2% of fill.
 void balance_tiles(std::vector<HoughPlan> &plans, int n_pairs, int num_sms) {
     const int gn = (int)plans.size();
+    if (gn == 0) return;
     for (int k = 1; k < gn; ++k)
         if (plans[k].n_tiles != plans[0].n_tiles || plans[k].n_rho != plans[0].n_rho) return;
     const int T0 = plans[0].n_tiles;
@@ -720,8 +721,9 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
     uint64_t *cand = (uint64_t *)ctx->cand.p;
 
     SobelLaunch SLn;
-    HoughLaunch HLn;
-    std::vector<int> order;
+    HoughLaunch HLn, HLp;   // interleaved-column and packed-pair voting launches
+    std::vector<int> order, sub_c, sub_p;
+    std::vector<char> is_cols;
     std::vector<int64_t> eoffs, coffs;
     std::vector<HoughPlan> plans;
 
@@ -741,20 +743,44 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         coffs.assign(gn, 0);
         plans.resize(gn);
         int64_t eoff = 0, coff = 0;
-        // one voting kernel per launch: the interleaved-column one only if
-        // every frame of the group gets an interleaved plan
-        bool cols = p.min_votes >= 1;
-        for (int k = 0; k < gn && cols; ++k) {
+        // voting kernels: the interleaved-column kernel for the frames whose
+        // plan allows it, the packed-pair kernel for the rest.  A group with
+        // both kinds votes in two launches only if each part fills the GPU on
+        // its own (else all frames take the packed-pair kernel in one launch,
+        // so that small mixed batches keep one concurrent launch).
+        is_cols.assign(gn, 0);
+        int tiles_c = 0, tiles_p = 0;
+        for (int k = 0; k < gn; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
-            plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, true);
-            cols = plans[k].cols;
-        }
-        if (!cols) {
-            for (int k = 0; k < gn; ++k) {
-                const ld_frame &fr = h_frames[g0 + k];
-                plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
+            if (p.min_votes >= 1) {
+                const HoughPlan hc = plan_for(ctx, fr.w, fr.h, p.n_theta, true);
+                if (hc.cols) {
+                    plans[k] = hc;
+                    is_cols[k] = 1;
+                    tiles_c += hc.n_tiles;
+                    continue;
+                }
             }
-            balance_tiles(plans, p.n_theta / 2, ctx->num_sms);
+            plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
+            tiles_p += plans[k].n_tiles;
+        }
+        if (tiles_c > 0 && tiles_p > 0 && (tiles_c < ctx->num_sms || tiles_p < ctx->num_sms)) {
+            for (int k = 0; k < gn; ++k)
+                if (is_cols[k]) {
+                    const ld_frame &fr = h_frames[g0 + k];
+                    plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
+                    is_cols[k] = 0;
+                }
+        }
+        {   // wave-filling tile counts for the packed-pair frames (equal plans only)
+            std::vector<HoughPlan> pp;
+            for (int k = 0; k < gn; ++k)
+                if (!is_cols[k]) pp.push_back(plans[k]);
+            if (!pp.empty()) {
+                balance_tiles(pp, p.n_theta / 2, ctx->num_sms);
+                for (int k = 0, i = 0; k < gn; ++k)
+                    if (!is_cols[k]) plans[k] = pp[i++];
+            }
         }
         for (int k = 0; k < gn; ++k) {
             const ld_frame &fr = h_frames[g0 + k];
@@ -790,96 +816,117 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             const int64_t cb = (int64_t)h_frames[g0 + b].w * h_frames[g0 + b].h * plans[b].pairs;
             return ca > cb;
         });
+        // One voting launch over the frames sub (queue order) with one kernel.
         // Interleaved kernel: when the launch's last wave would be at most half
         // full, split each tile of the last frames in queue order (together
         // at least as many tiles as that wave holds) into ns edge ranges
         // (pieces, at most num_sms in all), which spread over the wave.  A
         // launch with fewer tiles than SMs (small batches: latency) splits
         // every tile, if its frames are large enough.
-        int split_from = gn, ns_split = 1, split_tiles = 0, rows_max = 1;
-        if (cols) {
-            int U0 = 0;
-            int64_t px_min = INT64_MAX;
-            for (int k = 0; k < gn; ++k) {
-                U0 += plans[k].n_tiles;
-                rows_max = std::max(rows_max, plans[k].rows);
-                px_min = std::min(px_min, (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h);
-            }
-            const int S = ctx->num_sms, tail = U0 % S;
-            if (U0 < S && px_min >= kSplitFillPixels) {
-                const int ns = std::min(kMaxSplits, S / U0);
-                if (ns >= 2) {
-                    split_from = 0;
-                    ns_split = ns;
-                    split_tiles = U0;
+        struct Built {
+            int units = 0, pmax = 1, rows_max = 1;
+            int64_t words_max = 0;
+        };
+        auto build_launch = [&](HoughLaunch &HL, bool cols, const std::vector<int> &sub, int32_t *queue,
+                                Built &B) -> ld_status {
+            const int gs = (int)sub.size();
+            std::memset(&HL, 0, sizeof HL);
+            int split_from = gs, ns_split = 1, split_tiles = 0;
+            if (cols) {
+                int U0 = 0;
+                int64_t px_min = INT64_MAX;
+                for (int k : sub) {
+                    U0 += plans[k].n_tiles;
+                    B.rows_max = std::max(B.rows_max, plans[k].rows);
+                    px_min = std::min(px_min, (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h);
                 }
-            } else if (U0 > S && tail > 0 && 2 * tail <= S) {
-                int q = gn, units = 0;
-                while (q > 0 && units < tail) units += plans[order[--q]].n_tiles;
-                const int ns = std::min(kMaxSplits, S / units);
-                if (ns >= 2) {
-                    split_from = q;
-                    ns_split = ns;
-                    split_tiles = units;
+                const int S = ctx->num_sms, tail = U0 % S;
+                if (U0 < S && px_min >= kSplitFillPixels) {
+                    const int ns = std::min(kMaxSplits, S / U0);
+                    if (ns >= 2) {
+                        split_from = 0;
+                        ns_split = ns;
+                        split_tiles = U0;
+                    }
+                } else if (U0 > S && tail > 0 && 2 * tail <= S) {
+                    int q = gs, units = 0;
+                    while (q > 0 && units < tail) units += plans[sub[--q]].n_tiles;
+                    const int ns = std::min(kMaxSplits, S / units);
+                    if (ns >= 2) {
+                        split_from = q;
+                        ns_split = ns;
+                        split_tiles = units;
+                    }
+                }
+                HL.col_chunk = hough_cols_chunk(B.rows_max);
+                HL.part_stride = B.rows_max * kHoughColPairs;
+                if (split_tiles > 0) {
+                    const size_t cnt_bytes = ((size_t)split_tiles * 4 + 255) / 256 * 256;
+                    if (!ctx->part.ensure(split_scratch_bytes(split_tiles * ns_split, B.rows_max)))
+                        return fail(LD_ERR_NOMEM, "scratch partial accumulators");
+                    HL.tile_cnt = (int32_t *)ctx->part.p;
+                    HL.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
+                    const cudaError_t r = cudaMemsetAsync(ctx->part.p, 0, (size_t)split_tiles * 4, s);
+                    if (r != cudaSuccess) return cuda_fail(r, "cudaMemsetAsync(split counters)");
                 }
             }
-            HLn.col_chunk = hough_cols_chunk(rows_max);
-            HLn.part_stride = rows_max * kHoughColPairs;
-            if (split_tiles > 0) {
-                const size_t cnt_bytes = ((size_t)split_tiles * 4 + 255) / 256 * 256;
-                if (!ctx->part.ensure(split_scratch_bytes(split_tiles * ns_split, rows_max)))
-                    return fail(LD_ERR_NOMEM, "scratch partial accumulators");
-                HLn.tile_cnt = (int32_t *)ctx->part.p;
-                HLn.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
-                e = cudaMemsetAsync(ctx->part.p, 0, (size_t)split_tiles * 4, s);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(split counters)");
+            HL.n = gs;
+            HL.n_theta = p.n_theta;
+            HL.mode = kHoughCandidates;
+            HL.cand_m = M;
+            HL.min_votes = p.min_votes;
+            HL.top_k = p.top_k;
+            HL.nms_theta = p.nms_theta;
+            HL.nms_rho = p.nms_rho;
+            HL.trig = dt;
+            HL.queue = queue;
+            int split_base = 0;
+            for (int q = 0; q < gs; ++q) {
+                const int k = sub[q];
+                const ld_frame &fr = h_frames[g0 + k];
+                const HoughPlan &hp = plans[k];
+                HoughFrame &HF = HL.f[q];
+                HF.edges = edges + eoffs[k];
+                HF.count = sm.counts + k;
+                HF.cap = (int64_t)fr.w * fr.h;
+                HF.acc = nullptr;
+                HF.cand = cand + coffs[k];
+                HF.flags = sm.flags + k;
+                HF.done = sm.done + k;
+                HF.peaks = d_peaks + (size_t)(g0 + k) * p.top_k;
+                HF.n_peaks = d_n_peaks + g0 + k;
+                HF.status = d_status + g0 + k;
+                HF.w = fr.w;
+                HF.h = fr.h;
+                HF.D = hp.D;
+                HF.n_rho = hp.n_rho;
+                HF.unit_begin = B.units;
+                HF.n_splits = q >= split_from ? ns_split : 1;
+                HF.split_base = HF.n_splits > 1 ? split_base : 0;
+                if (HF.n_splits > 1) split_base += hp.n_tiles;
+                HF.pairs_per_tile = hp.pairs;
+                HF.n_tiles = hp.n_tiles;
+                HF.rows = hp.rows;
+                B.units += hp.n_tiles * HF.n_splits;
+                if (hp.pairs > B.pmax) B.pmax = hp.pairs;
+                const int64_t wds = (int64_t)hp.pairs * hp.n_rho;
+                if (wds > B.words_max) B.words_max = wds;
             }
+            HL.total_units = B.units;
+            return LD_OK;
+        };
+        sub_c.clear();
+        sub_p.clear();
+        for (int q = 0; q < gn; ++q) (is_cols[order[q]] ? sub_c : sub_p).push_back(order[q]);
+        Built bc, bp;
+        if (!sub_c.empty()) {
+            st = build_launch(HLn, true, sub_c, sm.queue, bc);
+            if (st != LD_OK) return st;
         }
-        HLn.n = gn;
-        HLn.n_theta = p.n_theta;
-        HLn.mode = kHoughCandidates;
-        HLn.cand_m = M;
-        HLn.min_votes = p.min_votes;
-        HLn.top_k = p.top_k;
-        HLn.nms_theta = p.nms_theta;
-        HLn.nms_rho = p.nms_rho;
-        HLn.trig = dt;
-        HLn.queue = sm.queue;
-        int units = 0, pmax = 1, split_base = 0;
-        int64_t words_max = 0;
-        for (int q = 0; q < gn; ++q) {
-            const int k = order[q];
-            const ld_frame &fr = h_frames[g0 + k];
-            const HoughPlan &hp = plans[k];
-            HoughFrame &HF = HLn.f[q];
-            HF.edges = edges + eoffs[k];
-            HF.count = sm.counts + k;
-            HF.cap = (int64_t)fr.w * fr.h;
-            HF.acc = nullptr;
-            HF.cand = cand + coffs[k];
-            HF.flags = sm.flags + k;
-            HF.done = sm.done + k;
-            HF.peaks = d_peaks + (size_t)(g0 + k) * p.top_k;
-            HF.n_peaks = d_n_peaks + g0 + k;
-            HF.status = d_status + g0 + k;
-            HF.w = fr.w;
-            HF.h = fr.h;
-            HF.D = hp.D;
-            HF.n_rho = hp.n_rho;
-            HF.unit_begin = units;
-            HF.n_splits = q >= split_from ? ns_split : 1;
-            HF.split_base = HF.n_splits > 1 ? split_base : 0;
-            if (HF.n_splits > 1) split_base += hp.n_tiles;
-            HF.pairs_per_tile = hp.pairs;
-            HF.n_tiles = hp.n_tiles;
-            HF.rows = hp.rows;
-            units += hp.n_tiles * HF.n_splits;
-            if (hp.pairs > pmax) pmax = hp.pairs;
-            const int64_t wds = (int64_t)hp.pairs * hp.n_rho;
-            if (wds > words_max) words_max = wds;
+        if (!sub_p.empty()) {
+            st = build_launch(HLp, false, sub_p, sm.queue + 1, bp);
+            if (st != LD_OK) return st;
         }
-        HLn.total_units = units;
-        const int hough_ctas = units < ctx->num_sms ? units : ctx->num_sms;
         // stage events of this call (first launch group), 3 per timed call
         cudaEvent_t *tev = nullptr;
         if (ctx->timing && g0 == 0 && ctx->timed_calls < kMaxTimedCalls) {
@@ -897,9 +944,14 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         e = launch_sobel(SLn, sob_ctas, s);
         if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
         if (tev) cudaEventRecord(tev[1], s);
-        e = cols ? launch_hough_cols(HLn, hough_ctas, rows_max, s)
-                 : launch_hough(HLn, hough_ctas, pmax, words_max, s);
-        if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+        if (!sub_c.empty()) {
+            e = launch_hough_cols(HLn, std::min(bc.units, ctx->num_sms), bc.rows_max, s);
+            if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+        }
+        if (!sub_p.empty()) {
+            e = launch_hough(HLp, std::min(bp.units, ctx->num_sms), bp.pmax, bp.words_max, s);
+            if (e != cudaSuccess) return cuda_fail(e, "hough launch");
+        }
         if (tev) cudaEventRecord(tev[2], s);
     }
     return LD_OK;

@@ -211,3 +211,14 @@ def test_detect_many_theta_bins(ctx, ldlib, ora, n_theta, top_k, nms_theta, nms_
     frames = [synth.pitched(r, seed=i) for i, r in enumerate(raw)]
     pk, cnt, st = _detect(ctx, ldlib, frames, [w for w, h in sizes], **kw)
     _check(ora, raw, pk, cnt, st, **kw)
+
+
+def test_detect_two_voting_launches(ctx, ldlib, ora):
+    # 14 x 1080p + 5 x 4K at 360 theta: the 1080p frames' 168 interleaved tiles
+    # and the 4K frames' 180 packed-pair tiles each fill the GPU, so the group
+    # votes in two launches (one per kernel).  Every frame against the oracle.
+    sizes = [(1920, 1080)] * 14 + [(3840, 2160)] * 5
+    raw = [synth.road_frame(6900 + i, w, h, synth.THROUGHPUT_1080P) for i, (w, h) in enumerate(sizes)]
+    kw = dict(n_theta=360, top_k=4)
+    pk, cnt, st = _detect(ctx, ldlib, raw, [w for w, h in sizes], **kw)
+    _check(ora, raw, pk, cnt, st, **kw)
