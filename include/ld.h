@@ -104,7 +104,9 @@ LD_API ld_status ld_ctx_destroy(ld_ctx *ctx);
 /* Pre-size the context scratch so that later ld_detect_batch calls with at
  * most `max_frames` frames totalling `max_pixels` pixels, and ld_hough_peaks
  * calls on at most `max_acc_cells` cells, allocate nothing (needed before
- * capturing those calls in a CUDA graph). */
+ * capturing those calls in a CUDA graph).  With max_frames > 0 this includes
+ * the partial accumulators of split voting tiles (one per SM at the largest
+ * interleaved accumulator, about 30 MB on a 152-SM GPU). */
 LD_API ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames,
                          int64_t max_acc_cells, const ld_params *p);
 
@@ -173,6 +175,13 @@ LD_API ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_the
  *                (LD_OK, or LD_ERR_TIMEOUT if a bounded wait gave up).
  * Edge lists and candidate buffers live in the context scratch, sized for
  * the worst case (every pixel an edge), so no capacity error can occur.
+ * Step 3 runs in one of two voting kernels, per launch group of up to 128
+ * frames: with min_votes >= 1, frames whose theta windows fit shared memory
+ * (up to about 2560x1440) take the interleaved-column kernel, the others the
+ * packed-pair kernel; a group with both kinds takes one launch per kernel
+ * when each part fills the GPU, else the packed-pair kernel for all.  The
+ * results never depend on the kernel, the tile sizes or the edge-range
+ * splits.
  */
 LD_API ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
                           const ld_params *p, ld_peak *d_peaks,
