@@ -222,3 +222,16 @@ def test_detect_two_voting_launches(ctx, ldlib, ora):
     kw = dict(n_theta=360, top_k=4)
     pk, cnt, st = _detect(ctx, ldlib, raw, [w for w, h in sizes], **kw)
     _check(ora, raw, pk, cnt, st, **kw)
+
+
+def test_detect_noise_frames_nearly_all_edges(ctx, ldlib, ora):
+    # uniform noise: ~93% of the pixels are edges (edge lists near w*h, cells
+    # with ~2000 votes, hundreds of streamed chunks per tile); a lone 1080p
+    # frame (tiles split over the GPU) and a 640x480 one in one call
+    rng = np.random.default_rng(77)
+    raw = [rng.integers(0, 256, size=(1080, 1920), dtype=np.uint8),
+           rng.integers(0, 256, size=(480, 640), dtype=np.uint8)]
+    for frames in ([raw[0]], raw):
+        kw = dict(n_theta=360, top_k=4)
+        pk, cnt, st = _detect(ctx, ldlib, frames, [f.shape[1] for f in frames], **kw)
+        _check(ora, frames, pk, cnt, st, **kw)
