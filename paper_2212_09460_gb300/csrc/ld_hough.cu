@@ -549,33 +549,44 @@ hough_kernel(const __grid_constant__ HoughLaunch L) {
 
 // ---------------------------------------------------------------- interleaved columns
 //
-// Second voting kernel for the full-vote detection path.  Each 32-lane
-// red.shared of the kernel above hits 32 random words, and 32 random words
-// fall on about 3.5 distinct-bank wavefronts.  Here lane l of a warp owns
-// slot l % 16 of a tile of up to 16 theta pairs, and the tile's words are
-// interleaved (word = row * 16 + slot), so slot l lives in banks l and l + 16
-// only.  The two half-warps vote two different edges into the same 16 slots,
-// so one red.shared costs at most 2 wavefronts (2 when any slot's two rows
-// agree in parity, i.e. almost always), against about 3.5 for 32 random
-// words.  Each theta's rho window starts at its own
-// minimum over the image corners, so a column needs only the frame's widest
-// window (at most D + 1 rows) instead of 2D + 1: 16 pairs of a 1080p frame
-// take 141 KB.  Each lane holds the (cos, sin) of both thetas of its pair, so
-// the pair {0, n/2} needs no special case.  Edge lists are read as 16-byte
-// groups of 4 edges, one group per half-warp and loop step (a broadcast
-// load); the first half of each streamed chunk goes to half-warp 0 and the
-// second to half-warp 1, so that the two edges voted together lie far apart
-// in the row-major list (far-apart edges seldom share a cell).  The edge
-// ring has 2 stages of 8192 edges (4096 when the accumulator leaves less
-// room): fewer, larger chunks measured faster.  A launch whose last wave would
-// be poorly filled splits the tiles of its last frames into edge ranges
-// (pieces), which fill that wave.  The vote has
-// no per-edge branch (the kernel is issue-bound without the bank conflicts):
-// addresses are 32-bit shared-window offsets, the lanes of unused slots vote
-// into their own spare columns, which are cleared before the selection, and
-// coordinates are clamped into the image.  The clamp is a memory guard only:
-// this kernel votes edge lists written by the Sobel kernel, whose entries are
-// always inside the image.
+// Second voting kernel, for the detection paths (candidate mode, min_votes
+// >= 1): the full vote of ld_detect_batch and the restricted vote of the
+// proposal path.
+//
+// Banks.  Each 32-lane red.shared of the kernel above hits 32 random words,
+// which fall on about 3.5 distinct-bank wavefronts.  Here lane l of a warp
+// owns slot l % 16 of a tile of up to 16 theta pairs, and the tile's words
+// are interleaved (word = row * 16 + slot), so slot l lives in banks l and
+// l + 16 only.  The two half-warps vote two different edges into the same 16
+// slots, so one red.shared costs at most 2 wavefronts (2 when any slot's two
+// rows agree in parity, i.e. almost always).
+//
+// Rows.  Each theta's rho window starts at its own minimum over the image
+// corners, so a column needs only the frame's widest window (at most D + 1
+// rows) instead of 2D + 1: 16 pairs of a 1080p frame take 141 KB.  Cells
+// outside a window have no votes, which min_votes >= 1 keeps out of the peaks.
+//
+// Vote.  Each lane holds the (cos, sin) of both thetas of its pair, so the
+// pair {0, n/2} needs no special case.  The vote has no per-edge branch (the
+// kernel is issue-bound once the bank conflicts are gone): one min.u16x2
+// clamps (y, x) into the image, x is folded into the multiply (e = y * 65536
+// + x, so e c + y (s - 65536 c) = x c + y s mod 2^32), addresses are 32-bit
+// shared-window offsets, and the lanes of unused slots vote into their own
+// spare columns, which are cleared before the selection.  The clamp is a
+// memory guard only: the edge lists come from the Sobel kernel, whose entries
+// are always inside the image.
+//
+// Edges.  The edge list streams through a 2-stage ring of 8192-edge chunks
+// (4096 when the accumulator leaves less room; fewer, larger chunks measured
+// faster) without block barriers.  Each half-warp reads a 16-byte group of 4
+// edges per loop step (a broadcast load).  The first half of each chunk goes to
+// half-warp 0 and the second to half-warp 1, so the two edges voted together
+// lie far apart in the row-major list (far-apart edges seldom share a cell).
+//
+// Pieces.  A launch whose last wave would be poorly filled, or a small launch
+// with fewer tiles than SMs, splits tiles into edge-range pieces.  Their
+// partial accumulators meet in global memory, and the last piece of a tile
+// adds them up and selects.
 constexpr int kColThreads = 1024;
 constexpr int kColWarps = kColThreads / 32;
 constexpr int kColStages = 2;                 // edge ring stages of L.col_chunk edges
