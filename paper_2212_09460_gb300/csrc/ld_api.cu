@@ -14,8 +14,10 @@
 #include <vector>
 
 #include "ld_internal.cuh"
+#include "ld_plan.h"
 
 using namespace ld;
+static_assert(kPlanColPairs == kHoughColPairs, "planning and kernel tile widths differ");
 
 namespace {
 
@@ -97,25 +99,6 @@ struct ld_ctx {
 };
 
 namespace {
-
-int64_t rho_max_of(int64_t w, int64_t h) {
-    const int64_t r2 = w * w + h * h;
-    int64_t d = (int64_t)std::sqrt((double)r2);
-    while (d * d < r2) ++d;
-    while (d > 0 && (d - 1) * (d - 1) >= r2) --d;
-    return d;
-}
-
-// Q16 table over k = 0..n_theta/2 (Eqs. 4-5 supply the rest on the device).
-std::vector<int32_t> make_trig(int n_theta) {
-    std::vector<int32_t> t(2 * (n_theta / 2 + 1));
-    for (int k = 0; k <= n_theta / 2; ++k) {
-        const double a = (double)k * M_PI / (double)n_theta;
-        t[2 * k] = (int32_t)std::llround(std::cos(a) * 65536.0);
-        t[2 * k + 1] = (int32_t)std::llround(std::sin(a) * 65536.0);
-    }
-    return t;
-}
 
 ld_status check_params(const ld_params *p) {
     if (!p) return LD_OK;
@@ -230,20 +213,9 @@ Small small_of(void *p) {
 // Split tiles of the interleaved voting kernel: at most num_sms pieces in a
 // launch; scratch = the pieces' arrival counters (one per tile, 256-byte
 // padded) then their partial accumulators.
-constexpr int kMaxSplits = 8;
-// A launch with fewer tiles than SMs splits every tile (to fill the GPU)
-// only when its frames have at least this many pixels: below it a tile's edge
-// stream is too short to pay for a piece's partial store and merge.
-constexpr int64_t kSplitFillPixels = 1 << 19;
 size_t split_scratch_bytes(int pieces, int rows) {
     return ((size_t)pieces * 4 + 255) / 256 * 256 + (size_t)pieces * rows * kHoughColPairs * 4;
 }
-
-struct HoughPlan {
-    int n_rho, D, pairs, n_tiles;
-    bool cols = false;   // interleaved-column kernel (tiles of <= kHoughColPairs pairs)
-    int rows = 0;        // its accumulator rows
-};
 
 HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
     HoughPlan hp;
@@ -256,38 +228,6 @@ HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
     hp.n_tiles = (n_pairs + hp.pairs - 1) / hp.pairs;
     hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;   // pairs are split evenly over the tiles
     return hp;
-}
-
-// Fraction of the persistent CTAs' slots that `units` equal work units fill.
-double wave_fill(int64_t units, int num_sms) {
-    const int64_t waves = (units + num_sms - 1) / num_sms;
-    return waves > 0 ? (double)units / (double)(waves * num_sms) : 1.0;
-}
-
-// For a launch group whose frames share one plan: the tile count in
-// [T, 1.25 T] (and at least 2 pairs per tile) whose units fill the last wave of
-// the persistent launch best; more tiles only when that gains > 2% of fill.
-void balance_tiles(std::vector<HoughPlan> &plans, int n_pairs, int num_sms) {
-    const int gn = (int)plans.size();
-    if (gn == 0) return;
-    for (int k = 1; k < gn; ++k)
-        if (plans[k].n_tiles != plans[0].n_tiles || plans[k].n_rho != plans[0].n_rho) return;
-    const int T0 = plans[0].n_tiles;
-    if ((int64_t)gn * T0 < num_sms) return;
-    int best = T0;
-    double best_fill = wave_fill((int64_t)gn * T0, num_sms);
-    for (int T = T0 + 1; T <= T0 + (T0 + 3) / 4 && 2 * T <= n_pairs; ++T) {
-        const double f = wave_fill((int64_t)gn * T, num_sms);
-        if (f > best_fill + 0.02) {
-            best = T;
-            best_fill = f;
-        }
-    }
-    if (best == T0) return;
-    for (HoughPlan &hp : plans) {
-        hp.n_tiles = best;
-        hp.pairs = (n_pairs + best - 1) / best;
-    }
 }
 
 HoughPlan plan_hough(int w, int h, int n_theta) {
@@ -312,27 +252,13 @@ HoughPlan plan_hough(int w, int h, int n_theta) {
     return hp;
 }
 
-// Rows of the interleaved-column accumulator for w x h frames: the widest
-// theta window, max - min + 1 over the image corners of
-// floor((x c + y s + 32768) / 65536), over the thetas the kernel votes
-// ((c_k, s_k) for k <= n/2 from the table, (-c_k, s_k) for n/2 < n - k < n).
+// Rows of the interleaved-column accumulator for w x h frames (window_rows,
+// cached in the context).
 int interleaved_rows(const ld_ctx *ctx, int w, int h, int n_theta) {
     const auto key = std::make_tuple(w, h, n_theta);
     auto it = ctx->col_rows.find(key);
     if (it != ctx->col_rows.end()) return it->second;
-    const std::vector<int32_t> t = make_trig(n_theta);
-    const int half = n_theta / 2;
-    auto fl = [](int64_t v) { return v >= 0 ? v / 65536 : -((-v + 65535) / 65536); };
-    int64_t rows = 1;
-    for (int k = 0; k < n_theta; ++k) {
-        const int kk = k <= half ? k : n_theta - k;
-        const int64_t c = k <= half ? t[2 * kk] : -t[2 * kk];
-        const int64_t s = t[2 * kk + 1];
-        const int64_t xlo = c < 0 ? (w - 1) * c : 0, xhi = c < 0 ? 0 : (w - 1) * c;
-        const int64_t ylo = s < 0 ? (h - 1) * s : 0, yhi = s < 0 ? 0 : (h - 1) * s;
-        rows = std::max(rows, fl(xhi + yhi + 32768) - fl(xlo + ylo + 32768) + 1);
-    }
-    const int r = (int)std::min<int64_t>(rows, 1 << 30);
+    const int r = window_rows(w, h, n_theta, make_trig(n_theta));
     ctx->col_rows[key] = r;
     return r;
 }
@@ -764,7 +690,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
             tiles_p += plans[k].n_tiles;
         }
-        if (tiles_c > 0 && tiles_p > 0 && (tiles_c < ctx->num_sms || tiles_p < ctx->num_sms)) {
+        if (tiles_c > 0 && tiles_p > 0 && !two_launches(tiles_c, tiles_p, ctx->num_sms)) {
             for (int k = 0; k < gn; ++k)
                 if (is_cols[k]) {
                     const ld_frame &fr = h_frames[g0 + k];
@@ -833,31 +759,18 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             std::memset(&HL, 0, sizeof HL);
             int split_from = gs, ns_split = 1, split_tiles = 0;
             if (cols) {
-                int U0 = 0;
                 int64_t px_min = INT64_MAX;
-                for (int k : sub) {
-                    U0 += plans[k].n_tiles;
+                std::vector<int> tiles_q(gs);
+                for (int q = 0; q < gs; ++q) {
+                    const int k = sub[q];
+                    tiles_q[q] = plans[k].n_tiles;
                     B.rows_max = std::max(B.rows_max, plans[k].rows);
                     px_min = std::min(px_min, (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h);
                 }
-                const int S = ctx->num_sms, tail = U0 % S;
-                if (U0 < S && px_min >= kSplitFillPixels) {
-                    const int ns = std::min(kMaxSplits, S / U0);
-                    if (ns >= 2) {
-                        split_from = 0;
-                        ns_split = ns;
-                        split_tiles = U0;
-                    }
-                } else if (U0 > S && tail > 0 && 2 * tail <= S) {
-                    int q = gs, units = 0;
-                    while (q > 0 && units < tail) units += plans[sub[--q]].n_tiles;
-                    const int ns = std::min(kMaxSplits, S / units);
-                    if (ns >= 2) {
-                        split_from = q;
-                        ns_split = ns;
-                        split_tiles = units;
-                    }
-                }
+                const PieceSplit ps = plan_pieces(tiles_q.data(), gs, px_min, ctx->num_sms);
+                split_from = ps.split_from;
+                ns_split = ps.ns;
+                split_tiles = ps.split_tiles;
                 HL.col_chunk = hough_cols_chunk(B.rows_max);
                 HL.part_stride = B.rows_max * kHoughColPairs;
                 if (split_tiles > 0) {

@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "ld_internal.cuh"
+#include "ld_plan.h"
 
 namespace ld {
 namespace {
@@ -148,25 +149,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_cols_units_kernel(const int
     for (int i = tid; i < slots; i += blockDim.x) tile_cnt[i] = 0;
     __syncthreads();
     if (tid == 0) {
-        int u0 = 0;
-        for (int f = 0; f < n; ++f) u0 += tiles_s[f];
-        int split_from = n, ns = 1;
-        const int tail = u0 % slots;
-        if (u0 < slots && fill) {
-            const int k = slots / u0 < 8 ? slots / u0 : 8;
-            if (k >= 2) {
-                split_from = 0;
-                ns = k;
-            }
-        } else if (u0 > slots && tail > 0 && 2 * tail <= slots) {
-            int q = n, units = 0;
-            while (q > 0 && units < tail) units += tiles_s[--q];
-            const int k = slots / units < 8 ? slots / units : 8;
-            if (k >= 2) {
-                split_from = q;
-                ns = k;
-            }
-        }
+        // the host plan's rule (ld_plan.h), with fill standing for the frame size
+        const PieceSplit ps = plan_pieces(tiles_s, n, fill ? kSplitFillPixels : 0, slots);
+        const int split_from = ps.split_from, ns = ps.ns;
         int ub = 0, sb = 0;
         for (int f = 0; f < n; ++f) {
             const int t = tiles_s[f], k = f >= split_from ? ns : 1;
