@@ -189,6 +189,12 @@ class ServeStats:
     wall_s: float = 0.0
     batch_device_ms: list = field(default_factory=list)   # (device ms, batch class, frames) per batch
     max_loop_gap_ms: float = 0.0   # longest time between two scheduler iterations
+    max_phase_ms: dict = field(default_factory=dict)   # longest single load / poll / submit / idle call
+
+    def phase(self, name: str, t0: float, t1: float) -> None:
+        ms = (t1 - t0) * 1e3
+        if name not in self.max_phase_ms or ms > self.max_phase_ms[name]:
+            self.max_phase_ms[name] = ms
 
 
 class Scheduler:
@@ -244,7 +250,9 @@ class Scheduler:
                     newly.append(f)
             if newly:
                 newly.sort(key=lambda f: f.t_arrival)
+                t0 = clock.now()
                 ex.load(newly)
+                st.phase("load", t0, clock.now())
                 for f in newly:
                     admitted.setdefault(ex.batch_class(f), deque()).append(f)
                 progressed = True
@@ -253,7 +261,9 @@ class Scheduler:
             for wi in range(ex.n_workers):
                 if not ex.busy(wi):
                     continue
+                t0 = clock.now()
                 res = ex.poll(wi)
+                st.phase("poll", t0, clock.now())
                 if res is None:
                     inflight += 1
                     continue
@@ -285,7 +295,9 @@ class Scheduler:
                 t_launch = clock.now()
                 for f in frames:
                     f.t_launch, f.batch = t_launch, seq
+                t0 = clock.now()
                 ex.submit(wi, frames, seq)
+                st.phase("submit", t0, clock.now())
                 st.launches += 1
                 st.batch_sizes.append(len(frames))
                 seq += 1
@@ -293,7 +305,9 @@ class Scheduler:
             st.max_slots_in_use = max(st.max_slots_in_use, adm.max_in_use)
             if not progressed:
                 busy = any(ex.busy(wi) for wi in range(ex.n_workers))
+                t0 = clock.now()
                 clock.idle(arrivals[ai].t_arrival if ai < total else None, busy)
+                st.phase("idle", t0, clock.now())
         st.wall_s = clock.now() - t_start
         return st
 
@@ -319,6 +333,7 @@ def summarize(st: ServeStats) -> dict:
             "proposal_fallback_rate": float(np.mean(fb)) if fb else None,
             "status_nonzero": int(sum(1 for f in fr if f.status != 0)),
             "max_loop_gap_ms": st.max_loop_gap_ms,
+            "max_phase_ms": dict(st.max_phase_ms),
             **_device_summary(st.batch_device_ms)}
 
 

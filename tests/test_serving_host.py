@@ -181,6 +181,10 @@ def test_light_load_serves_every_frame_alone(ora):
     assert np.mean(st.batch_sizes) < 1.5                        # arrivals rarely coincide
     s = summarize(st)
     assert s["frames"] == len(arr) and 0 < s["latency_ms_p50"] <= s["latency_ms_p99"] <= s["latency_ms_max"]
+    # stall attribution: the loop's longest gap and its longest call of each phase
+    ph = s["max_phase_ms"]
+    assert {"load", "poll", "submit", "idle"} <= set(ph) and ph["idle"] > 0
+    assert s["max_loop_gap_ms"] >= max(ph.values()) - 1e-9
 
 
 def test_heavy_load_batches_and_backpressure(ora):
