@@ -202,10 +202,13 @@ LD_API ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t 
  * on the calling thread's current device, plus one limit: ceil(n_theta*n_rho /
  * 16384) * (nms_theta*nms_rho*(top_k-1)+1) <= 131072 (a 360 x 4407
  * accumulator with 5x5 windows and top_k 4 needs 7372), else LD_ERR_INVALID.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls on a device share the
- * array (each call rewrites every slot it reads, nothing needs clearing), so
- * calls whose work overlaps on the GPU race: serialise them.
+ * The first call on a device looks up the array's device address and keeps
+ * it; make that first call before any stream capture, and do not call this
+ * entry point on a device after cudaDeviceReset (or another teardown of its
+ * primary context) in the same process, since the kept address is then stale.
+ * All calls on a device share the array (each call rewrites every slot it
+ * reads, nothing needs clearing), so calls whose work overlaps on the GPU
+ * race: serialise them.  p may be NULL for the defaults.
  */
 LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
                                        int32_t n_rho, const ld_params *p,
@@ -236,6 +239,16 @@ LD_API ld_status ld_autotune(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
  * up to 16 pairs; a launch group uses it only if every frame's plan does). */
 LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params *p,
                              int32_t *pairs_per_tile, int32_t *sobel_rows);
+
+/* Fault-injection knob for the bounded waits of the voting kernels (not a
+ * step of the method).  Later calls on ctx give up a wait for a streamed edge
+ * chunk after `polls` polls of its mbarrier: 0 gives up at once, a negative
+ * value restores the default 2^26 (polls <= 2^26, else LD_ERR_INVALID).  A CTA
+ * whose wait gave up flags its frame, waits (with the default limit) for the
+ * copies it issued itself, and stops; the frame's status stays LD_ERR_TIMEOUT
+ * and its peaks are unspecified.  Lets a test make a wait run out without any
+ * copy that fails to complete. */
+LD_API ld_status ld_ctx_set_wait_limit(ld_ctx *ctx, int64_t polls);
 
 /* Stage timing.  After ld_ctx_enable_timing(ctx, 1), every ld_detect_batch
  * call also records CUDA events on its stream around its launches: before

@@ -65,12 +65,27 @@ def forward(params: dict, x: np.ndarray, keep: bool = False):
     return (out.numpy(), [a.numpy() for a in acts]) if keep else out.numpy()
 
 
+def _conv3x3_relu_t(h: torch.Tensor, w: torch.Tensor, b: torch.Tensor, stride: int) -> torch.Tensor:
+    """One conv layer on NCHW: 3x3 cross-correlation, zero padding 1, the given
+    stride, + bias, ReLU; w is [Cout][3][3][Cin] (the kernels' layout)."""
+    return F.relu(F.conv2d(h, w.permute(0, 3, 1, 2), b, stride=stride, padding=1))
+
+
+def conv3x3_relu(x: np.ndarray, w: np.ndarray, b: np.ndarray, stride: int) -> np.ndarray:
+    """One conv layer of the network on NHWC input x [N][H][W][Cin] (float64):
+    y[n, i, j, co] = relu(b[co] + sum_{ky, kx, ci} w[co, ky, kx, ci] *
+    x[n, i*stride + ky - 1, j*stride + kx - 1, ci]) with x = 0 outside the input;
+    returns NHWC [N][(H-1)//stride+1][(W-1)//stride+1][Cout]."""
+    with torch.no_grad():
+        y = _conv3x3_relu_t(_t(x).permute(0, 3, 1, 2), _t(w), _t(b), stride)
+    return y.permute(0, 2, 3, 1).numpy()
+
+
 def _forward_t(P: dict, x: torch.Tensor):
     h = x[:, None, :, :]
     acts = []
     for i, (_, _, s) in enumerate(CHANNELS):
-        w = P[f"w{i}"].permute(0, 3, 1, 2)            # [Cout][3][3][Cin] -> [Cout][Cin][3][3]
-        h = F.relu(F.conv2d(h, w, P[f"b{i}"], stride=s, padding=1))
+        h = _conv3x3_relu_t(h, P[f"w{i}"], P[f"b{i}"], s)
         acts.append(h)
     g = F.adaptive_avg_pool2d(h, (POOL_H, POOL_W))    # [N, 32, 4, 8]
     feat = g.permute(0, 2, 3, 1).reshape(g.shape[0], -1)   # (bin row, bin col, channel)
@@ -84,6 +99,32 @@ def loss_and_grads(params: dict, x: np.ndarray, target: np.ndarray):
     loss = F.binary_cross_entropy_with_logits(logits, _t(target), reduction="mean")
     loss.backward()
     return float(loss.detach()), {k: v.grad.numpy() for k, v in P.items()}
+
+
+def intermediates(params: dict, x: np.ndarray, target: np.ndarray) -> dict:
+    """Every value of one forward and backward pass, for element-wise checks:
+    z[i] (layer i's pre-activation, NCHW), a[i] (its ReLU output), dy[i] (d loss
+    / d a[i]), feat, logits, dlogits (d loss / d logits), loss, and the
+    parameter gradients g[name]."""
+    P = {k: _t(v, grad=True) for k, v in params.items()}
+    h = _t(x)[:, None, :, :]
+    zs, acts = [], []
+    for i, (_, _, s) in enumerate(CHANNELS):
+        z = F.conv2d(h, P[f"w{i}"].permute(0, 3, 1, 2), P[f"b{i}"], stride=s, padding=1)
+        h = F.relu(z)
+        h.retain_grad()
+        zs.append(z)
+        acts.append(h)
+    g = F.adaptive_avg_pool2d(h, (POOL_H, POOL_W))
+    feat = g.permute(0, 2, 3, 1).reshape(g.shape[0], -1)
+    logits = feat @ P["wh"].T + P["bh"]
+    logits.retain_grad()
+    loss = F.binary_cross_entropy_with_logits(logits, _t(target), reduction="mean")
+    loss.backward()
+    return {"z": [z.detach().numpy() for z in zs], "a": [a.detach().numpy() for a in acts],
+            "dy": [a.grad.numpy() for a in acts], "feat": feat.detach().numpy(),
+            "logits": logits.detach().numpy(), "dlogits": logits.grad.numpy(), "loss": float(loss.detach()),
+            "g": {k: v.grad.numpy() for k, v in P.items()}}
 
 
 def pool_bins(n_in: int, n_out: int):

@@ -93,6 +93,7 @@ struct ld_ctx {
     // warp); pairs -1 selects the interleaved-column voting kernel
     std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     int force_pairs = 0, force_rows = 0;   // set while the autotuner times candidates
+    uint32_t wait_polls = kSpinLimit;      // consumer-side chunk waits of the voting kernels
     // (w, h, n_theta) -> rows of the interleaved-column accumulator
     mutable std::map<std::tuple<int, int, int>, int> col_rows;
     std::mutex mu;
@@ -322,6 +323,16 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
 
 }  // namespace
 
+// The parameters of a peak search on an n_theta-row accumulator, validated
+// as ld_hough_peaks validates them (NULL: the defaults).
+ld_status ld::peak_params(const ld_params *pp, int32_t n_theta, ld_params *out) {
+    ld_params p = pp ? *pp : defaults();
+    p.n_theta = (n_theta >= 2 && !(n_theta & 1)) ? n_theta : 2;   // n_theta of the table is unused here
+    const ld_status st = check_params(&p);
+    if (st == LD_OK) *out = p;
+    return st;
+}
+
 extern "C" {
 
 const char *ld_last_error(void) { return g_err.c_str(); }
@@ -345,6 +356,15 @@ ld_status ld_ctx_create(ld_ctx **out, int device) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
         c->num_sms = sms;
     *out = c;
+    return LD_OK;
+}
+
+ld_status ld_ctx_set_wait_limit(ld_ctx *ctx, int64_t polls) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_ctx_set_wait_limit: NULL ctx");
+    if (polls > (int64_t)kSpinLimit)
+        return fail(LD_ERR_INVALID, "ld_ctx_set_wait_limit: polls must be <= %u", kSpinLimit);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->wait_polls = polls < 0 ? kSpinLimit : (uint32_t)polls;
     return LD_OK;
 }
 
@@ -522,6 +542,7 @@ ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_e
     L.n = 1;
     L.n_theta = p.n_theta;
     L.mode = kHoughFullAcc;
+    L.wait_polls = ctx->wait_polls;
     L.trig = dt;
     L.queue = sm.queue;
     L.total_units = hp.n_tiles * ns;
@@ -786,6 +807,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             HL.n = gs;
             HL.n_theta = p.n_theta;
             HL.mode = kHoughCandidates;
+            HL.wait_polls = ctx->wait_polls;
             HL.cand_m = M;
             HL.min_votes = p.min_votes;
             HL.top_k = p.top_k;
@@ -1126,6 +1148,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     HL.n = n;
     HL.n_theta = p.n_theta;
     HL.mode = kHoughCandidates;
+    HL.wait_polls = ctx->wait_polls;
     HL.cand_m = M;
     HL.min_votes = p.min_votes;
     HL.top_k = p.top_k;

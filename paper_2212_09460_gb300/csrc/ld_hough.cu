@@ -76,9 +76,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true if the phase completed, false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
+// Bounded wait: true if the phase completed, false if it gave up after
+// `limit` polls (0: at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -428,7 +429,7 @@ __device__ __forceinline__ bool hough_unit(const HoughLaunch &L, const HoughFram
         const uint32_t g = seq + (uint32_t)c;
         const int st = (int)(g % kStages);
         const uint32_t par = (g / kStages) & 1u;
-        const bool ok = mbar_wait_bounded(&bars[st], par);
+        const bool ok = mbar_wait_bounded(&bars[st], par, L.wait_polls);
         if (!ok) abort_flag = 1;
         if (ok) {
             const uint32_t *buf = ring + st * kChunkEdges;
@@ -604,9 +605,11 @@ __device__ __forceinline__ int32_t window_min(int32_t c, int32_t s, int W, int H
     const int64_t ym = s < 0 ? (int64_t)(H - 1) * s : 0;
     return floor_q16(xm + ym + 32768);
 }
-// The same, also giving up once *abort is set (by another warp that gave up).
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// A bounded wait (`limit` polls) that also gives up once *abort is set (by
+// another warp that gave up).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort,
+                                                   uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u && *abort) return false;
     }
@@ -721,7 +724,8 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         const uint32_t g = seq + (uint32_t)c;
         const int st = (int)(g % kColStages);
         uint32_t ok = 1u;
-        if (lane == 0) ok = mbar_wait_or_abort(&R.bars[st], (g / kColStages) & 1u, &abort_flag) ? 1u : 0u;
+        if (lane == 0)
+            ok = mbar_wait_or_abort(&R.bars[st], (g / kColStages) & 1u, &abort_flag, L.wait_polls) ? 1u : 0u;
         ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
         __syncwarp();   // lane 0's wait orders the chunk's bytes for the whole warp
         if (!ok) {

@@ -108,7 +108,8 @@ struct HoughLaunch {
     int32_t top_k, nms_theta, nms_rho;   // candidate mode: the merge
     int32_t col_chunk;     // interleaved-column kernel: edges per streamed chunk
     int32_t part_stride;   // interleaved-column kernel: words per partial accumulator
-    int32_t pad_;
+    uint32_t wait_polls;   // a consumer-side wait for an edge chunk gives up after this
+                           // many polls (kSpinLimit normally; 0 gives up at once)
     uint32_t *part;        // interleaved-column kernel: partial accumulators of split tiles
     int32_t *tile_cnt;     // interleaved-column kernel: finished pieces per split tile (zeroed)
     int32_t *queue;        // work-queue head (zeroed before the launch)
@@ -231,6 +232,11 @@ cudaError_t launch_select_bands_cols(const float *logits, int n, int n_theta, fl
 
 // Set the calling thread's ld_last_error() message.
 void set_last_error(const char *msg);
+
+// Parameters of a peak search on an accumulator with n_theta rows: *pp (or the
+// defaults when pp is NULL) checked as ld_hough_peaks checks them; LD_OK and
+// *out filled, or an error with ld_last_error() set.
+ld_status peak_params(const ld_params *pp, int32_t n_theta, ld_params *out);
 
 // One-time per-device setup of a kernel (function attributes): `done` holds
 // one bit per device 0..63, set after `setup(device)` succeeded; later calls

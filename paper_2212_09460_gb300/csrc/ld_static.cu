@@ -11,9 +11,12 @@
 // __device__ array of fixed size that is part of the loaded library.
 //
 // The array holds kStaticCandKeys 8-byte keys (1 MiB) on every GPU that loads
-// the library, for the life of the process.  Every call on a device shares it
-// and it keeps the last call's contents; the kernels write every slot they
-// later read, so nothing has to be cleared between calls.  Two calls whose
+// the library, for the life of the process.  Its device address is looked up
+// once per device and kept, so the entry point must not be used on a device
+// after cudaDeviceReset (or any other teardown of its primary context) in the
+// same process: the kept address would then be stale.  Every call on a device
+// shares the array and it keeps the last call's contents; the kernels write
+// every slot they later read, so nothing has to be cleared between calls.  Two calls whose
 // work overlaps on the GPU (different streams, or different host threads)
 // race on the array: serialise them.
 #include <cstdio>
@@ -54,24 +57,21 @@ cudaError_t static_cand(int dev, uint64_t **out) {
 using namespace ld;
 
 extern "C" ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta, int32_t n_rho,
-                                          const ld_params *p, ld_peak *d_peaks, int32_t *d_n_peaks,
+                                          const ld_params *pp, ld_peak *d_peaks, int32_t *d_n_peaks,
                                           void *stream) {
     char msg[256];
-    if (!p || !d_acc || !d_peaks || !d_n_peaks) {
-        set_last_error("ld_hough_peaks_static: NULL argument");
+    ld_params q;
+    const ld_status st = peak_params(pp, n_theta, &q);   // NULL: the defaults, as ld_hough_peaks
+    if (st != LD_OK) return st;
+    const ld_params *p = &q;
+    if (!d_acc || !d_peaks || !d_n_peaks) {
+        set_last_error("ld_hough_peaks_static: NULL buffer");
         return LD_ERR_INVALID;
     }
     if (n_theta < 1 || n_theta > kMaxTheta || n_rho < 1 || n_rho > 65535) {
         snprintf(msg, sizeof msg, "ld_hough_peaks_static: accumulator %d x %d: need 1 <= n_theta <= %d, "
                                   "1 <= n_rho <= 65535", n_theta, n_rho, kMaxTheta);
         set_last_error(msg);
-        return LD_ERR_INVALID;
-    }
-    if (p->top_k < 1 || p->top_k > kMaxTopK || p->nms_theta < 1 || !(p->nms_theta & 1) || p->nms_rho < 1 ||
-        !(p->nms_rho & 1) || p->nms_theta > 255 || p->nms_rho > 255 ||
-        (int64_t)p->nms_theta * p->nms_rho * (p->top_k - 1) + 1 > 4096) {
-        set_last_error("ld_hough_peaks_static: need 1 <= top_k <= 16, odd nms sizes <= 255 and "
-                       "nms_theta*nms_rho*(top_k-1)+1 <= 4096");
         return LD_ERR_INVALID;
     }
     const int M = p->nms_theta * p->nms_rho * (p->top_k - 1) + 1;

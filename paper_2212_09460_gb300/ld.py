@@ -82,6 +82,7 @@ _SIGS = {
     "ld_hough_peaks": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
                         _P],
+    "ld_ctx_set_wait_limit": [_P, ctypes.c_int64],
     "ld_hough_peaks_static": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_autotune": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.c_int32, _P],
     "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
@@ -204,8 +205,9 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
 
 
 def ld_hough_peaks_static(d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) -> None:
-    """ld_hough_peaks without a context and without any device allocation."""
-    _check(load().ld_hough_peaks_static(d_acc, n_theta, n_rho, ctypes.byref(p), d_peaks, d_n_peaks, stream))
+    """ld_hough_peaks without a context and without any device allocation (p None: the defaults)."""
+    _check(load().ld_hough_peaks_static(d_acc, n_theta, n_rho, None if p is None else ctypes.byref(p), d_peaks,
+                                        d_n_peaks, stream))
 
 
 def _frames_array(frames):
@@ -224,6 +226,11 @@ def ld_ctx_plan(ctx, w, h, p) -> tuple[int, int]:
     pairs, rows = ctypes.c_int32(), ctypes.c_int32()
     _check(load().ld_ctx_plan(ctx, w, h, ctypes.byref(p), ctypes.byref(pairs), ctypes.byref(rows)))
     return pairs.value, rows.value
+
+
+def ld_ctx_set_wait_limit(ctx: int, polls: int) -> None:
+    """Voting kernels' edge-chunk waits give up after `polls` polls (0: at once, < 0: the default)."""
+    _check(load().ld_ctx_set_wait_limit(ctx, polls))
 
 
 def ld_ctx_enable_timing(ctx: int, enable: bool) -> None:
@@ -396,6 +403,9 @@ class Context:
         if img.dtype != torch.uint8 or img.dim() != 2 or not img.is_cuda or img.stride(1) != 1:
             raise ValueError("image must be a 2-D uint8 CUDA tensor with unit column stride")
         return img.data_ptr(), img.shape[1], img.shape[0], img.stride(0)
+
+    def set_wait_limit(self, polls: int) -> None:
+        ld_ctx_set_wait_limit(self.handle, polls)
 
     def reserve(self, max_pixels: int, max_frames: int, max_acc_cells: int, p: ld_params) -> None:
         ld_ctx_reserve(self.handle, max_pixels, max_frames, max_acc_cells, p)

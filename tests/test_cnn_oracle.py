@@ -110,3 +110,58 @@ def test_band_targets():
     # a horizontal line y = 500 (theta 90 deg, rho 500) only in band 500*8//1080 = 3
     r = cnn.row_band_targets(np.array([[180, 500 + D, 1]]), 1920, 1080, 360)
     assert list(np.nonzero(r)[0]) == [3]
+
+
+def _golden_row_bands():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "row_bands.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            w, h, th, rho, bands = line.split()
+            rows.append((int(w), int(h), int(th), int(rho), [int(b) for b in bands.split(",")]))
+    return rows
+
+
+@pytest.mark.parametrize("case", _golden_row_bands(), ids=lambda c: f"theta{c[2]}_rho{c[3]}")
+def test_row_band_targets_oblique_lines(case):
+    # hand-derived bands of oblique lines (tests/golden/row_bands.txt): a sign
+    # or index slip in the cos != 0 branch changes the band set
+    w, h, th, rho, bands = case
+    D = int(np.ceil(np.hypot(w, h)))
+    t = cnn.row_band_targets(np.array([[th, rho + D, 1]]), w, h, 360)
+    assert list(np.nonzero(t)[0]) == bands
+
+
+def _conv_bruteforce(x, w, b, stride):
+    # y[n,i,j,co] = relu(b[co] + sum w[co,ky,kx,ci] x[n, i*s+ky-1, j*s+kx-1, ci]), zero outside
+    n, h, wd, ci = x.shape
+    co = w.shape[0]
+    oh, ow = (h - 1) // stride + 1, (wd - 1) // stride + 1
+    y = np.zeros((n, oh, ow, co))
+    for a in range(n):
+        for i in range(oh):
+            for j in range(ow):
+                for o in range(co):
+                    acc = b[o]
+                    for ky in range(3):
+                        for kx in range(3):
+                            yy, xx = i * stride + ky - 1, j * stride + kx - 1
+                            if 0 <= yy < h and 0 <= xx < wd:
+                                for c in range(ci):
+                                    acc += w[o, ky, kx, c] * x[a, yy, xx, c]
+                    y[a, i, j, o] = max(acc, 0.0)
+    return y
+
+
+@pytest.mark.parametrize("cin,cout,stride,h,w", [(1, 4, 1, 5, 6), (3, 2, 2, 7, 5), (2, 3, 2, 6, 8), (4, 2, 1, 4, 3)])
+def test_conv3x3_relu_bruteforce(cin, cout, stride, h, w):
+    # the single-layer definition against plain loops (tap order, padding,
+    # stride, weight layout [Cout][3][3][Cin], bias, ReLU)
+    rng = np.random.default_rng(cin * 31 + stride)
+    x = rng.standard_normal((2, h, w, cin))
+    wt = rng.standard_normal((cout, 3, 3, cin))
+    b = rng.standard_normal(cout) * 0.3
+    np.testing.assert_allclose(cnn.conv3x3_relu(x, wt, b, stride), _conv_bruteforce(x, wt, b, stride),
+                               rtol=1e-12, atol=1e-12)

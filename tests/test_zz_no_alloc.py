@@ -22,9 +22,9 @@ from paper_2212_09460_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _static_peaks(ld, acc_dev, p):
+def _static_peaks(ld, acc_dev, p, top_k=None):
     n_theta, n_rho = acc_dev.shape
-    peaks = torch.full((p.top_k, 3), -7, dtype=torch.int32, device=acc_dev.device)
+    peaks = torch.full((p.top_k if p is not None else top_k, 3), -7, dtype=torch.int32, device=acc_dev.device)
     n = torch.full((1,), -7, dtype=torch.int32, device=acc_dev.device)
     ld.ld_hough_peaks_static(acc_dev.data_ptr(), n_theta, n_rho, p, peaks.data_ptr(), n.data_ptr(),
                              torch.cuda.current_stream().cuda_stream)
@@ -48,15 +48,40 @@ def _accumulators(ora):
 
 
 def test_static_peaks_match_context_peaks_twice(ctx, ldlib, ora):
+    # both entry points, and the oracle's greedy (Sec. 2.3 "Hough Peak"), agree
     real, ties = _accumulators(ora)
     for acc, kw in ((real, dict(top_k=4)), (ties, dict(top_k=16, nms_theta=3, nms_rho=7, min_votes=2))):
         p = ldlib.params(**kw)
         acc_dev = torch.from_numpy(acc).cuda()
         ref = _ctx_peaks(ctx, acc_dev, p)
+        np.testing.assert_array_equal(ref, ora.peaks(acc, p.top_k, p.nms_theta, p.nms_rho, p.min_votes))
         first = _static_peaks(ldlib, acc_dev, p)
         second = _static_peaks(ldlib, acc_dev, p)
         np.testing.assert_array_equal(first, ref)
         np.testing.assert_array_equal(second, ref)
+
+
+def test_static_peaks_null_params_are_the_defaults(ctx, ldlib, ora):
+    # p = NULL means the defaults (top_k 4, 5 x 5, min_votes 1), as for ld_hough_peaks
+    real, _ = _accumulators(ora)
+    acc_dev = torch.from_numpy(real).cuda()
+    got = _static_peaks(ldlib, acc_dev, None, top_k=4)
+    np.testing.assert_array_equal(got, ora.peaks(real, 4, 5, 5, 1))
+    np.testing.assert_array_equal(got, _ctx_peaks(ctx, acc_dev, ldlib.params()))
+
+
+def test_static_peaks_rejects_reserved_field(ldlib):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    p = ldlib.params()
+    p.reserved = 1
+    dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
+    peaks = torch.zeros((4, 3), dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ldlib.LdError) as ei:
+        ldlib.ld_hough_peaks_static(dummy.data_ptr(), 4, 4, p, peaks.data_ptr(), n.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert ei.value.status == ldlib.LD_ERR_INVALID
 
 
 def test_static_peaks_alternating_inputs(ctx, ldlib, ora):
