@@ -3,15 +3,17 @@
 // (Sec. 2.2, Sec. 4.2), and compaction of the 255 pixels into the packed
 // (y << 16) | x edge list the voting stage reads (Sec. 4.3).
 //
-// Arithmetic.  With T, M, B the rows above, at and below the pixel,
-// P = M + B, Q = T + M and R = B - T (per column), the Sobel components are
-// gx = (P+Q)(x+1) - (P+Q)(x-1) and gy = R(x-1) + 2R(x) + R(x+1), and
-//   gx + gy = 2 [P(x+1) - Q(x-1) + R(x)] = 2u,
-//   gy - gx = 2 [P(x-1) - Q(x+1) + R(x)] = 2w,
+// Arithmetic.  With T, M, B the rows above, at and below the pixel, let
+// P = M + B and Q = T + M per column, and SP(x) = P(x) + P(x+1), SQ(x) =
+// Q(x) + Q(x+1) their horizontal pair sums.  The Sobel components are
+// gx = (P+Q)(x+1) - (P+Q)(x-1) and gy = (B-T)(x-1) + 2(B-T)(x) + (B-T)(x+1),
+// and with B - T = P - Q:
+//   gx + gy = 2 [SP(x) - SQ(x-1)] = 2u,
+//   gy - gx = 2 [SP(x-1) - SQ(x)] = 2w,
 // so |Gx| + |Gy| = max(|gx + gy|, |gx - gy|) = 2 max(|u|, |w|), and for a
 // threshold T in [1, 255] the saturated magnitude min(|Gx|+|Gy|, 255) >= T
-// exactly when max(|u|, |w|) >= ceil(T/2).  Q of a row is P of the row above
-// and R = P - Q, so a row costs one P, one R, u and w.
+// exactly when max(|u|, |w|) >= ceil(T/2).  Q of a row is P of the row above,
+// so SQ is the previous row's SP: a row costs one P, one SP, u and w.
 //
 // Every quantity is an integer of magnitude < 2048, computed exactly in
 // fp16x2 in units of 2^-24: the fp16 numbers k * 2^-24 for |k| < 2048 are
@@ -29,17 +31,25 @@
 // contiguous bytes per row (16-byte copies, fully coalesced) and produces the
 // middle 480 pixels: lanes 0 and 31 only supply the left and right halo.  A
 // warp slides down a run of 8*G rows, prefetching 6 rows ahead into shared
-// memory (cp.async);
-// every 8 rows it takes one atomic on the frame's edge counter for the
-// warp's edges (a warp prefix sum gives each lane its slots) and writes them.
-// Zero padding is virtual: loads outside the image read 0.
+// memory (cp.async).  Zero padding is virtual: loads outside the image read 0.
+//
+// Compaction.  Every 8 rows a lane holds its edge flags as four 32-bit words
+// (bits 0-15: pixels 0-15 of rows 2k, bits 16-31: of rows 2k+1).  Edges
+// cluster (the 3x3 ring around a salt pixel, the sides of a lane stripe), so a
+// lane that extracted its own pixels' edges would leave the rest of the warp
+// waiting.  Instead each 32 x 32 bit matrix of a word across the warp is
+// transposed with five shuffle-xor steps: lane l then holds pixel l % 16 of
+// rows 2k + l / 16 of all 32 lanes' segments, which spreads every cluster over
+// several lanes.  A warp prefix sum and one atomic on the frame's counter give
+// each lane its slots; the lanes write their edges into per-warp staging slots
+// that the warp copies out with coalesced stores.
 #include "ld_internal.cuh"
 
 namespace ld {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
-constexpr int kStage = 1024;   // edge staging slots per warp (8-row group)
+constexpr int kStage = 1024;   // edge staging slots per warp (one 8-row group)
 
 __device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b) {
     uint32_t d;
@@ -69,8 +79,9 @@ __device__ __forceinline__ uint32_t h2_edge_acc(uint32_t u, uint32_t w, uint32_t
 // cp.async.wait_group, so no barrier is needed.
 constexpr int kRing = 8;       // row slots per warp
 constexpr int kAhead = 6;      // rows in flight ahead of the one being used
-// dynamic shared memory: the row rings and the edge staging slots (64 KB)
+// dynamic shared memory: the row rings and the staging slots (64 KB)
 constexpr int kSobelSmem = kSobelWarps * (kRing * 512 + kStage * 4);
+static_assert(kAhead <= kRing - 2, "a fetch must not overwrite a row still to be read");
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int nbytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
@@ -79,21 +90,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Start the copy of this lane's 16 bytes of row y into its slot (nb bytes
-// of the row from column x, the rest zero-filled; nb = 0 outside the image
-// or the run) and close the copy group: one group per row, possibly empty.
-__device__ __forceinline__ void fetch_row(const uint8_t *img, int pitch, int h, int x, int nb_lane, int y,
-                                          bool want, uint32_t slot) {
-    const bool ok = want && (unsigned)y < (unsigned)h && nb_lane > 0;
-    const uint8_t *src = ok ? img + (size_t)y * pitch + x : img;
-    cp_async16(slot, src, ok ? nb_lane : 0);
-    cp_async_commit();
-}
-
 __device__ __forceinline__ uint4 lds128(uint32_t a) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
+}
+
+// Position of the highest set bit of m (m != 0).
+__device__ __forceinline__ uint32_t bfind32(uint32_t m) {
+    uint32_t d;
+    asm("bfind.u32 %0, %1;" : "=r"(d) : "r"(m));
+    return d;
 }
 
 // 16 bytes -> 8 half pairs (p_j, p_{j+8}) in units of 2^-24.
@@ -112,13 +119,12 @@ __device__ __forceinline__ void to_halves(const uint4 q, uint32_t (&Bb)[8]) {
     Bb[7] = __byte_perm(t3, 0u, 0x4342);
 }
 
-// Sliding state of a lane: row y (Mb) as halves, and Q = P of row y-1
-// (T + M) with its two end words shifted in from the adjacent lanes:
-// Qm0 = Q at (x-1) for word 0, Qp7 = Q at (x+1) for word 7.  The top row
-// itself is not needed: R = B - T = P - Q.
+// Sliding state of a lane: the centre row M as halves, and SQ = SP of the
+// previous output row, with SQm0 = SQ at (x-1) for word 0 (shifted in from
+// the previous lane).
 struct Window {
-    uint32_t Mb[8], Q[8];
-    uint32_t Qm0, Qp7;
+    uint32_t M[8], SQ[8];
+    uint32_t SQm0;
 };
 
 // Advance the window by one row (the new bottom row q) and, if EMIT, return
@@ -126,33 +132,31 @@ struct Window {
 // an edge.  All 32 lanes of the warp must call this (shuffles).
 template <bool EMIT>
 __device__ __forceinline__ uint32_t step(Window &S, const uint4 q, uint32_t tau) {
-    uint32_t Bb[8], P[8];
-    to_halves(q, Bb);
+    uint32_t B[8], P[8], SP[8];
+    to_halves(q, B);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) P[j] = h2_add(S.Mb[j], Bb[j]);   // M + B
+    for (int j = 0; j < 8; ++j) P[j] = h2_add(S.M[j], B[j]);   // M + B
     const uint32_t nx = __shfl_down_sync(kFull, P[0], 1);   // next lane's pixels (16, 24)
-    const uint32_t pv = __shfl_up_sync(kFull, P[7], 1);     // previous lane's pixels (-9, -1)
     const uint32_t Pp7 = __byte_perm(P[0], nx, 0x5432);     // P at (8, 16): x+1 of word 7
-    const uint32_t Pm0 = __byte_perm(P[7], pv, 0x1076);     // P at (-1, 7): x-1 of word 0
+#pragma unroll
+    for (int j = 0; j < 8; ++j) SP[j] = h2_add(P[j], j < 7 ? P[j + 1] : Pp7);
+    const uint32_t pv = __shfl_up_sync(kFull, SP[7], 1);    // previous lane's SP at (-9, -1)
+    const uint32_t SPm0 = __byte_perm(SP[7], pv, 0x1076);   // SP at (-1, 7): x-1 of word 0
     uint32_t acc = 0;
     if (EMIT) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const uint32_t R = h2_sub(P[j], S.Q[j]);   // B - T, exact
-            const uint32_t Pp = j < 7 ? P[j + 1] : Pp7, Pm = j > 0 ? P[j - 1] : Pm0;
-            const uint32_t Qp = j < 7 ? S.Q[j + 1] : S.Qp7, Qm = j > 0 ? S.Q[j - 1] : S.Qm0;
-            const uint32_t u = h2_add(h2_sub(Pp, Qm), R);
-            const uint32_t w = h2_add(h2_sub(Pm, Qp), R);
+            const uint32_t u = h2_sub(SP[j], j > 0 ? S.SQ[j - 1] : S.SQm0);   // SP(x) - SQ(x-1)
+            const uint32_t w = h2_sub(j > 0 ? SP[j - 1] : SPm0, S.SQ[j]);     // SP(x-1) - SQ(x)
             acc = h2_edge_acc(u, w, tau, 0x00010001u << j, acc);   // + 2^j units per edge
         }
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        S.Mb[j] = Bb[j];
-        S.Q[j] = P[j];
+        S.M[j] = B[j];
+        S.SQ[j] = SP[j];
     }
-    S.Qm0 = Pm0;
-    S.Qp7 = Pp7;
+    S.SQm0 = SPm0;
     return __byte_perm(acc, 0u, 0x4420);   // bits 0-7: pixels 0-7, bits 8-15: pixels 8-15
 }
 
@@ -202,49 +206,53 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
     const uint32_t tau_u = (uint32_t)(L.threshold + 1) >> 1;   // ceil(T / 2), T in [1, 255]
     const uint32_t tau = tau_u | (tau_u << 16);                  // in units of 2^-24
 
-    // this lane's row slots: ring_s[warp][k % kRing][lane * 16]; relative
-    // row k is image row y0 - 1 + k, output row y0 + r needs k = r .. r + 2,
-    // and the run needs k = 0 .. n_k - 1
+    // this lane's row slots ring_s[warp][k % kRing][lane * 16]: relative row k
+    // is image row y0 - 1 + k; output row y0 + 8g + r needs k = 8g + r .. + 2
     extern __shared__ __align__(16) uint8_t smem_dyn[];
     uint8_t(*ring_s)[kRing][512] = reinterpret_cast<uint8_t(*)[kRing][512]>(smem_dyn);
-    uint32_t(*stage_s)[kStage] = reinterpret_cast<uint32_t(*)[kStage]>(smem_dyn + kSobelWarps * kRing * 512);
+    uint32_t *const stage = reinterpret_cast<uint32_t *>(smem_dyn + kSobelWarps * kRing * 512) + warp * kStage;
     const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(&ring_s[warp][0][lane * 16]);
-    const int n_k = y_last - y0 + 2;
+    // the next row to fetch is image row yf, at pf; rows up to y_last (the last
+    // output row's lower neighbour) that lie inside the image are read, the rest
+    // of the slot (and rows outside the image) is zero-filled
+    const unsigned y_lim = (unsigned)min(h, y_last + 1);
+    int yf = y0 - 1;
+    const uint8_t *pf = img + (nb_lane > 0 ? xl : 0) + (ptrdiff_t)(y0 - 1) * pitch;
+    auto fetch = [&](int slot) {
+        const int nb = ((unsigned)yf < y_lim) ? nb_lane : 0;
+        cp_async16(slot0 + (uint32_t)slot * 512u, nb ? pf : img, nb);
+        cp_async_commit();   // one group per row, possibly empty
+        ++yf;
+        pf += pitch;
+    };
 #pragma unroll
-    for (int k = 0; k < kAhead; ++k)
-        fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + k, k < n_k, slot0 + (uint32_t)(k % kRing) * 512u);
+    for (int k = 0; k < kAhead; ++k) fetch(k);
 
-    // window primed with rows y0-1 and y0 (the first step only builds P)
+    // window primed with rows y0-1 and y0 (the first step only builds SP)
     Window S;
-    {
-        cp_async_wait<kAhead - 1>();
-        to_halves(lds128(slot0), S.Mb);
+    cp_async_wait<kAhead - 1>();
+    to_halves(lds128(slot0), S.M);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) S.Q[j] = 0u;
-        S.Qm0 = S.Qp7 = 0u;
-        fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + kAhead, kAhead < n_k,
-                  slot0 + (uint32_t)(kAhead % kRing) * 512u);
-        cp_async_wait<kAhead - 1>();
-        const uint4 q1 = lds128(slot0 + 512u);
-        fetch_row(img, pitch, h, xl, nb_lane, y0 + kAhead, kAhead + 1 < n_k,
-                  slot0 + (uint32_t)((kAhead + 1) % kRing) * 512u);
-        step<false>(S, q1, tau);
-    }
+    for (int j = 0; j < 8; ++j) S.SQ[j] = 0u;
+    S.SQm0 = 0u;
+    fetch(kAhead % kRing);
+    cp_async_wait<kAhead - 1>();
+    step<false>(S, lds128(slot0 + 512u), tau);
+    fetch((kAhead + 1) % kRing);
 
     for (int yg = y0; yg < y_last; yg += 8) {   // warp-uniform
+        const int nr = y_last - yg;              // output rows in this group (1..8)
         uint32_t m2[4];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int y = yg + r;
-            const int k = y - y0 + 2;             // bottom row of output row y
             cp_async_wait<kAhead - 1>();
-            const uint4 q = lds128(slot0 + (uint32_t)(k % kRing) * 512u);
-            const int kn = k + kAhead;            // next row to fetch
-            fetch_row(img, pitch, h, xl, nb_lane, y0 - 1 + kn, kn < n_k, slot0 + (uint32_t)(kn % kRing) * 512u);
+            const uint4 q = lds128(slot0 + (uint32_t)((r + 2) % kRing) * 512u);   // bottom row of y
+            fetch((r + 2 + kAhead) % kRing);
             uint32_t mk = step<true>(S, q, tau) & colmask;
-            if (y >= y_last || (clear && (y == 0 || y == h - 1))) mk = 0;
-            if (r & 1) m2[r >> 1] |= mk << 16; else m2[r >> 1] = mk;
-            if (BIN && y < y_last && lane >= 1 && lane <= 30 && xl < pitch) {
+            if (r >= nr || (clear && (y == 0 || y == h - 1))) mk = 0;
+            if (r & 1) m2[r >> 1] = __byte_perm(m2[r >> 1], mk, 0x5410); else m2[r >> 1] = mk;
+            if (BIN && r < nr && lane >= 1 && lane <= 30 && xl < pitch) {
                 uint4 o;
                 o.x = spread4(mk & 0xF);
                 o.y = spread4((mk >> 4) & 0xF);
@@ -269,8 +277,26 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
             if (bx + 1 < pw) row[bx + 1] = (uint8_t)c1;
         }
 
-        // the group's edges: warp prefix sum, one atomic, then each lane's own
-        const int cnt = __popc(m2[0]) + __popc(m2[1]) + __popc(m2[2]) + __popc(m2[3]);
+        // transpose the four 32 x 32 bit matrices (word k of every lane): lane l
+        // ends with bit l of each lane's word, i.e. bit s of T[k] is pixel
+        // x0 + 16 s + l % 16 of row yg + 2k + l / 16, x0 = the strip's first column
+        uint32_t T[4] = {m2[0], m2[1], m2[2], m2[3]};
+#pragma unroll
+        for (int j = 16; j >= 1; j >>= 1) {
+            const uint32_t mlo = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                                 : j == 2 ? 0x33333333u : 0x55555555u;   // bit positions b with b & j == 0
+            const bool up = (lane & j) == 0;
+            const uint32_t keep = up ? mlo : ~mlo;
+            const uint32_t rot = up ? (uint32_t)j : (uint32_t)(32 - j);   // rotate left by j / right by j
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t y = __shfl_xor_sync(kFull, T[k], j);
+                T[k] = (T[k] & keep) | (__funnelshift_l(y, y, rot) & ~keep);
+            }
+        }
+
+        // the group's edges: warp prefix sum, one atomic on the frame's counter
+        const int cnt = __popc(T[0]) + __popc(T[1]) + __popc(T[2]) + __popc(T[3]);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -282,49 +308,33 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
         int base = 0;
         if (lane == 31) base = atomicAdd(F.count, tot);
         base = __shfl_sync(kFull, base, 31);
-        const int64_t pos0 = (int64_t)base + (incl - cnt);
-        if (tot <= kStage && (int64_t)base + tot <= F.cap) {
-            // each lane writes its edges to the warp's staging slots, then the
-            // warp copies them out with coalesced stores
-            uint32_t *st = &stage_s[warp][incl - cnt];
+        const uint32_t b0 = ((uint32_t)(yg + (lane >> 4)) << 16) + (uint32_t)(sx * kSobelStripW - 16 + (lane & 15));
+        if (tot <= kStage && (int64_t)base + tot <= F.cap) {   // warp-uniform
+            uint32_t *st = stage + (incl - cnt);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                uint32_t m = m2[k];
-                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
+                uint32_t m = T[k];
+                const uint32_t bk = b0 + ((uint32_t)(2 * k) << 16);
                 while (m) {
-                    const int i = 31 - __clz(m);
-                    m ^= 1u << i;
-                    // bit i < 16: pixel i of row yg+2k; i >= 16: pixel i-16 of the next row
-                    *st++ = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
+                    const uint32_t sb = bfind32(m);
+                    m &= ~(1u << sb);
+                    *st++ = bk + 16u * sb;
                 }
             }
             __syncwarp();
             uint32_t *dst = F.edges + base;
-            for (int i = lane; i < tot; i += 32) dst[i] = stage_s[warp][i];
+            for (int i = lane; i < tot; i += 32) dst[i] = stage[i];
             __syncwarp();
-        } else if ((int64_t)base + tot <= F.cap) {   // warp-uniform: every slot fits
-            uint32_t *dst = F.edges + pos0;
+        } else {   // a group denser than the staging slots, or a list that overflows
+            int64_t pos = (int64_t)base + (incl - cnt);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                uint32_t m = m2[k];
-                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
+                uint32_t m = T[k];
+                const uint32_t bk = b0 + ((uint32_t)(2 * k) << 16);
                 while (m) {
-                    const int i = 31 - __clz(m);
-                    m ^= 1u << i;
-                    // bit i < 16: pixel i of row yg+2k; i >= 16: pixel i-16 of the next row
-                    *dst++ = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
-                }
-            }
-        } else {                                // overflow: write what fits, count all
-            int64_t pos = pos0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t m = m2[k];
-                const uint32_t v0 = ((uint32_t)(yg + 2 * k) << 16) + (uint32_t)xl;
-                while (m) {
-                    const int i = 31 - __clz(m);
-                    m ^= 1u << i;
-                    if (pos < F.cap) F.edges[pos] = v0 + (uint32_t)i + (uint32_t)(i & 16) * 4095u;
+                    const uint32_t sb = bfind32(m);
+                    m &= ~(1u << sb);
+                    if (pos < F.cap) F.edges[pos] = bk + 16u * sb;
                     ++pos;
                 }
             }
