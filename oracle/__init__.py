@@ -65,6 +65,8 @@ def _load():
         lib.ldo_detect.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, i32,
                                    i32, i32, P, P, P, P, P]
         lib.ldo_detect.restype = i32
+        lib.ldo_hough_lines.argtypes = [P, i64, i32, i32, i32, P, i32, i32, i32, i32, P, P, P]
+        lib.ldo_hough_lines.restype = None
         _lib = lib
         return lib
 
@@ -162,3 +164,23 @@ def detect(img: np.ndarray, n_theta: int, top_k: int, threshold: int = 128,
                            int(min_votes), _ptr(mag), _ptr(binimg), _ptr(edges),
                            _ptr(acc), _ptr(out))
     return out[:n].copy()
+
+
+def hough_lines(edges: np.ndarray, w: int, h: int, n_theta: int, peaks: np.ndarray,
+                fill_gap: int = 20, min_length: int = 40, max_segments: int = 16):
+    """Segments behind each peak (the paper's Step 4 "Hough lines" without the
+    drawing): returns (segments, counts, support) with segments int32
+    [n_peaks][max_segments][6] rows (x1, y1, x2, y2, theta_idx, rho_idx) (rows
+    past counts[p] are zero), counts [n_peaks] kept segments per peak, support
+    [n_peaks] supporting pixels per peak."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    peaks = np.ascontiguousarray(np.asarray(peaks, dtype=np.int32).reshape(-1, 3))
+    n_p = peaks.shape[0]
+    segs = np.zeros((max(n_p, 1), max(max_segments, 1), 6), np.int32)
+    counts = np.zeros(max(n_p, 1), np.int32)
+    support = np.zeros(max(n_p, 1), np.int32)
+    _load().ldo_hough_lines(_ptr(edges) if edges.size else None, edges.size, int(w), int(h),
+                            int(n_theta), _ptr(peaks) if n_p else None, n_p, int(fill_gap),
+                            int(min_length), int(max_segments), _ptr(segs), _ptr(counts),
+                            _ptr(support))
+    return segs[:n_p], counts[:n_p], support[:n_p]

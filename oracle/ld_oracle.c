@@ -239,3 +239,89 @@ int ldo_detect(const uint8_t *img, int w, int h, int pitch, int border,
     return ldo_peaks(acc, n_theta, 2 * D + 1, top_k, nms_theta, nms_rho,
                      min_votes, peaks);
 }
+
+/* Sort key of a supporting pixel: along x (then y) for a line closer to
+ * horizontal than to vertical, along y (then x) otherwise. */
+typedef struct { int x, y; } ldo_pt;
+static int g_lines_by_x;
+static int cmp_pt(const void *pa, const void *pb)
+{
+    const ldo_pt *a = (const ldo_pt *)pa, *b = (const ldo_pt *)pb;
+    int a1 = g_lines_by_x ? a->x : a->y, b1 = g_lines_by_x ? b->x : b->y;
+    int a2 = g_lines_by_x ? a->y : a->x, b2 = g_lines_by_x ? b->y : b->x;
+    if (a1 != b1) return a1 < b1 ? -1 : 1;
+    if (a2 != b2) return a2 < b2 ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Hough lines: the line segments behind each peak (Step 4 of Sec. 1 without
+ * the drawing; the paper hands the peaks to MATLAB's "Hough lines", Sec. 5,
+ * Fig. 12, and states no parameters).  For peak p = (theta_idx k, rho_idx r):
+ *   - its supporting pixels are the edges whose Q16 rho at theta_k (the vote's
+ *     own rounding, Eq. 3 with Eqs. 4-5) equals r - D, so their number is the
+ *     peak's vote count;
+ *   - they are ordered along the line: by x (then y) when |c_k| <= |s_k| (the
+ *     line is at most 45 degrees from horizontal), else by y (then x);
+ *   - consecutive pixels more than fill_gap apart (squared Euclidean distance
+ *     > fill_gap^2) start a new segment;
+ *   - a segment is kept when its first and last pixel are at least min_length
+ *     apart (squared distance >= min_length^2).
+ * segs receives, per peak, up to max_segments kept segments in line order as
+ * (x1, y1, x2, y2, theta_idx, rho_idx) with (x1, y1) the first pixel:
+ * segs[(p * max_segments + i) * 6 + field].  counts[p] = the number of kept
+ * segments (may exceed max_segments; only max_segments are written),
+ * support[p] = the number of supporting pixels.
+ */
+void ldo_hough_lines(const uint32_t *edges, int64_t n_edges, int w, int h,
+                     int n_theta, const int32_t *peaks, int n_peaks,
+                     int fill_gap, int min_length, int max_segments,
+                     int32_t *segs, int32_t *counts, int32_t *support)
+{
+    int D = ldo_rho_max(w, h);
+    int32_t *c = (int32_t *)malloc(sizeof(int32_t) * n_theta);
+    int32_t *s = (int32_t *)malloc(sizeof(int32_t) * n_theta);
+    ldo_trig_q16(n_theta, c, s);
+    ldo_pt *pts = (ldo_pt *)malloc(sizeof(ldo_pt) * (size_t)(n_edges > 0 ? n_edges : 1));
+    int64_t gap2 = (int64_t)fill_gap * fill_gap, len2 = (int64_t)min_length * min_length;
+    for (int p = 0; p < n_peaks; p++) {
+        int k = peaks[3 * p + 0], r = peaks[3 * p + 1];
+        int64_t n = 0;
+        for (int64_t e = 0; e < n_edges; e++) {
+            int64_t x = edges[e] & 0xFFFF, y = edges[e] >> 16;
+            int64_t rho = floor_div(x * c[k] + y * s[k] + 32768, 65536);
+            if (rho == (int64_t)r - D) {
+                pts[n].x = (int)x;
+                pts[n].y = (int)y;
+                n++;
+            }
+        }
+        support[p] = (int32_t)n;
+        g_lines_by_x = abs(c[k]) <= abs(s[k]);
+        qsort(pts, (size_t)n, sizeof(ldo_pt), cmp_pt);
+        int kept = 0;
+        int64_t a = 0;
+        while (a < n) {
+            int64_t b = a;   /* the segment is pts[a..b] */
+            while (b + 1 < n) {
+                int64_t dx = pts[b + 1].x - pts[b].x, dy = pts[b + 1].y - pts[b].y;
+                if (dx * dx + dy * dy > gap2) break;
+                b++;
+            }
+            int64_t dx = pts[b].x - pts[a].x, dy = pts[b].y - pts[a].y;
+            if (dx * dx + dy * dy >= len2) {
+                if (kept < max_segments) {
+                    int32_t *o = segs + ((size_t)p * max_segments + kept) * 6;
+                    o[0] = pts[a].x; o[1] = pts[a].y; o[2] = pts[b].x; o[3] = pts[b].y;
+                    o[4] = k; o[5] = r;
+                }
+                kept++;
+            }
+            a = b + 1;
+        }
+        counts[p] = kept;
+    }
+    free(pts);
+    free(c);
+    free(s);
+}
