@@ -216,6 +216,71 @@ LD_API ld_status ld_hough_peaks_static(const int32_t *d_acc, int32_t n_theta,
                                        void *stream);
 
 /*
+ * Hough lines: the line segments behind each peak (Step 4 of Sec. 1 without
+ * the drawing; the paper hands the peaks to MATLAB's "Hough lines", Sec. 5,
+ * Fig. 12, with no parameters stated).  For a peak (theta_idx k, rho_idx r)
+ * the supporting pixels are the edges whose Q16 rho at theta_k is cell r (the
+ * vote's own rounding, so their number is the peak's vote count).  They are
+ * ordered along the line -- by x then y when |c_k| <= |s_k| (the line is at
+ * most 45 degrees from horizontal), else by y then x -- and split wherever two
+ * consecutive pixels are farther apart than fill_gap (squared Euclidean
+ * distance > fill_gap^2); a piece is kept when its end pixels are at least
+ * min_length apart (squared distance >= min_length^2).  A segment runs from
+ * its first pixel (x1, y1) to its last (x2, y2) in that order.
+ */
+typedef struct {
+    int32_t fill_gap;      /* largest gap inside a segment, pixels, 0..65535     [20] */
+    int32_t min_length;    /* shortest kept segment, pixels, 0..65535            [40] */
+    int32_t max_segments;  /* segments stored per peak, 1..4096                   [16] */
+    int32_t reserved;      /* must be 0 */
+} ld_lines_params;
+
+typedef struct {
+    int32_t x1, y1, x2, y2;     /* first and last supporting pixel */
+    int32_t theta_idx, rho_idx; /* the peak's cell */
+} ld_segment;
+
+/* Fill *lp with the defaults listed in ld_lines_params. */
+LD_API ld_status ld_lines_params_default(ld_lines_params *lp);
+
+/*
+ * Hough lines of one frame from its edge list and peaks.
+ *   d_edges      uint32 edge list as for ld_hough_vote (16-byte aligned,
+ *                distinct in-image pixels; entries outside the image are skipped).
+ *   d_edge_count int32 [1]: min(count, capacity) edges are read (capacity =
+ *                p->edge_capacity or w*h when 0).
+ *   d_peaks      ld_peak [p->top_k] and d_n_peaks int32 [1], as ld_hough_peaks
+ *                writes them (theta_idx < p->n_theta, rho_idx < 2D+1).
+ *   d_segments   ld_segment [top_k][lp->max_segments] output: peak j's kept
+ *                segments in line order (the first max_segments of them).
+ *   d_n_segments int32 [top_k] output: kept segments per peak (may exceed
+ *                max_segments; 0 for j >= *d_n_peaks).
+ *   d_support    int32 [top_k] output (nullable): supporting pixels per peak.
+ * Sizes: as ld_hough_vote, and max(w, h) <= 8192 (a peak's supporting pixels,
+ * at most 2 max(w, h), are sorted in shared memory), else LD_ERR_INVALID.
+ * p and lp may be NULL for the defaults.
+ */
+LD_API ld_status ld_hough_lines(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_edge_count,
+                                int32_t w, int32_t h, const ld_params *p, const ld_peak *d_peaks,
+                                const int32_t *d_n_peaks, const ld_lines_params *lp,
+                                ld_segment *d_segments, int32_t *d_n_segments, int32_t *d_support,
+                                void *stream);
+
+/*
+ * Steps 1-4 with the Hough lines: ld_detect_batch, then the segments of every
+ * frame's peaks from the frame's edge list (kept in the context scratch).
+ * Outputs as ld_detect_batch plus d_segments [n][top_k][max_segments],
+ * d_n_segments [n][top_k] and d_support [n][top_k] (nullable), laid out per
+ * frame as ld_hough_lines writes them.  Frames need max(w, h) <= 8192.
+ * The segments of a frame are meaningful when its d_status is LD_OK.
+ */
+LD_API ld_status ld_detect_lines_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                                       const ld_params *p, const ld_lines_params *lp,
+                                       ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status,
+                                       ld_segment *d_segments, int32_t *d_n_segments,
+                                       int32_t *d_support, void *stream);
+
+/*
  * Autotuner for ld_detect_batch.  For every distinct frame size among
  * h_frames (device images, as in ld_detect_batch), it times ld_detect_batch
  * on the frames of that size, `iters` calls per candidate: first the voting

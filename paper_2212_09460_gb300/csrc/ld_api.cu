@@ -318,8 +318,34 @@ int rows_for(const ld_ctx *ctx, const ld_frame *fr, int g0, int g1, int n_theta)
     return pick_sobel_groups(ctas_g1, ctx->num_sms);
 }
 
+// Hough-lines request riding on a detection call (ld_detect_lines_batch).
+struct LinesReq {
+    ld_lines_params lp;
+    ld_segment *segs;   // [n][top_k][max_segments]
+    int32_t *n_segs;    // [n][top_k]
+    int32_t *support;   // nullable [n][top_k]
+};
+
 ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
-                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s);
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines = nullptr);
+
+ld_lines_params lines_defaults() {
+    ld_lines_params q;
+    q.fill_gap = 20;
+    q.min_length = 40;
+    q.max_segments = 16;
+    q.reserved = 0;
+    return q;
+}
+
+ld_status check_lines(const ld_lines_params &q) {
+    if (q.fill_gap < 0 || q.fill_gap > 65535 || q.min_length < 0 || q.min_length > 65535)
+        return fail(LD_ERR_INVALID, "fill_gap and min_length must be in [0, 65535]");
+    if (q.max_segments < 1 || q.max_segments > 4096)
+        return fail(LD_ERR_INVALID, "max_segments must be in [1, 4096], got %d", q.max_segments);
+    if (q.reserved != 0) return fail(LD_ERR_INVALID, "ld_lines_params.reserved must be 0");
+    return LD_OK;
+}
 
 }  // namespace
 
@@ -613,6 +639,84 @@ ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_theta, int
     return LD_OK;
 }
 
+ld_status ld_lines_params_default(ld_lines_params *lp) {
+    if (!lp) return fail(LD_ERR_INVALID, "ld_lines_params_default: NULL");
+    *lp = lines_defaults();
+    return LD_OK;
+}
+
+ld_status ld_hough_lines(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_edge_count, int32_t w, int32_t h,
+                         const ld_params *pp, const ld_peak *d_peaks, const int32_t *d_n_peaks,
+                         const ld_lines_params *lpp, ld_segment *d_segments, int32_t *d_n_segments,
+                         int32_t *d_support, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_hough_lines: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    const ld_lines_params lp = lpp ? *lpp : lines_defaults();
+    st = check_lines(lp);
+    if (st != LD_OK) return st;
+    if (!d_edges || !aligned16(d_edges) || !d_edge_count || !d_peaks || !d_n_peaks || !d_segments || !d_n_segments)
+        return fail(LD_ERR_INVALID, "ld_hough_lines: NULL or misaligned buffer");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, ht);
+    if (st != LD_OK) return st;
+    if (w > kLinesMaxSide || h > kLinesMaxSide)
+        return fail(LD_ERR_INVALID, "ld_hough_lines: max(w, h) must be <= %d", kLinesMaxSide);
+    LinesLaunch LL;
+    std::memset(&LL, 0, sizeof LL);
+    LL.n = 1;
+    LL.top_k = p.top_k;
+    LL.n_theta = p.n_theta;
+    LL.fill_gap = lp.fill_gap;
+    LL.min_length = lp.min_length;
+    LL.max_segments = lp.max_segments;
+    LL.trig = dt;
+    LinesFrame &LF = LL.f[0];
+    LF.edges = d_edges;
+    LF.count = d_edge_count;
+    LF.cap = p.edge_capacity > 0 ? p.edge_capacity : (int64_t)w * h;
+    LF.peaks = d_peaks;
+    LF.n_peaks = d_n_peaks;
+    LF.segs = d_segments;
+    LF.n_segs = d_n_segments;
+    LF.support = d_support;
+    LF.w = w;
+    LF.h = h;
+    LF.D = (int32_t)rho_max_of(w, h);
+    const cudaError_t e = launch_lines(LL, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lines launch");
+    return LD_OK;
+}
+
+ld_status ld_detect_lines_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                                const ld_lines_params *lpp, ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status,
+                                ld_segment *d_segments, int32_t *d_n_segments, int32_t *d_support, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_lines_batch: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    LinesReq req;
+    req.lp = lpp ? *lpp : lines_defaults();
+    st = check_lines(req.lp);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1 || !d_peaks || !d_n_peaks || !d_status || !d_segments || !d_n_segments)
+        return fail(LD_ERR_INVALID, "ld_detect_lines_batch: bad arguments");
+    req.segs = d_segments;
+    req.n_segs = d_n_segments;
+    req.support = d_support;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    return detect_impl(ctx, h_frames, n, p, d_peaks, d_n_peaks, d_status, (cudaStream_t)stream, &req);
+}
+
 ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
                           ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status, void *stream) {
     if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_batch: NULL ctx");
@@ -632,7 +736,7 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
 namespace {
 
 ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
-                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s) {
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines) {
     ld_status st;
     const int32_t *dt;
     const std::vector<int32_t> *ht;
@@ -644,6 +748,8 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
         if (!f.img || f.pitch < f.w || (f.pitch & 15) || !aligned16(f.img) || f.reserved != 0)
             return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
+        if (lines && (f.w > kLinesMaxSide || f.h > kLinesMaxSide))
+            return fail(LD_ERR_INVALID, "frame %d: Hough lines need max(w, h) <= %d", i, kLinesMaxSide);
     }
     const int M = cand_m(p);
     // scratch for the largest group of frames
@@ -888,6 +994,35 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             if (e != cudaSuccess) return cuda_fail(e, "hough launch");
         }
         if (tev) cudaEventRecord(tev[2], s);
+        if (lines) {   // the group's edge lists and peaks are in place: its Hough lines
+            LinesLaunch LL;
+            std::memset(&LL, 0, sizeof LL);
+            LL.n = gn;
+            LL.top_k = p.top_k;
+            LL.n_theta = p.n_theta;
+            LL.fill_gap = lines->lp.fill_gap;
+            LL.min_length = lines->lp.min_length;
+            LL.max_segments = lines->lp.max_segments;
+            LL.trig = dt;
+            for (int k = 0; k < gn; ++k) {
+                const ld_frame &fr = h_frames[g0 + k];
+                const size_t fi = (size_t)(g0 + k);
+                LinesFrame &LF = LL.f[k];
+                LF.edges = edges + eoffs[k];
+                LF.count = sm.counts + k;
+                LF.cap = (int64_t)fr.w * fr.h;
+                LF.peaks = d_peaks + fi * p.top_k;
+                LF.n_peaks = d_n_peaks + fi;
+                LF.segs = lines->segs + fi * p.top_k * lines->lp.max_segments;
+                LF.n_segs = lines->n_segs + fi * p.top_k;
+                LF.support = lines->support ? lines->support + fi * p.top_k : nullptr;
+                LF.w = fr.w;
+                LF.h = fr.h;
+                LF.D = plans[k].D;
+            }
+            e = launch_lines(LL, s);
+            if (e != cudaSuccess) return cuda_fail(e, "lines launch");
+        }
     }
     return LD_OK;
 }

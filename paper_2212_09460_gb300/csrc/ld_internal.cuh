@@ -167,7 +167,31 @@ __host__ __device__ inline uint64_t peak_key(int32_t votes, int32_t theta, int32
            (uint64_t(0xFFFFu - uint32_t(theta)) << 16) | uint64_t(0xFFFFu - uint32_t(rho));
 }
 
+// ---------------------------------------------------------------- Hough lines
+constexpr int kLinesKeys = 16384;      // supporting pixels one CTA holds (2 max(w, h))
+constexpr int kLinesMaxSide = kLinesKeys / 2;
+
+struct LinesFrame {
+    const uint32_t *edges;  // 16-byte aligned edge list
+    const int32_t *count;
+    int64_t cap;
+    const ld_peak *peaks;   // [top_k]
+    const int32_t *n_peaks;
+    ld_segment *segs;       // [top_k][max_segments]
+    int32_t *n_segs;        // [top_k]
+    int32_t *support;       // nullable [top_k]
+    int32_t w, h, D, pad_;
+};
+
+struct LinesLaunch {
+    int32_t n, top_k, n_theta, fill_gap, min_length, max_segments;
+    const int32_t *trig;    // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
+    LinesFrame f[kMaxLaunchFrames];
+};
+
 // ---------------------------------------------------------------- launchers
+// One CTA per (frame, peak slot).
+cudaError_t launch_lines(const LinesLaunch &L, cudaStream_t s);
 cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s);
 // Persistent launch: n_ctas CTAs (at most one per SM) pull L.total_units
 // work units from L.queue.  acc_words_max: the largest pairs_per_tile * n_rho

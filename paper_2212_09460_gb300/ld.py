@@ -38,6 +38,16 @@ class ld_peak(ctypes.Structure):
     _fields_ = [("theta_idx", ctypes.c_int32), ("rho_idx", ctypes.c_int32), ("votes", ctypes.c_int32)]
 
 
+class ld_lines_params(ctypes.Structure):
+    _fields_ = [("fill_gap", ctypes.c_int32), ("min_length", ctypes.c_int32), ("max_segments", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ld_segment(ctypes.Structure):
+    _fields_ = [("x1", ctypes.c_int32), ("y1", ctypes.c_int32), ("x2", ctypes.c_int32), ("y2", ctypes.c_int32),
+                ("theta_idx", ctypes.c_int32), ("rho_idx", ctypes.c_int32)]
+
+
 class ld_frame(ctypes.Structure):
     _fields_ = [("img", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("pitch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -83,6 +93,11 @@ _SIGS = {
     "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
                         _P],
     "ld_ctx_set_wait_limit": [_P, ctypes.c_int64],
+    "ld_lines_params_default": [ctypes.POINTER(ld_lines_params)],
+    "ld_hough_lines": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P,
+                       ctypes.POINTER(ld_lines_params), _P, _P, _P, _P],
+    "ld_detect_lines_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
+                              ctypes.POINTER(ld_lines_params), _P, _P, _P, _P, _P, _P, _P],
     "ld_hough_peaks_static": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_autotune": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.c_int32, _P],
     "ld_ctx_plan": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), ctypes.POINTER(ctypes.c_int32),
@@ -202,6 +217,33 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
     """frames: sequence of (device_ptr, w, h, pitch), or a ctypes ld_frame array."""
     arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
     _check(load().ld_detect_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
+
+
+def ld_lines_params_default() -> ld_lines_params:
+    q = ld_lines_params()
+    _check(load().ld_lines_params_default(ctypes.byref(q)))
+    return q
+
+
+def lines_params(fill_gap=20, min_length=40, max_segments=16) -> ld_lines_params:
+    q = ld_lines_params()
+    _check(load().ld_lines_params_default(ctypes.byref(q)))
+    q.fill_gap, q.min_length, q.max_segments = fill_gap, min_length, max_segments
+    return q
+
+
+def ld_hough_lines(ctx, d_edges, d_count, w, h, p, d_peaks, d_n_peaks, lp, d_segs, d_nsegs, d_support,
+                   stream) -> None:
+    _check(load().ld_hough_lines(ctx, d_edges, d_count, w, h, None if p is None else ctypes.byref(p), d_peaks,
+                                 d_n_peaks, None if lp is None else ctypes.byref(lp), d_segs, d_nsegs, d_support,
+                                 stream))
+
+
+def ld_detect_lines_batch(ctx, frames, p, lp, d_peaks, d_n_peaks, d_status, d_segs, d_nsegs, d_support,
+                          stream) -> None:
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_lines_batch(ctx, arr, len(arr), ctypes.byref(p), ctypes.byref(lp), d_peaks, d_n_peaks,
+                                        d_status, d_segs, d_nsegs, d_support, stream))
 
 
 def ld_hough_peaks_static(d_acc, n_theta, n_rho, p, d_peaks, d_n_peaks, stream) -> None:
@@ -504,6 +546,39 @@ class Context:
             out = torch.empty((len(descs), (h + 7) // 8, (w + 7) // 8), dtype=torch.uint8, device=frames[0].device)
         ld_edge_pool_batch(self.handle, descs, p, out.data_ptr(), _stream_handle(stream))
         return out
+
+    def hough_lines(self, edges, count, w: int, h: int, p: ld_params, peaks, n_peaks, lp: ld_lines_params,
+                    stream=None):
+        """Hough lines of one frame from device tensors (edge list, count [1],
+        peaks [top_k][3], n_peaks [1]); returns (segments [top_k][max_segments][6],
+        n_segments [top_k], support [top_k])."""
+        torch = _torch()
+        dev = edges.device
+        segs = torch.zeros((p.top_k, lp.max_segments, 6), dtype=torch.int32, device=dev)
+        nseg = torch.zeros(p.top_k, dtype=torch.int32, device=dev)
+        sup = torch.zeros(p.top_k, dtype=torch.int32, device=dev)
+        ld_hough_lines(self.handle, edges.data_ptr(), count.data_ptr(), w, h, p, peaks.data_ptr(), n_peaks.data_ptr(),
+                       lp, segs.data_ptr(), nseg.data_ptr(), sup.data_ptr(), _stream_handle(stream))
+        return segs, nseg, sup
+
+    def detect_lines_batch(self, frames, p: ld_params, lp: ld_lines_params, widths=None, stream=None):
+        """Steps 1-4 and the Hough lines; returns (peaks, n_peaks, status,
+        segments [n][top_k][max_segments][6], n_segments [n][top_k], support [n][top_k])."""
+        torch = _torch()
+        if isinstance(frames, PreparedBatch):
+            descs, dev = frames.array, frames.device
+        else:
+            descs, dev = self._descs(frames, widths), frames[0].device
+        n = len(descs)
+        peaks = torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev)
+        npk = torch.zeros(n, dtype=torch.int32, device=dev)
+        st = torch.zeros(n, dtype=torch.int32, device=dev)
+        segs = torch.zeros((n, p.top_k, lp.max_segments, 6), dtype=torch.int32, device=dev)
+        nseg = torch.zeros((n, p.top_k), dtype=torch.int32, device=dev)
+        sup = torch.zeros((n, p.top_k), dtype=torch.int32, device=dev)
+        ld_detect_lines_batch(self.handle, descs, p, lp, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
+                              segs.data_ptr(), nseg.data_ptr(), sup.data_ptr(), _stream_handle(stream))
+        return peaks, npk, st, segs, nseg, sup
 
     def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
         """Steps 1-4 on a list of uint8 CUDA tensors (or a PreparedBatch);

@@ -32,6 +32,8 @@ def test_struct_layouts_match_header(ld):
     assert ctypes.sizeof(ld.ld_params) == 40
     assert ctypes.sizeof(ld.ld_peak) == 12
     assert ctypes.sizeof(ld.ld_frame) == 24
+    assert ctypes.sizeof(ld.ld_lines_params) == 16
+    assert ctypes.sizeof(ld.ld_segment) == 24
     assert ctypes.sizeof(ld.ld_synth_stripe) == 64
     assert ctypes.sizeof(ld.ld_synth_frame) == 328
 
