@@ -67,6 +67,10 @@ def _load():
         lib.ldo_detect.restype = i32
         lib.ldo_hough_lines.argtypes = [P, i64, i32, i32, i32, P, i32, i32, i32, i32, P, P, P]
         lib.ldo_hough_lines.restype = None
+        lib.ldo_canny.argtypes = [P, i32, i32, i32, i32, i32, P, P]
+        lib.ldo_canny.restype = None
+        lib.ldo_canny_blur.argtypes = [P, i32, i32, i32, P]
+        lib.ldo_canny_blur.restype = None
         _lib = lib
         return lib
 
@@ -184,3 +188,22 @@ def hough_lines(edges: np.ndarray, w: int, h: int, n_theta: int, peaks: np.ndarr
                             int(min_length), int(max_segments), _ptr(segs), _ptr(counts),
                             _ptr(support))
     return segs[:n_p], counts[:n_p], support[:n_p]
+
+
+def canny(img: np.ndarray, t_low: int = 100, t_high: int = 200, return_mag: bool = False):
+    """Canny edges in place of Steps 1-2 (the paper's future work): 0/255 map
+    [h][w] (and the magnitude |gx| + |gy| of the blurred image, int32 [h][w])."""
+    img, w, h, pitch = _img(img)
+    out = np.empty((h, w), np.uint8)
+    mag = np.empty((h, w), np.int32) if return_mag else None
+    _load().ldo_canny(_ptr(img), w, h, pitch, int(t_low), int(t_high), _ptr(out),
+                      _ptr(mag) if return_mag else None)
+    return (out, mag) if return_mag else out
+
+
+def canny_blur(img: np.ndarray) -> np.ndarray:
+    """The Canny Gaussian stage alone: (sum of 5x5 binomial x pixels + 128) >> 8."""
+    img, w, h, pitch = _img(img)
+    out = np.empty((h, w), np.uint8)
+    _load().ldo_canny_blur(_ptr(img), w, h, pitch, _ptr(out))
+    return out

@@ -325,3 +325,107 @@ void ldo_hough_lines(const uint32_t *edges, int64_t n_edges, int w, int h,
     free(c);
     free(s);
 }
+
+/*
+ * Canny edge detection in place of Steps 1-2 (the paper's future work, Sec. 7),
+ * producing the same 0/255 map and edge list the Hough vote reads.  Every stage
+ * works on the image domain with zero outside it (the padding of Sec. 3.1),
+ * in integers:
+ *   1. Gaussian blur with the 5x5 binomial kernel b b^T, b = (1 4 6 4 1) (sum
+ *      256), rounded: G = (sum K I + 128) >> 8, 0..255.
+ *   2. Sobel on G (the kernels of Step 1): gx, gy, magnitude M = |gx| + |gy|
+ *      (Eq. 1, not saturated, 0..2040).
+ *   3. Direction sector from tan(22.5 deg) = 27146 / 65536 and tan(67.5 deg) =
+ *      158218 / 65536 (rounded): |gy| 65536 <= 27146 |gx| compares along x,
+ *      |gy| 65536 >= 158218 |gx| along y, otherwise along the diagonal
+ *      (x-1, y-1)-(x+1, y+1) when gx gy > 0, else (x+1, y-1)-(x-1, y+1).
+ *   4. Non-maximum suppression: a pixel stays if M > 0, M > M(n1) and
+ *      M >= M(n2), where n1 is the neighbour of the pair with the smaller y (the
+ *      smaller x along x): a ridge two pixels wide keeps one pixel.
+ *   5. Hysteresis: a kept pixel is strong if M >= t_high, weak if t_low <= M <
+ *      t_high; the edges are the strong pixels and every weak pixel joined to a
+ *      strong one by an 8-connected chain of weak or strong pixels.
+ * bin receives 0/255 [h][w]; mag (nullable) M [h][w] as int32.
+ */
+static int ldo_g_at(const uint8_t *g, int w, int h, int x, int y)
+{
+    return (x < 0 || y < 0 || x >= w || y >= h) ? 0 : g[(size_t)y * w + x];
+}
+
+void ldo_canny(const uint8_t *img, int w, int h, int pitch, int t_low, int t_high,
+               uint8_t *bin, int32_t *mag_out)
+{
+    static const int B5[5] = {1, 4, 6, 4, 1};
+    size_t n = (size_t)w * h;
+    uint8_t *g = (uint8_t *)malloc(n);
+    int32_t *m = (int32_t *)malloc(n * sizeof(int32_t));
+    uint8_t *sec = (uint8_t *)malloc(n);
+    uint8_t *cls = (uint8_t *)malloc(n);
+    int32_t *queue = (int32_t *)malloc(n * sizeof(int32_t));
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            int s = 0;
+            for (int j = -2; j <= 2; j++)
+                for (int i = -2; i <= 2; i++)
+                    s += B5[j + 2] * B5[i + 2] * pix(img, w, h, pitch, x + i, y + j);
+            g[(size_t)y * w + x] = (uint8_t)((s + 128) >> 8);
+        }
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            int gx = (ldo_g_at(g, w, h, x + 1, y - 1) + 2 * ldo_g_at(g, w, h, x + 1, y) + ldo_g_at(g, w, h, x + 1, y + 1))
+                   - (ldo_g_at(g, w, h, x - 1, y - 1) + 2 * ldo_g_at(g, w, h, x - 1, y) + ldo_g_at(g, w, h, x - 1, y + 1));
+            int gy = (ldo_g_at(g, w, h, x - 1, y + 1) + 2 * ldo_g_at(g, w, h, x, y + 1) + ldo_g_at(g, w, h, x + 1, y + 1))
+                   - (ldo_g_at(g, w, h, x - 1, y - 1) + 2 * ldo_g_at(g, w, h, x, y - 1) + ldo_g_at(g, w, h, x + 1, y - 1));
+            int64_t ax = abs(gx), ay = abs(gy);
+            m[(size_t)y * w + x] = (int32_t)(ax + ay);
+            int sc;
+            if (ay * 65536 <= 27146 * ax) sc = 0;
+            else if (ay * 65536 >= 158218 * ax) sc = 2;
+            else sc = ((int64_t)gx * gy > 0) ? 1 : 3;
+            sec[(size_t)y * w + x] = (uint8_t)sc;
+        }
+    /* neighbour offsets (n1, n2) per sector: n1 has the smaller y (smaller x along x) */
+    static const int DX1[4] = {-1, -1, 0, 1}, DY1[4] = {0, -1, -1, -1};
+    static const int DX2[4] = {1, 1, 0, -1}, DY2[4] = {0, 1, 1, 1};
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            size_t i = (size_t)y * w + x;
+            int sc = sec[i], v = m[i];
+            int x1 = x + DX1[sc], y1 = y + DY1[sc], x2 = x + DX2[sc], y2 = y + DY2[sc];
+            int v1 = (x1 < 0 || y1 < 0 || x1 >= w || y1 >= h) ? 0 : m[(size_t)y1 * w + x1];
+            int v2 = (x2 < 0 || y2 < 0 || x2 >= w || y2 >= h) ? 0 : m[(size_t)y2 * w + x2];
+            int keep = v > 0 && v > v1 && v >= v2;
+            cls[i] = !keep ? 0 : (v >= t_high ? 2 : (v >= t_low ? 1 : 0));
+        }
+    /* flood fill from the strong pixels through weak ones (8-connected) */
+    size_t qh = 0, qt = 0;
+    memset(bin, 0, n);
+    for (size_t i = 0; i < n; i++)
+        if (cls[i] == 2) { bin[i] = 255; queue[qt++] = (int32_t)i; }
+    while (qh < qt) {
+        int i = queue[qh++], x = i % w, y = i / w;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int xx = x + dx, yy = y + dy;
+                if (xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                size_t j = (size_t)yy * w + xx;
+                if (cls[j] && !bin[j]) { bin[j] = 255; queue[qt++] = (int32_t)j; }
+            }
+    }
+    if (mag_out) memcpy(mag_out, m, n * sizeof(int32_t));
+    free(g); free(m); free(sec); free(cls); free(queue);
+}
+
+/* Gaussian stage alone (step 1 above), for pinning: out [h][w]. */
+void ldo_canny_blur(const uint8_t *img, int w, int h, int pitch, uint8_t *out)
+{
+    static const int B5[5] = {1, 4, 6, 4, 1};
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            int s = 0;
+            for (int j = -2; j <= 2; j++)
+                for (int i = -2; i <= 2; i++)
+                    s += B5[j + 2] * B5[i + 2] * pix(img, w, h, pitch, x + i, y + j);
+            out[(size_t)y * w + x] = (uint8_t)((s + 128) >> 8);
+        }
+}
