@@ -281,6 +281,42 @@ LD_API ld_status ld_detect_lines_batch(ld_ctx *ctx, const ld_frame *h_frames, in
                                        int32_t *d_support, void *stream);
 
 /*
+ * Canny edge detection in place of Steps 1-2 (the paper's future work, Sec. 7),
+ * behind the same edge-list boundary as ld_sobel_binarize.  Integer stages, each
+ * with zero outside the image (the padding of Sec. 3.1): a 5x5 binomial blur
+ * G = (sum b_i b_j I + 128) >> 8 with b = (1 4 6 4 1); the Sobel magnitude
+ * M = |gx| + |gy| of G (Eq. 1, not saturated); the gradient sector from
+ * tan(22.5) = 27146/65536 and tan(67.5) = 158218/65536 (|gy| 65536 <= 27146 |gx|:
+ * along x; >= 158218 |gx|: along y; else the diagonal of the sign of gx gy);
+ * non-maximum suppression keeping M > 0, M > M(n1), M >= M(n2) with n1 the
+ * neighbour with the smaller y (smaller x along x); hysteresis: the edges are
+ * the 8-connected components of kept pixels with M >= t_low that hold one with
+ * M >= t_high.  p->border = LD_BORDER_CLEAR also zeroes the 1-pixel frame;
+ * p->threshold is not used.
+ */
+typedef struct {
+    int32_t t_low;         /* weak edge threshold on M, 1..2040    [100] */
+    int32_t t_high;        /* strong edge threshold on M, t_low..2040 [200] */
+    int32_t reserved0, reserved1;   /* must be 0 */
+} ld_canny_params;
+
+/* Fill *cp with the defaults listed in ld_canny_params. */
+LD_API ld_status ld_canny_params_default(ld_canny_params *cp);
+
+/* Canny edges of one frame: arguments and outputs as ld_sobel_binarize (the
+ * edge list in unspecified order, the true count, optional 0/255 map); the
+ * context holds 6 bytes of scratch per pixel.  cp may be NULL for the defaults. */
+LD_API ld_status ld_canny(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
+                          const ld_params *p, const ld_canny_params *cp, uint8_t *d_bin,
+                          uint32_t *d_edges, int32_t *d_edge_count, void *stream);
+
+/* Steps 1-4 as ld_detect_batch with Canny edges in place of Steps 1-2. */
+LD_API ld_status ld_detect_canny_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                                       const ld_params *p, const ld_canny_params *cp,
+                                       ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status,
+                                       void *stream);
+
+/*
  * Autotuner for ld_detect_batch.  For every distinct frame size among
  * h_frames (device images, as in ld_detect_batch), it times ld_detect_batch
  * on the frames of that size, `iters` calls per candidate: first the voting

@@ -86,6 +86,7 @@ struct ld_ctx {
     DevBuf edges, small, cand;            // detect_batch / hough_peaks scratch
     DevBuf prop;                          // proposal path: edge-count maps, activations, pair lists
     DevBuf part;                          // interleaved voting: split tiles' partial accumulators + counters
+    DevBuf canny;                         // Canny: class map, union-find forest, strong marks
     std::vector<cudaEvent_t> ev;   // 3 events per timed call, reused in order
     int timed_calls = 0;           // timed calls since the last ld_ctx_stage_ms
     bool timing = false;
@@ -327,7 +328,32 @@ struct LinesReq {
 };
 
 ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
-                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines = nullptr);
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines = nullptr,
+                      const ld_canny_params *canny = nullptr);
+
+ld_canny_params canny_defaults() {
+    ld_canny_params q;
+    q.t_low = 100;
+    q.t_high = 200;
+    q.reserved0 = q.reserved1 = 0;
+    return q;
+}
+
+ld_status check_canny(const ld_canny_params &q) {
+    if (q.t_low < 1 || q.t_low > 2040 || q.t_high < q.t_low || q.t_high > 2040)
+        return fail(LD_ERR_INVALID, "Canny thresholds: need 1 <= t_low <= t_high <= 2040");
+    if (q.reserved0 || q.reserved1) return fail(LD_ERR_INVALID, "ld_canny_params.reserved must be 0");
+    return LD_OK;
+}
+
+// Canny scratch of px pixels: class map, strong marks, then the forest (4-byte aligned).
+size_t canny_scratch_bytes(int64_t px) { return ((size_t)px * 2 + 15) / 16 * 16 + (size_t)px * 4; }
+void canny_scratch(void *base, int64_t px_total, int64_t px_off, CannyFrame &F) {
+    uint8_t *b = (uint8_t *)base;
+    F.cls = b + px_off;
+    F.strong = b + px_total + px_off;
+    F.parent = (int32_t *)(b + ((size_t)px_total * 2 + 15) / 16 * 16) + px_off;
+}
 
 ld_lines_params lines_defaults() {
     ld_lines_params q;
@@ -405,6 +431,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->cand.release();
         ctx->prop.release();
         ctx->part.release();
+        ctx->canny.release();
     }
     delete ctx;
     return LD_OK;
@@ -532,6 +559,75 @@ ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_
     e = launch_sobel(L, sobel_frame_ctas(w, h, L.groups), s);
     if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
     return LD_OK;
+}
+
+ld_status ld_canny_params_default(ld_canny_params *cp) {
+    if (!cp) return fail(LD_ERR_INVALID, "ld_canny_params_default: NULL");
+    *cp = canny_defaults();
+    return LD_OK;
+}
+
+ld_status ld_canny(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch, const ld_params *pp,
+                   const ld_canny_params *cpp, uint8_t *d_bin, uint32_t *d_edges, int32_t *d_edge_count,
+                   void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_canny: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    const ld_canny_params cp = cpp ? *cpp : canny_defaults();
+    st = check_canny(cp);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, nullptr);
+    if (st != LD_OK) return st;
+    if (!d_img || !d_edges || !d_edge_count) return fail(LD_ERR_INVALID, "ld_canny: NULL buffer");
+    if (pitch < w || (pitch & 15) || !aligned16(d_img) || (d_bin && !aligned16(d_bin)))
+        return fail(LD_ERR_INVALID, "pitch must be >= w and a multiple of 16, buffers 16-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int64_t px = (int64_t)w * h;
+    if (!ctx->canny.ensure(canny_scratch_bytes(px))) return fail(LD_ERR_NOMEM, "scratch Canny");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_edge_count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
+    CannyLaunch CL;
+    std::memset(&CL, 0, sizeof CL);
+    CL.n = 1;
+    CL.t_low = cp.t_low;
+    CL.t_high = cp.t_high;
+    CL.border = p.border;
+    CL.total_px = px;
+    CannyFrame &CF = CL.f[0];
+    CF.img = d_img;
+    CF.bin = d_bin;
+    CF.edges = d_edges;
+    CF.count = d_edge_count;
+    canny_scratch(ctx->canny.p, px, 0, CF);
+    CF.cap = p.edge_capacity > 0 ? p.edge_capacity : px;
+    CF.w = w;
+    CF.h = h;
+    CF.pitch = pitch;
+    e = launch_canny(CL, canny_tiles(w, h), s);
+    if (e != cudaSuccess) return cuda_fail(e, "canny launch");
+    return LD_OK;
+}
+
+ld_status ld_detect_canny_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                                const ld_canny_params *cpp, ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status,
+                                void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_canny_batch: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    const ld_canny_params cp = cpp ? *cpp : canny_defaults();
+    st = check_canny(cp);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1 || !d_peaks || !d_n_peaks || !d_status)
+        return fail(LD_ERR_INVALID, "ld_detect_canny_batch: bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    return detect_impl(ctx, h_frames, n, p, d_peaks, d_n_peaks, d_status, (cudaStream_t)stream, nullptr, &cp);
 }
 
 ld_status ld_hough_vote(ld_ctx *ctx, const uint32_t *d_edges, const int32_t *d_edge_count, int32_t w,
@@ -736,7 +832,8 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
 namespace {
 
 ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params &p, ld_peak *d_peaks,
-                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines) {
+                      int32_t *d_n_peaks, int32_t *d_status, cudaStream_t s, const LinesReq *lines,
+                      const ld_canny_params *canny) {
     ld_status st;
     const int32_t *dt;
     const std::vector<int32_t> *ht;
@@ -982,8 +1079,44 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             ++ctx->timed_calls;
         }
         if (tev) cudaEventRecord(tev[0], s);
-        e = launch_sobel(SLn, sob_ctas, s);
-        if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+        if (canny) {   // Canny edges in place of Steps 1-2, into the same lists
+            int64_t px = 0;
+            for (int k = 0; k < gn; ++k) px += (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h;
+            if (!ctx->canny.ensure(canny_scratch_bytes(px))) return fail(LD_ERR_NOMEM, "scratch Canny");
+            CannyLaunch CL;
+            std::memset(&CL, 0, sizeof CL);
+            CL.n = gn;
+            CL.t_low = canny->t_low;
+            CL.t_high = canny->t_high;
+            CL.border = p.border;
+            CL.total_px = px;
+            int tiles = 0;
+            int64_t off = 0;
+            for (int k = 0; k < gn; ++k) {
+                const ld_frame &fr = h_frames[g0 + k];
+                CannyFrame &CF = CL.f[k];
+                CF.img = fr.img;
+                CF.bin = nullptr;
+                CF.edges = edges + eoffs[k];
+                CF.count = sm.counts + k;
+                CF.status_init = d_status + g0 + k;
+                CF.npeaks_init = d_n_peaks + g0 + k;
+                canny_scratch(ctx->canny.p, px, off, CF);
+                CF.cap = (int64_t)fr.w * fr.h;
+                CF.px_begin = off;
+                CF.w = fr.w;
+                CF.h = fr.h;
+                CF.pitch = fr.pitch;
+                CF.tile_begin = tiles;
+                tiles += canny_tiles(fr.w, fr.h);
+                off += (int64_t)fr.w * fr.h;
+            }
+            e = launch_canny(CL, tiles, s);
+            if (e != cudaSuccess) return cuda_fail(e, "canny launch");
+        } else {
+            e = launch_sobel(SLn, sob_ctas, s);
+            if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+        }
         if (tev) cudaEventRecord(tev[1], s);
         if (!sub_c.empty()) {
             e = launch_hough_cols(HLn, std::min(bc.units, ctx->num_sms), bc.rows_max, s);

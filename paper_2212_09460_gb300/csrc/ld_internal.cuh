@@ -189,7 +189,34 @@ struct LinesLaunch {
     LinesFrame f[kMaxLaunchFrames];
 };
 
+// ---------------------------------------------------------------- Canny
+struct CannyFrame {
+    const uint8_t *img;
+    uint8_t *bin;          // nullable 0/255 map [h][pitch]
+    uint32_t *edges;
+    int32_t *count;
+    int32_t *status_init;  // nullable: set to LD_ERR_TIMEOUT until the frame's peaks are merged
+    int32_t *npeaks_init;  // nullable: set to 0 likewise
+    uint8_t *cls;          // scratch [h][w]: 0, 1 weak, 2 strong
+    int32_t *parent;       // scratch [h][w]: union-find forest
+    uint8_t *strong;       // scratch [h][w]: root holds a strong pixel
+    int64_t cap;
+    int64_t px_begin;      // first pixel of this frame in the launch's pixel range
+    int32_t w, h, pitch;
+    int32_t tile_begin;    // first 32 x 32 tile of this frame
+};
+
+struct CannyLaunch {
+    int32_t n, t_low, t_high, border;
+    int64_t total_px;
+    CannyFrame f[kMaxLaunchFrames];
+};
+
 // ---------------------------------------------------------------- launchers
+// Canny edges of a launch's frames (four launches on the stream); n_tiles =
+// the sum of canny_tiles over the frames.
+cudaError_t launch_canny(const CannyLaunch &L, int n_tiles, cudaStream_t s);
+int canny_tiles(int w, int h);
 // One CTA per (frame, peak slot).
 cudaError_t launch_lines(const LinesLaunch &L, cudaStream_t s);
 cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s);

@@ -48,6 +48,11 @@ class ld_segment(ctypes.Structure):
                 ("theta_idx", ctypes.c_int32), ("rho_idx", ctypes.c_int32)]
 
 
+class ld_canny_params(ctypes.Structure):
+    _fields_ = [("t_low", ctypes.c_int32), ("t_high", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
+
+
 class ld_frame(ctypes.Structure):
     _fields_ = [("img", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("pitch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -94,6 +99,11 @@ _SIGS = {
                         _P],
     "ld_ctx_set_wait_limit": [_P, ctypes.c_int64],
     "ld_lines_params_default": [ctypes.POINTER(ld_lines_params)],
+    "ld_canny_params_default": [ctypes.POINTER(ld_canny_params)],
+    "ld_canny": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
+                 ctypes.POINTER(ld_canny_params), _P, _P, _P, _P],
+    "ld_detect_canny_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
+                              ctypes.POINTER(ld_canny_params), _P, _P, _P, _P],
     "ld_hough_lines": [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P,
                        ctypes.POINTER(ld_lines_params), _P, _P, _P, _P],
     "ld_detect_lines_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params),
@@ -217,6 +227,29 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
     """frames: sequence of (device_ptr, w, h, pitch), or a ctypes ld_frame array."""
     arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
     _check(load().ld_detect_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
+
+
+def ld_canny_params_default() -> ld_canny_params:
+    q = ld_canny_params()
+    _check(load().ld_canny_params_default(ctypes.byref(q)))
+    return q
+
+
+def canny_params(t_low=100, t_high=200) -> ld_canny_params:
+    q = ld_canny_params_default()
+    q.t_low, q.t_high = t_low, t_high
+    return q
+
+
+def ld_canny(ctx, d_img, w, h, pitch, p, cp, d_bin, d_edges, d_count, stream) -> None:
+    _check(load().ld_canny(ctx, d_img, w, h, pitch, None if p is None else ctypes.byref(p),
+                           None if cp is None else ctypes.byref(cp), d_bin, d_edges, d_count, stream))
+
+
+def ld_detect_canny_batch(ctx, frames, p, cp, d_peaks, d_n_peaks, d_status, stream) -> None:
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_canny_batch(ctx, arr, len(arr), ctypes.byref(p), ctypes.byref(cp), d_peaks, d_n_peaks,
+                                        d_status, stream))
 
 
 def ld_lines_params_default() -> ld_lines_params:
@@ -546,6 +579,35 @@ class Context:
             out = torch.empty((len(descs), (h + 7) // 8, (w + 7) // 8), dtype=torch.uint8, device=frames[0].device)
         ld_edge_pool_batch(self.handle, descs, p, out.data_ptr(), _stream_handle(stream))
         return out
+
+    def canny(self, img, p: ld_params, cp: ld_canny_params, want_binary: bool = False, width: int | None = None,
+              stream=None) -> SobelOut:
+        """Canny edges of a [h][pitch] uint8 tensor (``width`` = w if padded)."""
+        torch = _torch()
+        ptr, pw, h, pitch = self._img(img)
+        w = pw if width is None else width
+        cap = p.edge_capacity if p.edge_capacity > 0 else w * h
+        edges = torch.empty(max(cap, 4), dtype=torch.int32, device=img.device)
+        count = torch.empty(1, dtype=torch.int32, device=img.device)
+        binary = torch.empty_like(img) if want_binary else None
+        ld_canny(self.handle, ptr, w, h, pitch, p, cp, binary.data_ptr() if binary is not None else None,
+                 edges.data_ptr(), count.data_ptr(), _stream_handle(stream))
+        return SobelOut(edges, count, binary)
+
+    def detect_canny_batch(self, frames, p: ld_params, cp: ld_canny_params, widths=None, stream=None):
+        """Steps 1-4 with Canny edges; returns (peaks [n][top_k][3], n_peaks [n], status [n])."""
+        torch = _torch()
+        if isinstance(frames, PreparedBatch):
+            descs, dev = frames.array, frames.device
+        else:
+            descs, dev = self._descs(frames, widths), frames[0].device
+        n = len(descs)
+        peaks = torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev)
+        npk = torch.zeros(n, dtype=torch.int32, device=dev)
+        st = torch.zeros(n, dtype=torch.int32, device=dev)
+        ld_detect_canny_batch(self.handle, descs, p, cp, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
+                              _stream_handle(stream))
+        return peaks, npk, st
 
     def hough_lines(self, edges, count, w: int, h: int, p: ld_params, peaks, n_peaks, lp: ld_lines_params,
                     stream=None):

@@ -34,6 +34,7 @@ def test_struct_layouts_match_header(ld):
     assert ctypes.sizeof(ld.ld_frame) == 24
     assert ctypes.sizeof(ld.ld_lines_params) == 16
     assert ctypes.sizeof(ld.ld_segment) == 24
+    assert ctypes.sizeof(ld.ld_canny_params) == 16
     assert ctypes.sizeof(ld.ld_synth_stripe) == 64
     assert ctypes.sizeof(ld.ld_synth_frame) == 328
 
