@@ -281,6 +281,29 @@ LD_API ld_status ld_detect_lines_batch(ld_ctx *ctx, const ld_frame *h_frames, in
                                        int32_t *d_support, void *stream);
 
 /*
+ * Steps 1-3 without an edge list, in the spirit of the paper's FPGA dataflow
+ * (Sec. 3.3: pixels stream through one unit per theta; Table 1): each CTA
+ * finds the edge pixels of a 32 x 32 block of the image (Steps 1-2 as in
+ * ld_sobel_binarize) and votes them into a shared-memory accumulator over
+ * every theta and the rho cells the block reaches, then adds its non-zero
+ * cells into d_acc.  The result equals ld_sobel_binarize followed by
+ * ld_hough_vote.
+ *   d_img   as for ld_sobel_binarize.
+ *   d_acc   int32 [n_theta][2D+1] output, fully overwritten (zeroed here first).
+ * Sizes: as ld_sobel_binarize, and p->n_theta <= 1024.
+ */
+LD_API ld_status ld_sobel_hough_fused(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h,
+                                      int32_t pitch, const ld_params *p, int32_t *d_acc, void *stream);
+
+/* Steps 1-4 as ld_detect_batch, with Steps 1-3 fused as in
+ * ld_sobel_hough_fused into per-frame accumulators in the context scratch
+ * (n_theta * (2D+1) int32 cells per frame), then the peaks of each.
+ * p->n_theta <= 1024. */
+LD_API ld_status ld_detect_fused_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                                       const ld_params *p, ld_peak *d_peaks, int32_t *d_n_peaks,
+                                       int32_t *d_status, void *stream);
+
+/*
  * Canny edge detection in place of Steps 1-2 (the paper's future work, Sec. 7),
  * behind the same edge-list boundary as ld_sobel_binarize.  Integer stages, each
  * with zero outside the image (the padding of Sec. 3.1): a 5x5 binomial blur

@@ -87,6 +87,7 @@ struct ld_ctx {
     DevBuf prop;                          // proposal path: edge-count maps, activations, pair lists
     DevBuf part;                          // interleaved voting: split tiles' partial accumulators + counters
     DevBuf canny;                         // Canny: class map, union-find forest, strong marks
+    DevBuf fused;                         // fused Steps 1-3: per-frame accumulators
     std::vector<cudaEvent_t> ev;   // 3 events per timed call, reused in order
     int timed_calls = 0;           // timed calls since the last ld_ctx_stage_ms
     bool timing = false;
@@ -432,6 +433,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->prop.release();
         ctx->part.release();
         ctx->canny.release();
+        ctx->fused.release();
     }
     delete ctx;
     return LD_OK;
@@ -558,6 +560,159 @@ ld_status ld_sobel_binarize(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_
     F.tiles_x = sobel_strips(w);
     e = launch_sobel(L, sobel_frame_ctas(w, h, L.groups), s);
     if (e != cudaSuccess) return cuda_fail(e, "sobel launch");
+    return LD_OK;
+}
+
+ld_status ld_sobel_hough_fused(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
+                               const ld_params *pp, int32_t *d_acc, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_sobel_hough_fused: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (p.n_theta > kFusedMaxTheta) return fail(LD_ERR_INVALID, "fused path: n_theta must be <= %d", kFusedMaxTheta);
+    if (!d_img || !d_acc) return fail(LD_ERR_INVALID, "ld_sobel_hough_fused: NULL buffer");
+    if (pitch < w || (pitch & 15) || !aligned16(d_img))
+        return fail(LD_ERR_INVALID, "pitch must be >= w and a multiple of 16, the image 16-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    st = check_size(w, h, p, ht);
+    if (st != LD_OK) return st;
+    const int D = (int)rho_max_of(w, h), n_rho = 2 * D + 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_acc, 0, (size_t)p.n_theta * n_rho * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(acc)");
+    FusedLaunch FL;
+    std::memset(&FL, 0, sizeof FL);
+    FL.n = 1;
+    FL.n_theta = p.n_theta;
+    FL.threshold = p.threshold;
+    FL.border = p.border;
+    FL.trig = dt;
+    FusedFrame &FF = FL.f[0];
+    FF.img = d_img;
+    FF.acc = d_acc;
+    FF.w = w;
+    FF.h = h;
+    FF.pitch = pitch;
+    FF.D = D;
+    FF.n_rho = n_rho;
+    FF.tiles_x = (w + kFusedBlock - 1) / kFusedBlock;
+    e = launch_fused_vote(FL, fused_blocks(w, h), s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+    return LD_OK;
+}
+
+ld_status ld_detect_fused_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                                ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_fused_batch: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (p.n_theta > kFusedMaxTheta) return fail(LD_ERR_INVALID, "fused path: n_theta must be <= %d", kFusedMaxTheta);
+    if (!h_frames || n < 1 || !d_peaks || !d_n_peaks || !d_status)
+        return fail(LD_ERR_INVALID, "ld_detect_fused_batch: bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        const ld_frame &f = h_frames[i];
+        st = check_size(f.w, f.h, p, ht);
+        if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
+        if (!f.img || f.pitch < f.w || (f.pitch & 15) || !aligned16(f.img) || f.reserved != 0)
+            return fail(LD_ERR_INVALID, "frame %d: NULL image, bad pitch or alignment", i);
+    }
+    const int M = cand_m(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int g0 = 0; g0 < n; g0 += kMaxLaunchFrames) {
+        const int g1 = std::min(n, g0 + kMaxLaunchFrames), gn = g1 - g0;
+        // per-frame accumulators, then the candidates of their chunks
+        std::vector<int64_t> aoff(gn), coff(gn);
+        int64_t acells = 0, ccount = 0;
+        int chunks = 0;
+        for (int k = 0; k < gn; ++k) {
+            const ld_frame &f = h_frames[g0 + k];
+            const int64_t cells = (int64_t)p.n_theta * (2 * rho_max_of(f.w, f.h) + 1);
+            aoff[k] = acells;
+            acells += (cells + 3) / 4 * 4;
+            coff[k] = ccount;
+            const int nc = (int)((cells + kSelectChunk - 1) / kSelectChunk);
+            ccount += (int64_t)nc * M;
+            chunks += nc;
+        }
+        if (!ctx->fused.ensure((size_t)acells * 4)) return fail(LD_ERR_NOMEM, "scratch accumulators");
+        if (!ctx->cand.ensure((size_t)ccount * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
+        int32_t *acc = (int32_t *)ctx->fused.p;
+        uint64_t *cand = (uint64_t *)ctx->cand.p;
+        cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)acells * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(acc)");
+        FusedLaunch FL;
+        std::memset(&FL, 0, sizeof FL);
+        FL.n = gn;
+        FL.n_theta = p.n_theta;
+        FL.threshold = p.threshold;
+        FL.border = p.border;
+        FL.trig = dt;
+        SelectLaunch SL;
+        std::memset(&SL, 0, sizeof SL);
+        SL.n = gn;
+        SL.cand_m = M;
+        SL.min_votes = p.min_votes;
+        MergeLaunch ML;
+        std::memset(&ML, 0, sizeof ML);
+        ML.n = gn;
+        ML.top_k = p.top_k;
+        ML.nms_theta = p.nms_theta;
+        ML.nms_rho = p.nms_rho;
+        int blocks = 0, chunk_begin = 0;
+        for (int k = 0; k < gn; ++k) {
+            const ld_frame &f = h_frames[g0 + k];
+            const int D = (int)rho_max_of(f.w, f.h), n_rho = 2 * D + 1;
+            const int64_t cells = (int64_t)p.n_theta * n_rho;
+            const int nc = (int)((cells + kSelectChunk - 1) / kSelectChunk);
+            FusedFrame &FF = FL.f[k];
+            FF.img = f.img;
+            FF.acc = acc + aoff[k];
+            FF.status_init = d_status + g0 + k;
+            FF.npeaks_init = d_n_peaks + g0 + k;
+            FF.w = f.w;
+            FF.h = f.h;
+            FF.pitch = f.pitch;
+            FF.D = D;
+            FF.n_rho = n_rho;
+            FF.tile_begin = blocks;
+            FF.tiles_x = (f.w + kFusedBlock - 1) / kFusedBlock;
+            blocks += fused_blocks(f.w, f.h);
+            SelectJob &J = SL.j[k];
+            J.acc = FF.acc;
+            J.cand = cand + coff[k];
+            J.cells = cells;
+            J.n_rho = n_rho;
+            J.n_chunks = nc;
+            J.chunk_begin = chunk_begin;
+            chunk_begin += nc;
+            MergeJob &MJ = ML.j[k];
+            MJ.cand = cand + coff[k];
+            MJ.n_cand = (int64_t)nc * M;
+            MJ.peaks = d_peaks + (size_t)(g0 + k) * p.top_k;
+            MJ.n_peaks = d_n_peaks + g0 + k;
+            MJ.status = d_status + g0 + k;
+        }
+        e = launch_fused_vote(FL, blocks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+        e = launch_select(SL, chunks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "select launch");
+        e = launch_merge(ML, s);
+        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+    }
     return LD_OK;
 }
 

@@ -1,0 +1,145 @@
+// ld_fused.cu -- Steps 1-3 without an edge list: each CTA takes a 32 x 32
+// block of a frame, finds its edge pixels (Sobel |Gx|+|Gy| on the zero-padded
+// image, Eq. 1, saturated and thresholded, Sec. 2.2) and votes them straight
+// into a shared-memory accumulator that covers every theta bin but only the
+// rho cells the block can reach (Eq. 3 with the Q16 table of Eqs. 4-5), then
+// adds its non-zero cells into the frame's int32 accumulator in global memory.
+//
+// This is the paper's FPGA dataflow (Sec. 3.3: pixels stream through one
+// processing element per theta, no list of edge coordinates in between) laid
+// out for a GPU: the pixel stream is cut into blocks so that a block's rho
+// range is short.  For a block of side 32, rho over the block spans at most
+// floor(31 (|cos| + |sin|) + 1) <= 45 cells per theta, so the block's
+// accumulator is at most kFusedRows x n_theta counters.  The votes are the
+// same integers as the two-stage path's, so the accumulator (and the peaks
+// taken from it) are identical.
+#include "ld_internal.cuh"
+
+namespace ld {
+namespace {
+
+constexpr int kFB = kFusedBlock;          // block side
+constexpr int kFThreads = kFB * kFB;      // one pixel per thread
+
+__device__ __forceinline__ int32_t floor_q16_i64(int64_t v) {
+    return (int32_t)(v >= 0 ? v / 65536 : -((-v + 65535) / 65536));
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) fused_vote_kernel(const __grid_constant__ FusedLaunch L) {
+    extern __shared__ __align__(16) int32_t fsm[];
+    const int n_theta = L.n_theta;
+    int32_t *acc_s = fsm;                                   // [kFusedRows][n_theta]
+    int32_t *rmin_s = acc_s + kFusedRows * n_theta;         // [n_theta] rho of row 0
+    int32_t *cs_s = rmin_s + n_theta;                       // [n_theta][2] Q16 (c, s)
+    uint32_t *edges_s = reinterpret_cast<uint32_t *>(cs_s + 2 * n_theta);   // [kFThreads]
+    __shared__ uint8_t patch[kFB + 2][kFB + 2];
+    __shared__ int n_edges;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.f[mid].tile_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const FusedFrame &F = L.f[lo];
+    const int local = blockIdx.x - F.tile_begin;
+    const int x0 = (local % F.tiles_x) * kFB, y0 = (local / F.tiles_x) * kFB;
+    const int w = F.w, h = F.h;
+    if (local == 0 && tid == 0) {   // until the merge writes the frame's peaks
+        if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
+        if (F.npeaks_init) *F.npeaks_init = 0;
+    }
+
+    // the block's pixels with a 1-pixel halo, zero outside the image
+    for (int i = tid; i < (kFB + 2) * (kFB + 2); i += kFThreads) {
+        const int r = i / (kFB + 2), c = i % (kFB + 2);
+        const int y = y0 - 1 + r, x = x0 - 1 + c;
+        patch[r][c] = (x >= 0 && y >= 0 && x < w && y < h) ? F.img[(size_t)y * F.pitch + x] : 0;
+    }
+    // per theta: Q16 (c, s) (Eqs. 4-5) and the smallest rho over the block's corners
+    const int half = n_theta / 2;
+    const int bx1 = min(x0 + kFB, w) - 1, by1 = min(y0 + kFB, h) - 1;
+    for (int k = tid; k < n_theta; k += kFThreads) {
+        const int kk = k <= half ? k : n_theta - k;
+        const int32_t c = k <= half ? L.trig[2 * kk] : -L.trig[2 * kk];
+        const int32_t s = L.trig[2 * kk + 1];
+        cs_s[2 * k] = c;
+        cs_s[2 * k + 1] = s;
+        const int64_t xm = c < 0 ? (int64_t)bx1 * c : (int64_t)x0 * c;
+        const int64_t ym = s < 0 ? (int64_t)by1 * s : (int64_t)y0 * s;
+        rmin_s[k] = floor_q16_i64(xm + ym + 32768);
+    }
+    for (int i = tid; i < kFusedRows * n_theta; i += kFThreads) acc_s[i] = 0;
+    if (tid == 0) n_edges = 0;
+    __syncthreads();
+
+    // Steps 1-2 for this thread's pixel
+    const int px = tid % kFB, py = tid / kFB;
+    const int x = x0 + px, y = y0 + py;
+    bool edge = false;
+    if (x < w && y < h) {
+        const uint8_t *a = patch[py] + px, *b = patch[py + 1] + px, *d = patch[py + 2] + px;
+        const int gx = (a[2] + 2 * b[2] + d[2]) - (a[0] + 2 * b[0] + d[0]);
+        const int gy = (d[0] + 2 * d[1] + d[2]) - (a[0] + 2 * a[1] + a[2]);
+        int m = abs(gx) + abs(gy);
+        m = m > 255 ? 255 : m;
+        edge = m >= L.threshold;
+        if (L.border == LD_BORDER_CLEAR && (x == 0 || y == 0 || x == w - 1 || y == h - 1)) edge = false;
+    }
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, edge);
+    if (bal) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&n_edges, __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (edge) edges_s[base + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)y << 16) | (uint32_t)x;
+    }
+    __syncthreads();
+
+    // Step 3 into the block's accumulator: pair j = (edge j / n_theta, theta j % n_theta)
+    const int ne = n_edges;
+    const int64_t pairs = (int64_t)ne * n_theta;
+    for (int64_t j = tid; j < pairs; j += kFThreads) {
+        const int e = (int)(j / n_theta), k = (int)(j - (int64_t)e * n_theta);
+        const uint32_t ev = edges_s[e];
+        const int ex = (int)(ev & 0xFFFFu), ey = (int)(ev >> 16);
+        const int32_t rho = (int32_t)((ex * cs_s[2 * k] + ey * cs_s[2 * k + 1] + 32768) >> 16);   // floor
+        const int row = rho - rmin_s[k];   // 0 .. 44 by the corner bound
+        if ((unsigned)row < (unsigned)kFusedRows) atomicAdd(&acc_s[row * n_theta + k], 1);
+    }
+    __syncthreads();
+
+    // the block's non-zero cells into the frame's accumulator
+    if (ne > 0) {
+        for (int i = tid; i < kFusedRows * n_theta; i += kFThreads) {
+            const int v = acc_s[i];
+            if (v) {
+                const int row = i / n_theta, k = i - row * n_theta;
+                atomicAdd(F.acc + (size_t)k * F.n_rho + (rmin_s[k] + row + F.D), v);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t fused_smem_bytes(int n_theta) {
+    return (size_t)(kFusedRows * n_theta + 3 * n_theta) * 4 + (size_t)kFThreads * 4;
+}
+
+int fused_blocks(int w, int h) { return ((w + kFB - 1) / kFB) * ((h + kFB - 1) / kFB); }
+
+cudaError_t launch_fused_vote(const FusedLaunch &L, int n_blocks, cudaStream_t s) {
+    if (n_blocks <= 0) return cudaSuccess;
+    const size_t smem = fused_smem_bytes(L.n_theta);
+    if (smem > (size_t)kSmemLimit - 2048) return cudaErrorInvalidValue;
+    static std::atomic<uint64_t> attr_done{0};
+    const cudaError_t e = once_per_device(attr_done, [](int) {
+        return cudaFuncSetAttribute(fused_vote_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kSmemLimit - 2048);
+    });
+    if (e != cudaSuccess) return e;
+    fused_vote_kernel<<<n_blocks, kFThreads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace ld

@@ -212,7 +212,33 @@ struct CannyLaunch {
     CannyFrame f[kMaxLaunchFrames];
 };
 
+// ---------------------------------------------------------------- fused Steps 1-3
+constexpr int kFusedBlock = 32;        // block side (pixels)
+constexpr int kFusedRows = 48;         // rho cells a block reaches per theta (<= 45)
+constexpr int kFusedMaxTheta = 1024;   // the block's accumulator fits shared memory
+
+struct FusedFrame {
+    const uint8_t *img;
+    int32_t *acc;          // [n_theta][n_rho], zeroed before the launch
+    int32_t *status_init;  // nullable: LD_ERR_TIMEOUT until the frame's peaks are merged
+    int32_t *npeaks_init;  // nullable: 0 likewise
+    int32_t w, h, pitch, D, n_rho;
+    int32_t tile_begin;    // first block of this frame
+    int32_t tiles_x;       // blocks per row
+    int32_t pad_;
+};
+
+struct FusedLaunch {
+    int32_t n, n_theta, threshold, border;
+    const int32_t *trig;   // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
+    FusedFrame f[kMaxLaunchFrames];
+};
+
 // ---------------------------------------------------------------- launchers
+// Fused Steps 1-3 (no edge list): one CTA per 32 x 32 block.
+cudaError_t launch_fused_vote(const FusedLaunch &L, int n_blocks, cudaStream_t s);
+size_t fused_smem_bytes(int n_theta);
+int fused_blocks(int w, int h);
 // Canny edges of a launch's frames (four launches on the stream); n_tiles =
 // the sum of canny_tiles over the frames.
 cudaError_t launch_canny(const CannyLaunch &L, int n_tiles, cudaStream_t s);

@@ -99,6 +99,10 @@ _SIGS = {
                         _P],
     "ld_ctx_set_wait_limit": [_P, ctypes.c_int64],
     "ld_lines_params_default": [ctypes.POINTER(ld_lines_params)],
+    "ld_sobel_hough_fused": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
+                             _P, _P],
+    "ld_detect_fused_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
+                              _P],
     "ld_canny_params_default": [ctypes.POINTER(ld_canny_params)],
     "ld_canny": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
                  ctypes.POINTER(ld_canny_params), _P, _P, _P, _P],
@@ -227,6 +231,16 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
     """frames: sequence of (device_ptr, w, h, pitch), or a ctypes ld_frame array."""
     arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
     _check(load().ld_detect_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
+
+
+def ld_sobel_hough_fused(ctx, d_img, w, h, pitch, p, d_acc, stream) -> None:
+    _check(load().ld_sobel_hough_fused(ctx, d_img, w, h, pitch, None if p is None else ctypes.byref(p), d_acc,
+                                       stream))
+
+
+def ld_detect_fused_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> None:
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_fused_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
 
 
 def ld_canny_params_default() -> ld_canny_params:
@@ -579,6 +593,33 @@ class Context:
             out = torch.empty((len(descs), (h + 7) // 8, (w + 7) // 8), dtype=torch.uint8, device=frames[0].device)
         ld_edge_pool_batch(self.handle, descs, p, out.data_ptr(), _stream_handle(stream))
         return out
+
+    def sobel_hough_fused(self, img, p: ld_params, width: int | None = None, acc=None, stream=None):
+        """Steps 1-3 without an edge list: the int32 [n_theta][2D+1] accumulator."""
+        torch = _torch()
+        ptr, pw, h, pitch = self._img(img)
+        w = pw if width is None else width
+        _, _, D = ld_query_sizes(w, h, p)
+        if acc is None:
+            acc = torch.empty((p.n_theta, 2 * D + 1), dtype=torch.int32, device=img.device)
+        ld_sobel_hough_fused(self.handle, ptr, w, h, pitch, p, acc.data_ptr(), _stream_handle(stream))
+        return acc
+
+    def detect_fused_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
+        """Steps 1-4 with Steps 1-3 fused; returns (peaks, n_peaks, status) as detect_batch."""
+        torch = _torch()
+        if isinstance(frames, PreparedBatch):
+            descs, dev = frames.array, frames.device
+        else:
+            descs, dev = self._descs(frames, widths), frames[0].device
+        n = len(descs)
+        if out is None:
+            out = (torch.zeros((n, p.top_k, 3), dtype=torch.int32, device=dev),
+                   torch.zeros(n, dtype=torch.int32, device=dev), torch.zeros(n, dtype=torch.int32, device=dev))
+        peaks, npk, st = out
+        ld_detect_fused_batch(self.handle, descs, p, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
+                              _stream_handle(stream))
+        return peaks, npk, st
 
     def canny(self, img, p: ld_params, cp: ld_canny_params, want_binary: bool = False, width: int | None = None,
               stream=None) -> SobelOut:
