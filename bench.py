@@ -323,6 +323,76 @@ def oracle_stages(reps_by_px=((400_000, 5), (1_000_000, 3), (2_100_000, 3), (10*
     return out
 
 
+def next_rows(torch, ld, dev, frames, edges_total: float, flush, reps: int = 10) -> dict:
+    """The other hot-path rows on the same 64 x 1080p batch (frames in HBM, L2
+    flushed before each call): Hough lines after the peaks, Canny edges in place
+    of Sobel, and Steps 1-3 fused without an edge list; plus one 640x480 frame
+    through the fused path (CUDA-graph replay)."""
+    p = ld.params(n_theta=N_THETA, top_k=TOP_K)
+    lp = ld.lines_params()
+    cp = ld.canny_params()
+    s = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(reps):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    out = {}
+    with ld.Context(dev.index) as c:
+        prep = c.prepare(frames)
+        c.autotune(frames[:16], p, iters=2)
+        base = timed(lambda: c.detect_batch(prep, p, stream=s))
+        res = {}
+        lines_ms = timed(lambda: res.update(r=c.detect_lines_batch(prep, p, lp, stream=s)))
+        pk, npk, st, segs, nseg, sup = res["r"]
+        torch.cuda.synchronize(dev)
+        assert int(st.abs().sum()) == 0
+        extra_ms = max(lines_ms - base, 1e-6)
+        read_bytes = edges_total * 4 * TOP_K   # each (frame, peak) CTA reads its frame's edge list
+        out["hough_lines"] = {
+            "workload": f"{len(frames)} x 1920x1080, top-{TOP_K} peaks, fill_gap {lp.fill_gap}, min_length "
+                        f"{lp.min_length}", "ms_detect": base, "ms_detect_and_lines": lines_ms,
+            "lines_ms": extra_ms, "segments_per_frame": float(nseg.sum().item()) / len(frames),
+            "edge_list_reads_gbs": read_bytes / (extra_ms / 1e3) / 1e9,
+            "note": "lines_ms = detect+lines minus detect; the edge lists are re-read from L2 by the 4 peaks of a frame"}
+        canny_ms = timed(lambda: c.detect_canny_batch(prep, p, cp, stream=s))
+        e = c.canny(frames[0], p, cp)
+        torch.cuda.synchronize(dev)
+        out["canny"] = {"workload": f"{len(frames)} x 1920x1080, Canny (t_low {cp.t_low}, t_high {cp.t_high}) in "
+                                    f"place of Sobel, then the same vote and peaks",
+                        "ms_per_batch": canny_ms, "frames_per_s": len(frames) / (canny_ms / 1e3),
+                        "edges_frame0": int(e.count.item())}
+        fused_ms = timed(lambda: c.detect_fused_batch(prep, p, stream=s))
+        out["fused"] = {"workload": f"{len(frames)} x 1920x1080, Steps 1-3 fused without an edge list "
+                                    "(32x32 blocks vote into block accumulators, global int32 accumulators), "
+                                    "then select + merge", "ms_per_batch": fused_ms,
+                        "frames_per_s": len(frames) / (fused_ms / 1e3), "two_stage_ms": base}
+    from paper_2212_09460_gb300 import synth
+    p180 = ld.params(n_theta=180, top_k=2)
+    one = [torch.from_numpy(synth.road_frame(0, 640, 480, synth.LATENCY_640x480)).to(dev)]
+    with ld.Context(dev.index) as c:
+        c.reserve(640 * 480, 1, 0, p180)
+        outs = (torch.zeros((1, 2, 3), dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev),
+                torch.zeros(1, dtype=torch.int32, device=dev))
+        c.detect_fused_batch(one, p180, out=outs)   # sizes the scratch before the capture
+        torch.cuda.synchronize(dev)
+        ms1 = graph_time(torch, lambda: c.detect_fused_batch(one, p180, out=outs), 50, None)
+        assert int(outs[2].abs().sum()) == 0
+    out["fused_latency_640x480"] = {"workload": "one 640x480 frame (seed 0), 180 theta, top-2, fused Steps 1-3, "
+                                                "CUDA-graph replay, warm L2", "us_per_frame": ms1 * 1e3}
+    return out
+
+
 def smem_red_rates(torch, ld, dev, n_sms: int) -> dict:
     """Measured 32-bit shared-memory reduction rate of this GPU (Gred/s):
     conflict-free (lanes on distinct banks: the ceiling of a vote) and random
@@ -420,7 +490,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the mixed-resolution batching, single-frame latency, proposal and serving measurements")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the 8-camera serving run at the nominal 30 frames/s per camera (0: skip)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames per GPU (the workload is 64; smaller values are for profiling captures)")
@@ -569,7 +639,7 @@ def main():
         sobel_bytes = nf * W * H * 1 + e_sum * 4
         atom_nominal = n_sms * 32 * sm_max_mhz * 1e6 / 1e9       # Gvote/s: 32 banks/clk/SM
         atom_peak = red_rates["conflict_free"]
-        roof = {"bound": "alu", "kernel": "hough_cols_kernel (Step 3 interleaved-column voting + per-tile top-M "
+        roof = {"bound": "smem_atomic", "kernel": "hough_cols_kernel (Step 3 interleaved-column voting + per-tile top-M "
                                           "+ the frame's peak merge)",
                 "achieved": votes / hough_s / 1e9, "peak": atom_peak, "unit": "Gvote/s",
                 "frac": votes / hough_s / 1e9 / atom_peak, "traffic": measured_traffic("hough", nf),
@@ -586,6 +656,7 @@ def main():
         if mixed_host is not None:
             extra["batching"], extra["latency_640x480"] = batching_and_latency(
                 torch, ld, dev, mixed_host, lambda: flush.fill_(7))
+            extra["next_rows"] = next_rows(torch, ld, dev, frame_list, e_sum, lambda: flush.fill_(5))
             extra["proposal"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9))
             # the configuration's literal fallback rule (max band probability < 0.9)
             extra["proposal_fallback_0.9"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9),

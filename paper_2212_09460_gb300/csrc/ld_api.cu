@@ -216,8 +216,8 @@ Small small_of(void *p) {
 // Split tiles of the interleaved voting kernel: at most num_sms pieces in a
 // launch; scratch = the pieces' arrival counters (one per tile, 256-byte
 // padded) then their partial accumulators.
-size_t split_scratch_bytes(int pieces, int rows) {
-    return ((size_t)pieces * 4 + 255) / 256 * 256 + (size_t)pieces * rows * kHoughColPairs * 4;
+size_t split_scratch_bytes(int pieces, int words) {
+    return ((size_t)pieces * 4 + 255) / 256 * 256 + (size_t)pieces * words * 4;
 }
 
 HoughPlan plan_with_pairs(int w, int h, int n_theta, int pairs) {
@@ -266,17 +266,19 @@ int interleaved_rows(const ld_ctx *ctx, int w, int h, int n_theta) {
     return r;
 }
 
-// The interleaved-column plan (tiles of at most kHoughColPairs pairs, split
-// evenly), or a plan with cols == false if its accumulator does not fit.
+// The interleaved-column plan (tiles of at most `width` pairs, split evenly:
+// 16 slots, or 8 when the frame's window rows do not fit 16 columns), or a
+// plan with cols == false if even 8 columns do not fit.
 HoughPlan plan_cols(const ld_ctx *ctx, int w, int h, int n_theta) {
     HoughPlan hp;
     hp.D = (int)rho_max_of(w, h);
     hp.n_rho = 2 * hp.D + 1;
     const int n_pairs = n_theta / 2;
-    hp.n_tiles = (n_pairs + kHoughColPairs - 1) / kHoughColPairs;
-    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
     hp.rows = interleaved_rows(ctx, w, h, n_theta);
-    hp.cols = hp.rows <= hough_cols_max_rows();
+    hp.width = hp.rows <= hough_cols_max_rows(kHoughColPairs) ? kHoughColPairs : 8;
+    hp.n_tiles = (n_pairs + hp.width - 1) / hp.width;
+    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
+    hp.cols = hp.rows <= hough_cols_max_rows(hp.width);
     return hp;
 }
 
@@ -284,7 +286,7 @@ HoughPlan plan_cols(const ld_ctx *ctx, int w, int h, int n_theta) {
 // interleaved-column kernel (full vote in candidate mode with min_votes >= 1,
 // where cells outside a theta's window, which it does not hold, cannot be
 // candidates).  Forced (autotuner), else tuned, else the interleaved kernel
-// when it fits and its tiles hold at least 12 pairs on average (a lane per
+// when it fits and its tiles are at least 3/4 full on average (a lane per
 // pair: emptier tiles leave lanes idle), else the packed-pair plan.
 HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta, bool allow_cols) {
     int pairs = ctx->force_pairs;
@@ -295,7 +297,8 @@ HoughPlan plan_for(const ld_ctx *ctx, int w, int h, int n_theta, bool allow_cols
     if (pairs > 0) return plan_with_pairs(w, h, n_theta, pairs);
     if (allow_cols) {
         const HoughPlan hc = plan_cols(ctx, w, h, n_theta);
-        if (hc.cols && (pairs == -1 || n_theta >= 24 * hc.n_tiles)) return hc;
+        // tiles at least 3/4 full on average (n_pairs / n_tiles >= 0.75 width)
+        if (hc.cols && (pairs == -1 || 2 * n_theta >= 3 * hc.width * hc.n_tiles)) return hc;
     }
     return plan_hough(w, h, n_theta);
 }
@@ -477,7 +480,7 @@ ld_status ld_ctx_reserve(ld_ctx *ctx, int64_t max_pixels, int32_t max_frames, in
     int64_t nc = groups_frames * per_frame;
     if (acc_chunks * cand_m(p) > nc) nc = acc_chunks * cand_m(p);
     if (!ctx->cand.ensure((size_t)nc * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
-    if (max_frames > 0 && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hough_cols_max_rows())))
+    if (max_frames > 0 && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hough_cols_max_words())))
         return fail(LD_ERR_NOMEM, "scratch partial accumulators");
     return LD_OK;
 }
@@ -1012,7 +1015,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         for (int i = g0; i < g1; ++i) {
             ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
             const int T0 = plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta, false).n_tiles;
-            const int Tc = (p.n_theta / 2 + kHoughColPairs - 1) / kHoughColPairs;
+            const int Tc = plan_cols(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles;
             ca += (int64_t)std::max(Tc, std::min(p.n_theta / 2, T0 + (T0 + 3) / 4)) * M;   // room for balance_tiles
         }
         if (ed > max_edges) max_edges = ed;
@@ -1129,7 +1132,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         // launch with fewer tiles than SMs (small batches: latency) splits
         // every tile, if its frames are large enough.
         struct Built {
-            int units = 0, pmax = 1, rows_max = 1;
+            int units = 0, pmax = 1, words_cols = 16;   // words_cols: largest interleaved accumulator
             int64_t words_max = 0;
         };
         auto build_launch = [&](HoughLaunch &HL, bool cols, const std::vector<int> &sub, int32_t *queue,
@@ -1143,18 +1146,18 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
                 for (int q = 0; q < gs; ++q) {
                     const int k = sub[q];
                     tiles_q[q] = plans[k].n_tiles;
-                    B.rows_max = std::max(B.rows_max, plans[k].rows);
+                    B.words_cols = std::max(B.words_cols, plans[k].rows * plans[k].width);
                     px_min = std::min(px_min, (int64_t)h_frames[g0 + k].w * h_frames[g0 + k].h);
                 }
                 const PieceSplit ps = plan_pieces(tiles_q.data(), gs, px_min, ctx->num_sms);
                 split_from = ps.split_from;
                 ns_split = ps.ns;
                 split_tiles = ps.split_tiles;
-                HL.col_chunk = hough_cols_chunk(B.rows_max);
-                HL.part_stride = B.rows_max * kHoughColPairs;
+                HL.col_chunk = hough_cols_chunk(B.words_cols);
+                HL.part_stride = B.words_cols;
                 if (split_tiles > 0) {
                     const size_t cnt_bytes = ((size_t)split_tiles * 4 + 255) / 256 * 256;
-                    if (!ctx->part.ensure(split_scratch_bytes(split_tiles * ns_split, B.rows_max)))
+                    if (!ctx->part.ensure(split_scratch_bytes(split_tiles * ns_split, B.words_cols)))
                         return fail(LD_ERR_NOMEM, "scratch partial accumulators");
                     HL.tile_cnt = (int32_t *)ctx->part.p;
                     HL.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
@@ -1200,6 +1203,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
                 HF.pairs_per_tile = hp.pairs;
                 HF.n_tiles = hp.n_tiles;
                 HF.rows = hp.rows;
+                HF.col_width = hp.width;
                 B.units += hp.n_tiles * HF.n_splits;
                 if (hp.pairs > B.pmax) B.pmax = hp.pairs;
                 const int64_t wds = (int64_t)hp.pairs * hp.n_rho;
@@ -1274,7 +1278,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         }
         if (tev) cudaEventRecord(tev[1], s);
         if (!sub_c.empty()) {
-            e = launch_hough_cols(HLn, std::min(bc.units, ctx->num_sms), bc.rows_max, s);
+            e = launch_hough_cols(HLn, std::min(bc.units, ctx->num_sms), bc.words_cols, s);
             if (e != cudaSuccess) return cuda_fail(e, "hough launch");
         }
         if (!sub_p.empty()) {
@@ -1485,7 +1489,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     // the interleaved-column kernel votes the kept pairs when the frame fits it
     // and min_votes >= 1 (its windows leave unvoted cells out); device plan
     const HoughPlan hc = plan_cols(ctx, w, h, p.n_theta);
-    const bool cols = p.min_votes >= 1 && hc.cols;
+    const bool cols = p.min_votes >= 1 && hc.cols && hc.width == kHoughColPairs;
     const int n_pairs = p.n_theta / 2;
     const int64_t epf = ((int64_t)w * h + 3) / 4 * 4;
     if (!ctx->edges.ensure((size_t)(n * epf) * 4)) return fail(LD_ERR_NOMEM, "scratch edges");
@@ -1494,7 +1498,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     // units can shrink to fill the persistent launch's last wave
     const int tile_cap = cols ? hc.n_tiles : std::min(n_pairs, 2 * hp.n_tiles);
     if (!ctx->cand.ensure((size_t)n * tile_cap * M * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
-    if (cols && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hc.rows)))
+    if (cols && !ctx->part.ensure(split_scratch_bytes(ctx->num_sms, hc.rows * kHoughColPairs)))
         return fail(LD_ERR_NOMEM, "scratch partial accumulators");
     // proposal scratch, carved in 256-byte aligned pieces
     size_t off = 0;
@@ -1582,7 +1586,7 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
     HL.unit_begin_dev = ub;
     if (cols) {
         HL.col_plan = cplan;
-        HL.col_chunk = hough_cols_chunk(hc.rows);
+        HL.col_chunk = hough_cols_chunk(hc.rows * kHoughColPairs);
         HL.part_stride = hc.rows * kHoughColPairs;
         HL.tile_cnt = tile_cnt;
         HL.part = (uint32_t *)((uint8_t *)ctx->part.p + cnt_bytes);
@@ -1608,10 +1612,11 @@ ld_status ld_detect_batch_proposal(ld_ctx *ctx, const ld_frame *h_frames, int32_
         HF.pairs_per_tile = hp.pairs;
         HF.n_tiles = tile_cap;   // unused: the device plan gives each frame's tiles
         HF.rows = hc.rows;
+        HF.col_width = kHoughColPairs;
     }
     const int max_units = n * tile_cap * (cols ? kMaxSplits : 1);
     const int ctas = max_units < ctx->num_sms ? max_units : ctx->num_sms;
-    e = cols ? launch_hough_cols(HL, ctas, hc.rows, s)
+    e = cols ? launch_hough_cols(HL, ctas, hc.rows * kHoughColPairs, s)
              : launch_hough(HL, ctas, hp.pairs, (int64_t)hp.pairs * hp.n_rho, s);
     if (e != cudaSuccess) return cuda_fail(e, "hough launch");
     if (d_active_pairs) {

@@ -20,6 +20,8 @@ namespace {
 
 constexpr int kFB = kFusedBlock;          // block side
 constexpr int kFThreads = kFB * kFB;      // one pixel per thread
+constexpr int kRS = kFusedRows + 1;       // odd row stride of a theta's counters: lanes of
+                                          // consecutive thetas fall on different banks
 
 __device__ __forceinline__ int32_t floor_q16_i64(int64_t v) {
     return (int32_t)(v >= 0 ? v / 65536 : -((-v + 65535) / 65536));
@@ -28,8 +30,8 @@ __device__ __forceinline__ int32_t floor_q16_i64(int64_t v) {
 __global__ void __launch_bounds__(kFThreads, 1) fused_vote_kernel(const __grid_constant__ FusedLaunch L) {
     extern __shared__ __align__(16) int32_t fsm[];
     const int n_theta = L.n_theta;
-    int32_t *acc_s = fsm;                                   // [kFusedRows][n_theta]
-    int32_t *rmin_s = acc_s + kFusedRows * n_theta;         // [n_theta] rho of row 0
+    int32_t *acc_s = fsm;                                   // [n_theta][kRS]
+    int32_t *rmin_s = acc_s + kRS * n_theta;                // [n_theta] rho of row 0
     int32_t *cs_s = rmin_s + n_theta;                       // [n_theta][2] Q16 (c, s)
     uint32_t *edges_s = reinterpret_cast<uint32_t *>(cs_s + 2 * n_theta);   // [kFThreads]
     __shared__ uint8_t patch[kFB + 2][kFB + 2];
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_vote_kernel(const __grid_c
         const int64_t ym = s < 0 ? (int64_t)by1 * s : (int64_t)y0 * s;
         rmin_s[k] = floor_q16_i64(xm + ym + 32768);
     }
-    for (int i = tid; i < kFusedRows * n_theta; i += kFThreads) acc_s[i] = 0;
+    for (int i = tid; i < kRS * n_theta; i += kFThreads) acc_s[i] = 0;
     if (tid == 0) n_edges = 0;
     __syncthreads();
 
@@ -95,25 +97,30 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_vote_kernel(const __grid_c
     }
     __syncthreads();
 
-    // Step 3 into the block's accumulator: pair j = (edge j / n_theta, theta j % n_theta)
+    // Step 3 into the block's accumulator: thread t votes theta t % n_theta for
+    // the edges t / n_theta, + G, + 2G, ... (G = the thread groups that fit)
     const int ne = n_edges;
-    const int64_t pairs = (int64_t)ne * n_theta;
-    for (int64_t j = tid; j < pairs; j += kFThreads) {
-        const int e = (int)(j / n_theta), k = (int)(j - (int64_t)e * n_theta);
-        const uint32_t ev = edges_s[e];
-        const int ex = (int)(ev & 0xFFFFu), ey = (int)(ev >> 16);
-        const int32_t rho = (int32_t)((ex * cs_s[2 * k] + ey * cs_s[2 * k + 1] + 32768) >> 16);   // floor
-        const int row = rho - rmin_s[k];   // 0 .. 44 by the corner bound
-        if ((unsigned)row < (unsigned)kFusedRows) atomicAdd(&acc_s[row * n_theta + k], 1);
+    const int G = kFThreads / n_theta;   // >= 1 (n_theta <= 1024)
+    if (tid < G * n_theta) {
+        const int k = tid % n_theta;
+        const int32_t c = cs_s[2 * k], s = cs_s[2 * k + 1], r0 = rmin_s[k];
+        int32_t *col = acc_s + k * kRS;
+        for (int e = tid / n_theta; e < ne; e += G) {
+            const uint32_t ev = edges_s[e];
+            const int32_t rho = (int32_t)(((int)(ev & 0xFFFFu) * c + (int)(ev >> 16) * s + 32768) >> 16);   // floor
+            const int row = rho - r0;   // 0 .. 44 by the corner bound
+            if ((unsigned)row < (unsigned)kFusedRows) atomicAdd(col + row, 1);
+        }
     }
     __syncthreads();
 
-    // the block's non-zero cells into the frame's accumulator
+    // the block's non-zero cells into the frame's accumulator: consecutive
+    // threads take consecutive rho cells of one theta (contiguous addresses)
     if (ne > 0) {
-        for (int i = tid; i < kFusedRows * n_theta; i += kFThreads) {
+        for (int i = tid; i < kRS * n_theta; i += kFThreads) {
             const int v = acc_s[i];
             if (v) {
-                const int row = i / n_theta, k = i - row * n_theta;
+                const int k = i / kRS, row = i - k * kRS;
                 atomicAdd(F.acc + (size_t)k * F.n_rho + (rmin_s[k] + row + F.D), v);
             }
         }
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_vote_kernel(const __grid_c
 }  // namespace
 
 size_t fused_smem_bytes(int n_theta) {
-    return (size_t)(kFusedRows * n_theta + 3 * n_theta) * 4 + (size_t)kFThreads * 4;
+    return (size_t)(kRS * n_theta + 3 * n_theta) * 4 + (size_t)kFThreads * 4;
 }
 
 int fused_blocks(int w, int h) { return ((w + kFB - 1) / kFB) * ((h + kFB - 1) / kFB); }

@@ -120,21 +120,23 @@ struct PairRowLayout {
     __device__ __forceinline__ int rho(int slot, int half, int row) const { return row; }
 };
 
-// InterleavedLayout: word row * kCols + slot; row r of slot p holds the count
-// of theta_lo(p) at rho index r + lo[p] and of theta_hi(p) at r + hi[p] (each
-// theta's rho window starts at its own minimum over the image).
-constexpr int kCols = kHoughColPairs;
+// InterleavedLayout<W>: word row * W + slot (W = 16 or 8 slots); row r of
+// slot p holds the count of theta_lo(p) at rho index r + lo[p] and of
+// theta_hi(p) at r + hi[p] (each theta's rho window starts at its own minimum
+// over the image).
+constexpr int kCols = kHoughColPairs;   // the widest tile
+template <int W>
 struct InterleavedLayout {
     const int *lo, *hi;   // shared memory: rho index of row 0 per slot and half
     int rows;
     __device__ __forceinline__ void cells(int i, int &slot, int &rho_lo, int &rho_hi) const {
-        slot = i % kCols;
-        const int row = i / kCols;
+        slot = i % W;
+        const int row = i / W;
         rho_lo = row + lo[slot];
         rho_hi = row + hi[slot];
     }
     __device__ __forceinline__ int col_len() const { return rows; }
-    __device__ __forceinline__ int word(int slot, int row) const { return row * kCols + slot; }
+    __device__ __forceinline__ int word(int slot, int row) const { return row * W + slot; }
     __device__ __forceinline__ int rho(int slot, int half, int row) const { return row + (half ? hi[slot] : lo[slot]); }
 };
 
@@ -633,6 +635,7 @@ enum ColResult { kColAbort = -1, kColPiece = 0, kColTile = 1 };
 // the others' and selects.  Returns kColTile if this unit finished its tile
 // (candidates written), kColPiece if another piece will, kColAbort if a
 // bounded wait gave up (the frame is flagged; the CTA must stop).
+template <int NC>
 __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame &F, int tile, int split,
                                          int n_tiles, int ns, int split_base, uint32_t &seq, uint8_t *smem_raw,
                                          ColRing &R, SelectSmem &S, int &abort_flag, int &last_s, int *tj,
@@ -641,13 +644,16 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_avail = F.pair_list ? *F.pair_count : n_theta / 2;
     const int base = n_avail / n_tiles, extra = n_avail % n_tiles;
-    const int np = base + (tile < extra ? 1 : 0);   // <= kCols (plan)
+    const int np = base + (tile < extra ? 1 : 0);   // <= NC (plan)
     const int j0 = tile * base + min(tile, extra);
     const bool has0 = (F.pair_list ? F.pair_list[j0] : j0) == 0;
     const int W = F.w, H = F.h, D = F.D, rows = F.rows;
 
     // per-lane constants: (c, s) and Q16 offset of both thetas of the lane's pair
-    const int slot = lane % kCols, half = lane / kCols;
+    // lane -> (slot, part): NC = 16 slots: two half-warps, NC = 8: four
+    // quarter-warps, each voting its own edge into all NC slots
+    constexpr int kParts = 32 / NC;
+    const int slot = lane % NC, half = lane / NC;
     const int j = slot < np ? (F.pair_list ? F.pair_list[j0 + slot] : j0 + slot) : 0;   // unused: a spare column
     const int32_t cl = L.trig[2 * j], sl = L.trig[2 * j + 1];
     const int32_t ch = j == 0 ? L.trig[2 * (n_theta / 2)] : -cl;
@@ -658,7 +664,7 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
     // e = y * 65536 + x, so e c + y (s - 65536 c) = x c + y s (mod 2^32)
     const uint32_t sl2 = (uint32_t)sl - ((uint32_t)cl << 16), sh2 = (uint32_t)sh - ((uint32_t)ch << 16);
     const uint32_t lim = ((uint32_t)(H - 1) << 16) | (uint32_t)(W - 1);   // clamp of (y, x)
-    if (warp == 0 && half == 0) {
+    if (warp == 0 && half == 0) {   // lanes 0 .. NC-1
         tj[slot] = j;
         wlo[slot] = ml + D;   // rho index of row 0
         whi[slot] = mh + D;
@@ -666,29 +672,30 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
 
     uint32_t *ring = reinterpret_cast<uint32_t *>(smem_raw);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem_raw + (size_t)kColStages * chunk * 4);
-    const int words = rows * kCols;
+    const int words = rows * NC;
     const uint32_t acc_slot = smem_u32(acc) + (uint32_t)slot * 4u;
 
     // ---- zero the accumulator
     {
         uint4 *a4 = reinterpret_cast<uint4 *>(acc);
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < words / 4; i += kColThreads) a4[i] = z;   // words is a multiple of 16
+        for (int i = tid; i < words / 4; i += kColThreads) a4[i] = z;   // words is a multiple of 8
     }
     __syncthreads();
 
-    // ---- this unit's chunks: split `split` of the frame's chunks
+    // ---- this unit's edges: range `split` of ns, boundaries at multiples of 4
+    //      edges (16 bytes, for the bulk copies), streamed in chunks
     int64_t E = (int64_t)*F.count;
     if (E > F.cap) E = F.cap;
     if (E < 0) E = 0;
-    const int chunks_all = (int)((E + chunk - 1) / chunk);
-    const int c0 = (int)((int64_t)chunks_all * split / ns), c1 = (int)((int64_t)chunks_all * (split + 1) / ns);
-    const int n_chunks = c1 - c0;
+    const int64_t e0 = (E * split / ns) & ~int64_t(3);
+    const int64_t e1 = (split + 1 == ns) ? E : ((E * (split + 1) / ns) & ~int64_t(3));
+    const int n_chunks = e1 > e0 ? (int)((e1 - e0 + chunk - 1) / chunk) : 0;
 
-    auto issue = [&](int c) {   // local chunk c (frame chunk c0 + c)
+    auto issue = [&](int c) {   // local chunk c: edges e0 + c * chunk ..
         const int st = (int)((seq + (uint32_t)c) % kColStages);
-        const int64_t start = (int64_t)(c0 + c) * chunk;
-        const int n_c = (int)((E - start) < chunk ? (E - start) : chunk);
+        const int64_t start = e0 + (int64_t)c * chunk;
+        const int n_c = (int)((e1 - start) < chunk ? (e1 - start) : chunk);
         const int n4 = n_c & ~3;
         if (n4 > 0) {
             mbar_arrive_expect_tx(&R.bars[st], (uint32_t)n4 * 4u);
@@ -710,8 +717,8 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         const uint32_t y = ec >> 16;
         const uint32_t v1 = ec * (uint32_t)cl + y * sl2 + kql;   // = x c + y s + kq
         const uint32_t v2 = ec * (uint32_t)ch + y * sh2 + kqh;
-        red_add_shared_at(acc_slot + (v1 >> 16) * (kCols * 4), 1u);         // theta_lo
-        red_add_shared_at(acc_slot + (v2 >> 16) * (kCols * 4), 0x10000u);   // theta_hi
+        red_add_shared_at(acc_slot + (v1 >> 16) * (NC * 4), 1u);         // theta_lo
+        red_add_shared_at(acc_slot + (v2 >> 16) * (NC * 4), 0x10000u);   // theta_hi
     };
 
     // Warps stream the chunks without block barriers: lane 0 of each warp waits
@@ -732,11 +739,12 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
             if (lane == 0) atomicExch(&abort_flag, 1);
             break;
         }
-        const int64_t start = (int64_t)(c0 + c) * chunk;
-        const int n_c = (int)((E - start) < chunk ? (E - start) : chunk);
+        const int64_t start = e0 + (int64_t)c * chunk;
+        const int n_c = (int)((e1 - start) < chunk ? (e1 - start) : chunk);
         const int n4 = n_c & ~3;
-        const int G = n4 >> 2, Gh = (G + 1) >> 1;
-        const int g_lo = half ? Gh : 0, g_hi = half ? G : Gh;
+        // part `half` of the lanes takes the part-th of the chunk's 4-edge groups
+        const int G = n4 >> 2, Gh = (G + kParts - 1) / kParts;
+        const int g_lo = half * Gh, g_hi = min(G, g_lo + Gh);
         const uint4 *buf4 = reinterpret_cast<const uint4 *>(ring + st * chunk);
         for (int k = warp; k < Gh; k += kColWarps) {
             const int gi = g_lo + k;
@@ -748,7 +756,7 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
                 vote(q.w);
             }
         }
-        if (warp == kColWarps - 1 && half == 0)   // the chunk's last n_c % 4 edges
+        if (warp == kColWarps - 1 && half == 0)   // the last n_c % 4 edges (the frame's last chunk)
             for (int i = n4; i < n_c; ++i) vote(F.edges[start + i]);
         __syncwarp();
         if (lane == 0) {
@@ -777,9 +785,9 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         return kColAbort;
     }
     seq += (uint32_t)n_chunks;
-    if (np < kCols) {   // clear the spare columns (votes of the unused slots' lanes)
-        const int spare = kCols - np;
-        for (int i = tid; i < rows * spare; i += kColThreads) acc[(i / spare) * kCols + np + i % spare] = 0u;
+    if (np < NC) {   // clear the spare columns (votes of the unused slots' lanes)
+        const int spare = NC - np;
+        for (int i = tid; i < rows * spare; i += kColThreads) acc[(i / spare) * NC + np + i % spare] = 0u;
         __syncthreads();
     }
 
@@ -811,7 +819,7 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         __syncthreads();
     }
 
-    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, has0, tj, InterleavedLayout{wlo, whi, rows},
+    select_tile(L, F.cand + (size_t)tile * L.cand_m, acc, words, np, has0, tj, InterleavedLayout<NC>{wlo, whi, rows},
                 S, ring);
     return kColTile;
 }
@@ -851,8 +859,11 @@ __global__ void __launch_bounds__(kColThreads, 1) hough_cols_kernel(const __grid
         const int n_tiles = ub ? L.col_plan[3 * lo] : F.n_tiles;
         const int ns = ub ? L.col_plan[3 * lo + 1] : F.n_splits;
         const int sb = ub ? L.col_plan[3 * lo + 2] : F.split_base;
-        const int r = cols_unit(L, F, local / ns, local % ns, n_tiles, ns, sb, seq, smem_raw, R, S, abort_flag,
-                                piece_s, tile_j, win_lo, win_hi);
+        const int r = F.col_width == 8
+                          ? cols_unit<8>(L, F, local / ns, local % ns, n_tiles, ns, sb, seq, smem_raw, R, S,
+                                         abort_flag, piece_s, tile_j, win_lo, win_hi)
+                          : cols_unit<kCols>(L, F, local / ns, local % ns, n_tiles, ns, sb, seq, smem_raw, R, S,
+                                             abort_flag, piece_s, tile_j, win_lo, win_hi);
         if (r == kColAbort) break;
         if (r == kColTile) {
             __syncthreads();   // this tile's candidates are written
@@ -904,21 +915,26 @@ cudaError_t launch_hough(const HoughLaunch &L, int n_ctas, int pairs_max, int64_
     }
 }
 
-int hough_cols_max_rows() {
+int hough_cols_max_words() {
     const int avail = kSmemLimit - kStaticSmemReserve - kColRingMin;
-    return avail / (kCols * 4);
+    return avail / 4 / kCols * kCols;
 }
 
-int hough_cols_chunk(int rows_max) {
-    const int avail = kSmemLimit - kStaticSmemReserve - rows_max * kCols * 4;
+int hough_cols_max_rows(int width) { return hough_cols_max_words() / width; }
+
+int hough_cols_chunk(int words_max) {
+    const int avail = kSmemLimit - kStaticSmemReserve - words_max * 4;
     return avail >= kColStages * kColChunkMax * 4 ? kColChunkMax : kColChunkMin;
 }
 
-cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int rows_max, cudaStream_t s) {
+cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int words_max, cudaStream_t s) {
     if (n_ctas <= 0) return cudaSuccess;
-    if (rows_max < 1 || rows_max > hough_cols_max_rows() || (L.col_chunk != kColChunkMin && L.col_chunk != kColChunkMax))
+    if (words_max < 1 || words_max > hough_cols_max_words() ||
+        (L.col_chunk != kColChunkMin && L.col_chunk != kColChunkMax))
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kColStages * L.col_chunk * 4 + (size_t)rows_max * kCols * 4;
+    for (int i = 0; i < L.n; ++i)
+        if (L.f[i].col_width != 8 && L.f[i].col_width != kCols) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kColStages * L.col_chunk * 4 + (size_t)words_max * 4;
     if (smem > (size_t)(kSmemLimit - kStaticSmemReserve)) return cudaErrorInvalidValue;
     static std::atomic<uint64_t> attr_done{0};
     const cudaError_t e = once_per_device(attr_done, [](int) {

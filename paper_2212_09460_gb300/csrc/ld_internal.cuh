@@ -96,6 +96,8 @@ struct HoughFrame {
     int32_t rows;          // interleaved-column kernel: rows of the tile accumulator
     int32_t split_base;    // interleaved-column kernel, n_splits > 1: the frame's first tile
                            // in the launch's split-tile arrays (tile_cnt, part)
+    int32_t col_width;     // interleaved-column kernel: slots per tile (16, or 8 for long windows)
+    int32_t pad_;
 };
 
 struct HoughLaunch {
@@ -263,12 +265,16 @@ int hough_max_pairs(int n_rho);
 // frame's tiles may be split into n_splits edge ranges whose partial
 // accumulators meet in L.part.
 constexpr int kHoughColPairs = 16;
-// Largest `rows` that fits shared memory (with the smallest edge ring).
-int hough_cols_max_rows();
-// Edges per streamed chunk for an accumulator of rows_max rows (the largest
-// ring that fits).
-int hough_cols_chunk(int rows_max);
-cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int rows_max, cudaStream_t s);
+// Tiles of frames whose windows are too long for 16 slots use 8 slots (rows
+// twice as long), one per lane of a quarter-warp (HoughFrame::col_width).
+// Largest accumulator (rows x slots words) that fits shared memory with the
+// smallest edge ring, and the largest `rows` for a tile width.
+int hough_cols_max_words();
+int hough_cols_max_rows(int width);
+// Edges per streamed chunk for an accumulator of words_max words (the
+// largest ring that fits).
+int hough_cols_chunk(int words_max);
+cudaError_t launch_hough_cols(const HoughLaunch &L, int n_ctas, int words_max, cudaStream_t s);
 
 // Compiled tile sizes (theta pairs per CTA) of the voting kernel; a tile of
 // exactly one of these sizes runs without per-pair predicates.

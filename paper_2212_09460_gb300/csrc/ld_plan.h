@@ -25,7 +25,7 @@ constexpr int kMaxSplits = 8;
 // A launch with fewer tiles than SMs splits every tile (to fill the GPU) only
 // when its frames have at least this many pixels: below it a tile's edge
 // stream is too short to pay for a piece's partial store and merge.
-constexpr int64_t kSplitFillPixels = 1 << 19;
+constexpr int64_t kSplitFillPixels = 1 << 17;
 
 // D = ceil(sqrt(w^2 + h^2)): every rho of a w x h frame lies in [-D, D].
 inline int64_t rho_max_of(int64_t w, int64_t h) {
@@ -70,8 +70,9 @@ inline int window_rows(int w, int h, int n_theta, const std::vector<int32_t> &t)
 
 struct HoughPlan {
     int n_rho = 0, D = 0, pairs = 0, n_tiles = 0;
-    bool cols = false;   // interleaved-column kernel (tiles of <= kPlanColPairs pairs)
+    bool cols = false;   // interleaved-column kernel (tiles of <= width pairs)
     int rows = 0;        // its accumulator rows
+    int width = kPlanColPairs;   // its slots per tile: 16, or 8 when 16 x rows does not fit
 };
 
 // Fraction of the persistent CTAs' slots that `units` equal work units fill.

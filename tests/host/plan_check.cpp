@@ -109,7 +109,9 @@ int main() {
     CHECK(p.split_from == 0 && p.ns == 8 && p.split_tiles == 12);
     p = pieces(std::vector<int>(3, 12), 921600);     // three 720p frames: 36 tiles, 4 pieces
     CHECK(p.split_from == 0 && p.ns == 4 && p.split_tiles == 36);
-    p = pieces(std::vector<int>(1, 6), 307200);      // small frame: no split
+    p = pieces(std::vector<int>(1, 6), 307200);      // one 640x480 frame: 6 tiles in eighths
+    CHECK(p.split_from == 0 && p.ns == 8 && p.split_tiles == 6);
+    p = pieces(std::vector<int>(1, 6), 97 * 61);     // a tiny frame: no split
     CHECK(p.ns == 1 && p.split_from == 1 && p.split_tiles == 0);
     p = pieces(std::vector<int>(152, 1), 2073600);   // exactly one wave
     CHECK(p.ns == 1);

@@ -7,7 +7,8 @@ its frame, waits for the copies it issued itself and stops, so the call
 completes, the frames report LD_ERR_TIMEOUT, and the context stays usable:
 the next call with the default limit returns LD_OK and the oracle's peaks.
 Covers both voting kernels (the interleaved-column kernel for 1080p frames,
-the packed-pair kernel for min_votes 0 and for 4K frames).
+the packed-pair kernel for min_votes 0, and the 8-slot interleaved tiles of
+4K frames).
 """
 import numpy as np
 import pytest
@@ -24,9 +25,9 @@ def _run(c, ld, frames, p):
     return pk.cpu().numpy(), n.cpu().numpy(), st.cpu().numpy()
 
 
-@pytest.mark.parametrize("case", ["cols_1080p", "pairs_min_votes_0", "pairs_4k"])
+@pytest.mark.parametrize("case", ["cols_1080p", "pairs_min_votes_0", "cols8_4k"])
 def test_wait_timeout_reports_status_and_context_recovers(ldlib, ora, case):
-    if case == "pairs_4k":
+    if case == "cols8_4k":
         raw = [synth.road_frame(2080, 3840, 2160, synth.THROUGHPUT_1080P)]
         kw = dict(n_theta=360, top_k=4)
     else:

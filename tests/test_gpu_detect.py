@@ -155,7 +155,7 @@ def test_benchmark_config_uses_interleaved_kernel(ctx, ldlib):
     pairs, rows = ctx.plan(1920, 1080, p)
     assert pairs == -15 and rows in (1, 2, 4)
     pairs4k, _ = ctx.plan(3840, 2160, p)
-    assert pairs4k > 0   # 4K does not fit the interleaved accumulator
+    assert pairs4k == -8   # 4K windows take 8-slot interleaved tiles (16 x 4407 rows do not fit)
 
 
 # Split tiles: when a launch's last wave would be at most half full, the tiles
