@@ -176,18 +176,14 @@ __device__ void select_tile(const HoughLaunch &L, uint64_t *out, const uint32_t 
     // Fast path.  L = the M-th largest of the per-thread maxima: M distinct
     // cells have votes >= L, so every top-M cell does too.  The cells with
     // votes >= L ("survivors", usually a few hundred) are compacted as keys,
-    // which are unique and ordered like the peaks, and the first M keys of
-    // their descending sort are exactly the tile's top-M.  Too many
-    // survivors: the general path.
+    // which are unique and ordered like the peaks, and the M largest keys are
+    // exactly the tile's top-M: picked by rank (up to one survivor per
+    // thread) or by a descending sort.  Too many survivors: the general path.
     constexpr int kMaxSurv = 2048;
     if (total > M && M <= nthr) {
-        int *tm = reinterpret_cast<int *>(ring);
         uint64_t *keys = reinterpret_cast<uint64_t *>(ring + nthr);
-        tm[tid] = tmax;
         if (tid == 0) S.surv = 0;
-        __syncthreads();
-        block_sort_desc(tm, nthr);
-        const int Lth = tm[M - 1];
+        const int Lth = block_mth_largest(tmax, M, 16);   // counts are 16-bit
         if (Lth >= 0) {   // block-uniform
             for (int i = tid; i < words; i += nthr) {
                 const uint32_t wv = acc[i];
@@ -207,6 +203,10 @@ __device__ void select_tile(const HoughLaunch &L, uint64_t *out, const uint32_t 
             }
             __syncthreads();
             const int ns_ = S.surv;
+            if (ns_ <= nthr) {   // block-uniform
+                block_topm_by_rank(keys, ns_, M, out);
+                return;
+            }
             if (ns_ <= kMaxSurv) {   // block-uniform
                 int n2 = 1;
                 while (n2 < ns_) n2 <<= 1;

@@ -46,6 +46,37 @@ select_kernel(const __grid_constant__ SelectLaunch L) {
             umax = max(umax, u);
         }
     }
+    // Fast path: L = the M-th largest of the per-thread maxima (M distinct
+    // cells reach it, so every top-M cell does); the cells >= L, usually a few
+    // hundred, are compacted as unique keys and the M largest taken by rank.
+    // More survivors than the key buffer holds: the radix path below.
+    {
+        constexpr int kSurvKeys = 1024;
+        __shared__ uint64_t skeys[kSurvKeys];
+        __shared__ int n_surv;
+        if (tid == 0) n_surv = 0;
+        uint32_t Lu = 0;
+        if (block_mth_largest_u32(umax, cnt > 0, M, Lu)) {   // block-uniform
+            for (int i = tid; i < n; i += kSelectThreads) {
+                const int32_t v = a[i];
+                if (v >= mv && ((uint32_t)v ^ 0x80000000u) >= Lu) {
+                    const int slot = atomicAdd(&n_surv, 1);
+                    if (slot < kSurvKeys) {
+                        const int64_t li = c0 + i;
+                        const int th = (int)(li / J.n_rho), rh = (int)(li - (int64_t)th * J.n_rho);
+                        skeys[slot] = peak_key(v, th, rh);
+                    }
+                }
+            }
+            __syncthreads();
+            const int ns_ = n_surv;
+            if (ns_ <= kSurvKeys) {   // block-uniform
+                block_topm_by_rank(skeys, ns_, M, out);
+                return;
+            }
+        }
+        __syncthreads();
+    }
     const int total = block_sum(cnt, S);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -55,6 +55,46 @@ __device__ __forceinline__ void block_sort_desc(T *buf, int n) {
     }
 }
 
+// The M-th largest of one value per thread, for values below 2^nbits (a
+// thread without a value passes -1): the largest L >= 0 with at least M
+// threads holding a value >= L, fixed bit by bit from the top with block-wide
+// counts (the count of values >= L only falls as L grows); -1 if fewer than M
+// threads hold a value.  Every thread of the block must call it.
+__device__ __forceinline__ int block_mth_largest(int v, int M, int nbits) {
+    if (__syncthreads_count(v >= 0) < M) return -1;
+    int lo = 0;
+    for (int b = nbits - 1; b >= 0; --b) {
+        const int cand = lo | (1 << b);
+        if (__syncthreads_count(v >= cand) >= M) lo = cand;
+    }
+    return lo;
+}
+
+// The same over unsigned 32-bit values; `has` says whether the thread holds
+// one.  Returns false (no threshold) if fewer than M threads hold a value.
+__device__ __forceinline__ bool block_mth_largest_u32(uint32_t u, bool has, int M, uint32_t &L) {
+    if (__syncthreads_count(has) < M) return false;
+    uint32_t lo = 0;
+    for (int b = 31; b >= 0; --b) {
+        const uint32_t cand = lo | (1u << b);
+        if (__syncthreads_count(has && u >= cand) >= M) lo = cand;
+    }
+    L = lo;
+    return true;
+}
+
+// Exact top-M of n unique keys in shared memory by rank (the number of larger
+// keys): key i goes to out[rank_i] when rank_i < M, so out[0..min(n, M)) is
+// written in descending order.  Threads take keys tid, tid + blockDim.x, ...
+__device__ __forceinline__ void block_topm_by_rank(const uint64_t *keys, int n, int M, uint64_t *out) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t k = keys[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += keys[j] > k ? 1 : 0;
+        if (r < M) out[r] = k;
+    }
+}
+
 // Add the ballot counts of one warp-step to this warp's 16 digit counters
 // (kept by every lane in registers).
 __device__ __forceinline__ void ballot_digits(uint32_t (&wh)[16], bool m, uint32_t dig) {
