@@ -23,6 +23,7 @@
 // timeout flag and the CTA leaves after draining its own copies.
 #include "ld_internal.cuh"
 #include "ld_merge.cuh"
+#include "ld_plan.h"
 #include "ld_select.cuh"
 
 namespace ld {
@@ -805,16 +806,21 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         __syncthreads();
         if (!last_s) return kColPiece;   // block-uniform
         __threadfence();
+        // every 16-byte group gathers the other pieces' words in one pass (the
+        // loads are independent, so their latencies overlap)
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        for (int o = 0; o < ns; ++o) {
-            if (o == split) continue;
-            const uint4 *other = reinterpret_cast<const uint4 *>(L.part + (tile_ix * ns + o) * L.part_stride);
-            for (int i = tid; i < words / 4; i += kColThreads) {
-                const uint4 b = __ldcg(other + i);
-                uint4 a = acc4[i];
-                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                acc4[i] = a;
+        const uint4 *part4 = reinterpret_cast<const uint4 *>(L.part + tile_ix * ns * L.part_stride);
+        const int stride4 = L.part_stride / 4;
+        for (int i = tid; i < words / 4; i += kColThreads) {
+            uint4 a = acc4[i];
+#pragma unroll
+            for (int o = 0; o < kMaxSplits; ++o) {
+                if (o < ns && o != split) {
+                    const uint4 b = __ldcg(part4 + (size_t)o * stride4 + i);
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
             }
+            acc4[i] = a;
         }
         __syncthreads();
     }

@@ -48,16 +48,18 @@ struct SobelFrame {
     uint8_t *pool;         // nullable: 8x8 edge counts [ceil(h/8)][ceil(w/8)] (0..64)
     int64_t cap;
     int32_t w, h, pitch;
-    int32_t tile_begin;    // first CTA of this frame
+    int32_t tile_begin;    // first CTA of this frame (host bookkeeping)
     int32_t tiles_x;       // column strips (sobel_strips(w))
     int32_t pad_;
+    int64_t group_begin;   // first 8-row group of this frame in the launch (set by launch_sobel)
 };
 
 struct SobelLaunch {
     int32_t n;
     int32_t threshold;
     int32_t border;
-    int32_t groups;        // 8-row groups per warp task
+    int32_t groups;        // 8-row groups per warp task (host bookkeeping: caps the grid)
+    int64_t total_groups;  // set by launch_sobel
     SobelFrame f[kMaxLaunchFrames];
 };
 

@@ -43,6 +43,8 @@
 // several lanes.  A warp prefix sum and one atomic on the frame's counter give
 // each lane its slots; the lanes write their edges into per-warp staging slots
 // that the warp copies out with coalesced stores.
+#include <algorithm>
+
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -165,33 +167,14 @@ __device__ __forceinline__ uint32_t spread4(uint32_t nib) {
     return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
 }
 
+// One run of a warp: output rows [y0, y_last) (y0 a multiple of 8) of column
+// strip sx of frame F.
 template <bool BIN, bool POOL>
-__global__ void __launch_bounds__(kSobelThreads, 3)
-sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
-    // frame of this CTA (binary search over tile_begin)
-    const int t = blockIdx.x;
-    int lo = 0, hi = L.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.f[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-    }
-    const SobelFrame &F = L.f[lo];
-    const int local = t - F.tile_begin;
-    if (local == 0 && threadIdx.x == 0) {   // until the merge writes the frame's peaks
-        if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
-        if (F.npeaks_init) *F.npeaks_init = 0;
-    }
+__device__ __forceinline__ void sobel_run(const SobelLaunch &L, const SobelFrame &F, int sx, int y0, int y_last,
+                                          int warp, int lane, uint8_t *smem_dyn) {
     const uint8_t *const img = F.img;
-    const int w = F.w, h = F.h, pitch = F.pitch, strips = F.tiles_x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int run_rows = 8 * L.groups;
-    const int runs = (h + run_rows - 1) / run_rows;
-    const int task = local * kSobelWarps + warp;
-    if (task >= strips * runs) return;   // warp-uniform; no block barrier below
-    const int sx = task % strips, sy = task / strips;
+    const int w = F.w, h = F.h, pitch = F.pitch;
     const int xl = sx * kSobelStripW - 16 + 16 * lane;   // first pixel held by this lane
-    const int y0 = sy * run_rows;
-    const int y_last = min(h, y0 + run_rows);           // one past the last output row
     const int nb_lane = xl < 0 ? 0 : min(16, max(0, w - xl));   // bytes of a row this lane reads
 
     // output pixels of this lane: lanes 1..30, inside the image
@@ -208,7 +191,6 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
 
     // this lane's row slots ring_s[warp][k % kRing][lane * 16]: relative row k
     // is image row y0 - 1 + k; output row y0 + 8g + r needs k = 8g + r .. + 2
-    extern __shared__ __align__(16) uint8_t smem_dyn[];
     uint8_t(*ring_s)[kRing][512] = reinterpret_cast<uint8_t(*)[kRing][512]>(smem_dyn);
     uint32_t *const stage = reinterpret_cast<uint32_t *>(smem_dyn + kSobelWarps * kRing * 512) + warp * kStage;
     const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(&ring_s[warp][0][lane * 16]);
@@ -342,11 +324,59 @@ sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
     }
 }
 
+// Persistent warps: the launch's 8-row groups, ordered (frame, column strip,
+// group), are cut into one contiguous range per warp of the grid, so every
+// warp gets the same number of groups (to one) whatever the frame sizes; a
+// range runs down a strip and continues in the next strip or frame.
+template <bool BIN, bool POOL>
+__global__ void __launch_bounds__(kSobelThreads, 3)
+sobel_bin_edges_kernel(const __grid_constant__ SobelLaunch L) {
+    extern __shared__ __align__(16) uint8_t smem_dyn[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kSobelWarps, wid = (int64_t)blockIdx.x * kSobelWarps + warp;
+    int64_t r = L.total_groups * wid / nw;
+    const int64_t r1 = L.total_groups * (wid + 1) / nw;
+    while (r < r1) {   // warp-uniform
+        int lo = 0, hi = L.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.f[mid].group_begin <= r) lo = mid; else hi = mid - 1;
+        }
+        const SobelFrame &F = L.f[lo];
+        const int gps = (F.h + 7) >> 3;   // groups per strip
+        const int64_t local = r - F.group_begin;
+        const int sx = (int)(local / gps), g = (int)(local - (int64_t)sx * gps);
+        const int64_t left = r1 - r;
+        const int n = left < (int64_t)(gps - g) ? (int)left : gps - g;
+        if (local == 0 && lane == 0) {   // until the merge writes the frame's peaks
+            if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
+            if (F.npeaks_init) *F.npeaks_init = 0;
+        }
+        sobel_run<BIN, POOL>(L, F, sx, 8 * g, min(F.h, 8 * (g + n)), warp, lane, smem_dyn);
+        r += n;
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_sobel(const SobelLaunch &L, int n_ctas, cudaStream_t s) {
+cudaError_t launch_sobel(const SobelLaunch &Lin, int n_ctas, cudaStream_t s) {
     if (n_ctas <= 0) return cudaSuccess;
-    if (L.groups < 1 || L.groups > 64) return cudaErrorInvalidValue;
+    if (Lin.groups < 1 || Lin.groups > 64) return cudaErrorInvalidValue;
+    SobelLaunch L = Lin;   // the launch's group ranges (n_ctas, from the run length, caps the grid)
+    int64_t groups = 0;
+    for (int i = 0; i < L.n; ++i) {
+        L.f[i].group_begin = groups;
+        groups += (int64_t)sobel_strips(L.f[i].w) * ((L.f[i].h + 7) / 8);
+    }
+    L.total_groups = groups;
+    int dev = 0, sms = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+    const int64_t resident = (int64_t)sms * 3;                       // 3 CTAs of 8 warps per SM
+    const int64_t need = (groups + kSobelWarps - 1) / kSobelWarps;   // at least one group per warp
+    n_ctas = (int)std::min<int64_t>(std::min<int64_t>(need, resident), n_ctas);
+    if (n_ctas <= 0) return cudaSuccess;
     // the optional outputs are uniform over a launch (all frames or none)
     const bool bin = L.f[0].bin != nullptr, pool = L.f[0].pool != nullptr;
     for (int i = 1; i < L.n; ++i)
