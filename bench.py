@@ -282,7 +282,7 @@ def serving_run(seconds: float, rate_scale: float, workers: int = 3):
         st = srv.serve(seconds, rate_scale=rate_scale)
     finally:
         srv.close()
-    return {"seconds": seconds, "offered_frames_per_s": 8 * 30 * rate_scale, **serving.summarize(st)}
+    return {"seconds": seconds, "offered_frames_per_s": 8 * 30 * rate_scale, **serving.summarize(st, srv.admission)}
 
 
 def _oracle_detect(frame: np.ndarray) -> int:

@@ -113,9 +113,12 @@ class Admission:
     fraction of the offered bytes (frames/s x bytes); alloc(w, h) makes one
     slot's buffer.  An allocation that fails (MemoryError or RuntimeError,
     which covers the CUDA allocator's out-of-memory error) ends that size's
-    pool; a size with no slot raises AdmissionError."""
+    pool; a size with no slot raises AdmissionError.  The min_slots floor can
+    take the reservation past the budget: bytes_reserved and budget_bytes are
+    both kept, and the serving stats report them side by side."""
 
     def __init__(self, streams, budget_bytes: int, alloc, min_slots: int = 2):
+        self.budget_bytes = int(budget_bytes)
         sizes = sorted(set(map(tuple, streams)))
         offered = {s: sum(1 for t in streams if tuple(t) == s) * s[1] * pitch_of(s[0]) for s in sizes}
         total = sum(offered.values())
@@ -312,9 +315,12 @@ class Scheduler:
         return st
 
 
-def summarize(st: ServeStats) -> dict:
-    """Latency percentiles (ms, arrival -> peaks on the host) and throughput."""
+def summarize(st: ServeStats, adm: "Admission | None" = None) -> dict:
+    """Latency percentiles (ms, arrival -> peaks on the host) and throughput;
+    with adm, also the device bytes its slots reserve against its budget."""
     fr = st.frames
+    mem = {} if adm is None else {"bytes_reserved": adm.bytes_reserved, "budget_bytes": adm.budget_bytes,
+                                  "over_budget": adm.bytes_reserved > adm.budget_bytes}
     if not fr:
         return {"frames": 0}
     lat = np.array([(f.t_done - f.t_arrival) * 1e3 for f in fr])
@@ -334,7 +340,7 @@ def summarize(st: ServeStats) -> dict:
             "status_nonzero": int(sum(1 for f in fr if f.status != 0)),
             "max_loop_gap_ms": st.max_loop_gap_ms,
             "max_phase_ms": dict(st.max_phase_ms),
-            **_device_summary(st.batch_device_ms)}
+            **_device_summary(st.batch_device_ms), **mem}
 
 
 def _device_summary(bd: list) -> dict:
@@ -523,7 +529,7 @@ def main():
     srv = Server(workers=a.workers, max_batch=a.max_batch, use_proposal=not a.no_proposal)
     try:
         st = srv.serve(a.seconds, rate_scale=a.rate_scale)
-        print(json.dumps({"seconds": a.seconds, "rate_scale": a.rate_scale, **summarize(st)}))
+        print(json.dumps({"seconds": a.seconds, "rate_scale": a.rate_scale, **summarize(st, srv.admission)}))
     finally:
         srv.close()
 

@@ -179,8 +179,10 @@ def test_light_load_serves_every_frame_alone(ora):
     st, adm, ex = _serve(ora, arr)
     _check_served(ora, arr, st, adm, 8, 2)
     assert np.mean(st.batch_sizes) < 1.5                        # arrivals rarely coincide
-    s = summarize(st)
+    s = summarize(st, adm)
     assert s["frames"] == len(arr) and 0 < s["latency_ms_p50"] <= s["latency_ms_p99"] <= s["latency_ms_max"]
+    assert s["bytes_reserved"] == sum(adm.slots(z) * z[1] * pitch_of(z[0]) for z in adm.bufs)
+    assert s["budget_bytes"] == 1 << 20 and s["over_budget"] == (s["bytes_reserved"] > s["budget_bytes"])
     # stall attribution: the loop's longest gap and its longest call of each phase
     ph = s["max_phase_ms"]
     assert {"load", "poll", "submit", "idle"} <= set(ph) and ph["idle"] > 0
@@ -196,6 +198,7 @@ def test_heavy_load_batches_and_backpressure(ora):
     _check_served(ora, arr, st, adm, 4, 2)
     assert st.max_waiting > 0 and max(st.batch_sizes) == 4 and ex.max_concurrent == 2
     assert all(adm.slots(s) == 4 for s in adm.bufs)
+    assert summarize(st, adm)["over_budget"]   # the min_slots floor exceeds a zero budget, and says so
 
 
 def test_proposal_class_is_batched_apart_and_fallback_reported(ora):
