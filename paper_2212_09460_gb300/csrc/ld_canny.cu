@@ -12,12 +12,13 @@
 //      with M >= t_low that hold a strong pixel.
 //
 // Kernels:
-//   canny_nms_kernel     32 x 32 output tiles per CTA: the 40 x 40 input
-//                        patch, the 36 x 36 blur, the 34 x 34 magnitudes and
-//                        sectors live in shared memory; writes the class map
-//                        (0, 1 weak, 2 strong), parent[i] = i and strong[i] = 0.
-//   canny_union_kernel   one thread per pixel joins a candidate to its
-//                        candidate neighbours above and to the left (each
+//   canny_nms_kernel     stages 1-4 in one pass down a strip of rows per CTA
+//                        (one thread per column, a single barrier per row);
+//                        writes the class map (0, 1 weak, 2 strong) and, for
+//                        candidates only, parent[i] = i and strong[i] = 0.
+//   canny_union_kernel   a thread per 16 pixels of a row (one 16-byte read of
+//                        the classes) joins each candidate to its candidate
+//                        neighbours above and to the left (each
 //                        8-neighbour pair once) in a union-find forest: lock-free
 //                        linking of the larger root under the smaller with
 //                        atomicCAS (parent[i] <= i always, so finding a root
@@ -33,8 +34,6 @@
 namespace ld {
 namespace {
 
-constexpr int kTile = 32;
-constexpr int kCannyThreads = 256;
 constexpr int kPxThreads = 256;
 
 __device__ __forceinline__ int find_root(const int32_t *parent, int i) {
@@ -71,160 +70,298 @@ __device__ __forceinline__ int frame_of_tile(const CannyLaunch &L, int t) {
     return lo;
 }
 
-__device__ __forceinline__ int frame_of_px(const CannyLaunch &L, int64_t q) {
-    int lo = 0, hi = L.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.f[mid].px_begin <= q) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+// A CTA covers kRowsOut output columns and kStrip output rows of one frame
+// with one thread per column of its kRowsW-wide input window (x = X0 - 4 + c)
+// and walks down the rows.  Vertical neighbourhoods stay in registers (the
+// last five horizontal blur sums, the last three blurred rows); horizontal
+// ones go through shared memory rows.  The stages are skewed by one step so
+// that a step needs a single barrier: at step t (input row yi = Y0 - 4 + t)
+// a thread publishes the input pixel of row yi, the vertical Sobel parts of
+// row yi - 4 and the magnitude of row yi - 5, then after the barrier reads
+// them back to form the blur of row yi - 2 (-> Sobel parts of row yi - 3),
+// the magnitude and sector of row yi - 4, and the suppression of row yi - 6.
+// Shared rows are double-buffered (magnitudes: a ring of four) so that a
+// step's writes never meet the previous step's reads.
+constexpr int kRowsW = 128;
+constexpr int kRowsOut = kRowsW - 8;
+constexpr int kStrip = 64;
+
+__device__ __forceinline__ int load_px(const CannyFrame &F, int x, bool xin, int y) {
+    return (xin && y >= 0 && y < F.h) ? (int)F.img[(size_t)y * F.pitch + x] : 0;
 }
 
-__global__ void __launch_bounds__(kCannyThreads) canny_nms_kernel(const __grid_constant__ CannyLaunch L) {
-    constexpr int NI = kTile + 8, NG = kTile + 4, NM = kTile + 2;
-    __shared__ uint8_t I_s[NI][NI];
-    __shared__ int16_t H_s[NI][NG];   // horizontal binomial sums (<= 4080)
-    __shared__ uint8_t G_s[NG][NG];
-    __shared__ int16_t M_s[NM][NM];
-    __shared__ uint8_t S_s[NM][NM];
+__global__ void __launch_bounds__(kRowsW) canny_nms_kernel(const __grid_constant__ CannyLaunch L) {
+    __shared__ uint8_t Is[2][kRowsW + 4];    // input row, column c at [2 + c]
+    __shared__ uint32_t Vs[2][kRowsW + 2];   // Sobel parts, column c at [1 + c]
+    __shared__ int16_t Ms[4][kRowsW + 2];    // magnitude rows y at [y & 3], column c at [1 + c]
     const int fi = frame_of_tile(L, blockIdx.x);
     const CannyFrame &F = L.f[fi];
     const int local = blockIdx.x - F.tile_begin;
-    const int tiles_x = (F.w + kTile - 1) / kTile;
-    const int X0 = (local % tiles_x) * kTile, Y0 = (local / tiles_x) * kTile;
-    const int w = F.w, h = F.h, tid = threadIdx.x;
-    if (local == 0 && tid == 0) {   // until the merge writes the frame's peaks
+    const int w = F.w, h = F.h;
+    const int bxs = (w + kRowsOut - 1) / kRowsOut;
+    const int X0 = (local % bxs) * kRowsOut, Y0 = (local / bxs) * kStrip;
+    const int c = threadIdx.x, x = X0 - 4 + c;
+    const bool xin = x >= 0 && x < w;
+    const bool out_col = c >= 4 && c < kRowsW - 4 && x < w;
+    if (local == 0 && c == 0) {   // until the merge writes the frame's peaks
         if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
         if (F.npeaks_init) *F.npeaks_init = 0;
     }
-    // input patch, zero outside the image
-    for (int i = tid; i < NI * NI; i += kCannyThreads) {
-        const int r = i / NI, c = i % NI;
-        const int y = Y0 - 4 + r, x = X0 - 4 + c;
-        I_s[r][c] = (x >= 0 && y >= 0 && x < w && y < h) ? F.img[(size_t)y * F.pitch + x] : 0;
-    }
+    for (int i = c; i < 2 * (kRowsW + 4); i += kRowsW) (&Is[0][0])[i] = 0;
+    for (int i = c; i < 2 * (kRowsW + 2); i += kRowsW) (&Vs[0][0])[i] = 0;
+    for (int i = c; i < 4 * (kRowsW + 2); i += kRowsW) (&Ms[0][0])[i] = 0;
     __syncthreads();
-    for (int i = tid; i < NI * NG; i += kCannyThreads) {
-        const int r = i / NG, c = i % NG;
-        const uint8_t *row = I_s[r] + c;
-        H_s[r][c] = (int16_t)(row[0] + 4 * row[1] + 6 * row[2] + 4 * row[3] + row[4]);
-    }
-    __syncthreads();
-    for (int i = tid; i < NG * NG; i += kCannyThreads) {
-        const int r = i / NG, c = i % NG;
-        const int y = Y0 - 2 + r, x = X0 - 2 + c;
-        const int s = H_s[r][c] + 4 * H_s[r + 1][c] + 6 * H_s[r + 2][c] + 4 * H_s[r + 3][c] + H_s[r + 4][c];
-        G_s[r][c] = (x >= 0 && y >= 0 && x < w && y < h) ? (uint8_t)((s + 128) >> 8) : 0;
-    }
-    __syncthreads();
-    for (int i = tid; i < NM * NM; i += kCannyThreads) {
-        const int r = i / NM, c = i % NM;
-        const int y = Y0 - 1 + r, x = X0 - 1 + c;
+    const int yend = min(Y0 + kStrip, h);
+    const int T = yend - Y0 + 10;   // the last step suppresses row yend - 1
+    int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;   // horizontal blur sums, rows yi-4 .. yi
+    int g0 = 0, g1 = 0, g2 = 0;                    // blurred rows yi-4 .. yi-2
+    uint32_t vpend = 0;                            // Sobel parts awaiting publication
+    int mpend = 0, sc1 = 0, sc2 = 0;               // magnitude awaiting publication; sectors of the last two steps
+    int pf0 = load_px(F, x, xin, Y0 - 4), pf1 = load_px(F, x, xin, Y0 - 3);
+    for (int t = 0; t < T; ++t) {
+        const int yi = Y0 - 4 + t, b = t & 1;
+        const int cur = pf0;
+        pf0 = pf1;
+        pf1 = load_px(F, x, xin, yi + 2);
+        Is[b][2 + c] = (uint8_t)cur;
+        Vs[b][1 + c] = vpend;
+        Ms[(yi - 5) & 3][1 + c] = (int16_t)mpend;
+        __syncthreads();
+        // 5x5 binomial blur: horizontal sum of row yi, vertical over the last five
+        const uint8_t *q = Is[b] + c;   // columns c - 2 .. c + 2
+        const int hn = q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4];
+        h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = hn;
+        const int yg = yi - 2;
+        int gn = (h0 + 4 * h1 + 6 * h2 + 4 * h3 + h4 + 128) >> 8;
+        if (!xin || yg < 0 || yg >= h) gn = 0;
+        g0 = g1; g1 = g2; g2 = gn;
+        // Sobel parts of row yi - 3 at this column: smoothing G(y-1) + 2 G(y) + G(y+1)
+        // (low half) and difference G(y+1) - G(y-1) + 256 (high half)
+        vpend = (uint32_t)(g0 + 2 * g1 + g2) | ((uint32_t)(g2 - g0 + 256) << 16);
+        // magnitude and sector of row yi - 4 from the parts published this step
+        const uint32_t va = Vs[b][c], vb = Vs[b][c + 1], vc = Vs[b][c + 2];
+        const int gx = (int)(vc & 0xFFFFu) - (int)(va & 0xFFFFu);
+        const int gy = (int)(va >> 16) + 2 * (int)(vb >> 16) + (int)(vc >> 16) - 4 * 256;
+        const int ym = yi - 4;
         int m = 0, sc = 0;
-        if (x >= 0 && y >= 0 && x < w && y < h) {
-            const uint8_t *a = G_s[r] + c, *b = G_s[r + 1] + c, *d = G_s[r + 2] + c;   // rows y-1, y, y+1
-            const int gx = (a[2] + 2 * b[2] + d[2]) - (a[0] + 2 * b[0] + d[0]);
-            const int gy = (d[0] + 2 * d[1] + d[2]) - (a[0] + 2 * a[1] + a[2]);
-            const int64_t ax = gx < 0 ? -gx : gx, ay = gy < 0 ? -gy : gy;
-            m = (int)(ax + ay);
+        if (xin && ym >= 0 && ym < h) {
+            const int ax = abs(gx), ay = abs(gy);   // <= 1020: the products below fit 32 bits
+            m = ax + ay;
             if (ay * 65536 <= 27146 * ax) sc = 0;
             else if (ay * 65536 >= 158218 * ax) sc = 2;
             else sc = (gx > 0) == (gy > 0) ? 1 : 3;   // gx gy > 0 (neither is 0 here)
         }
-        M_s[r][c] = (int16_t)m;
-        S_s[r][c] = (uint8_t)sc;
-    }
-    __syncthreads();
-    for (int i = tid; i < kTile * kTile; i += kCannyThreads) {
-        const int r = i / kTile, c = i % kTile;
-        const int y = Y0 + r, x = X0 + c;
-        if (x >= w || y >= h) continue;
-        const int sc = S_s[r + 1][c + 1], m = M_s[r + 1][c + 1];
-        // (n1, n2) per sector: along x (x-1, x+1); (x-1,y-1), (x+1,y+1); along y; (x+1,y-1), (x-1,y+1)
-        const int dx1 = sc == 0 ? -1 : sc == 1 ? -1 : sc == 2 ? 0 : 1;
-        const int dy1 = sc == 0 ? 0 : -1;
-        const int m1 = M_s[r + 1 + dy1][c + 1 + dx1], m2 = M_s[r + 1 - dy1][c + 1 - dx1];
-        const bool keep = m > 0 && m > m1 && m >= m2;
-        const uint8_t cls = !keep ? 0 : (m >= L.t_high ? 2 : (m >= L.t_low ? 1 : 0));
-        const size_t p = (size_t)y * w + x;
-        F.cls[p] = cls;
-        F.parent[p] = (int32_t)p;
-        F.strong[p] = 0;
+        mpend = m;
+        // suppression of row yn = yi - 6 (sector from two steps ago), magnitude rows yn-1 .. yn+1
+        const int yn = yi - 6, scn = sc2;
+        sc2 = sc1;
+        sc1 = sc;
+        if (t >= 10 && out_col) {
+            // (n1, n2) per sector: along x (x-1, x+1); (x-1,y-1), (x+1,y+1); along y; (x+1,y-1), (x-1,y+1)
+            const int dx1 = scn == 0 ? -1 : scn == 1 ? -1 : scn == 2 ? 0 : 1;
+            const int dy1 = scn == 0 ? 0 : -1;
+            const int mc = Ms[yn & 3][1 + c];
+            const int m1 = Ms[(yn + dy1) & 3][1 + c + dx1], m2 = Ms[(yn - dy1) & 3][1 + c - dx1];
+            const bool keep = mc > 0 && mc > m1 && mc >= m2;
+            const uint8_t cls = !keep ? 0 : (mc >= L.t_high ? 2 : (mc >= L.t_low ? 1 : 0));
+            // the forest and the strong marks are initialised for candidates only
+            // (nothing else reads them)
+            const int p = yn * w + x;
+            F.cls[p] = cls;
+            if (cls) {
+                F.parent[p] = p;
+                F.strong[p] = 0;
+            }
+        }
     }
 }
 
+// Per-pixel kernels: a thread takes 16 consecutive pixels of a row (chunk
+// q of the launch: the frame by its first chunk, then the row and column).
+struct Chunk {
+    const CannyFrame *F;
+    int y, x0, n;   // pixels x0 .. x0 + n - 1 of row y
+    bool ok;
+};
+
+__device__ __forceinline__ Chunk chunk_of(const CannyLaunch &L, int64_t q) {
+    Chunk c;
+    c.ok = false;
+    if (q >= L.total_chunks) return c;
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.f[mid].chunk_begin <= q) lo = mid; else hi = mid - 1;
+    }
+    c.F = &L.f[lo];
+    const int cpr = (c.F->w + 15) >> 4;
+    const int64_t local = q - c.F->chunk_begin;
+    c.y = (int)(local / cpr);
+    c.x0 = (int)(local - (int64_t)c.y * cpr) * 16;
+    c.n = min(16, c.F->w - c.x0);
+    c.ok = true;
+    return c;
+}
+
+// The classes of a chunk's n <= 16 pixels as bit masks: bit i of *cand for a
+// candidate (weak or strong), of *strong for a strong pixel.
+__device__ __forceinline__ void load_cls16(const uint8_t *cls, int n, uint32_t *cand, uint32_t *strong) {
+    uint32_t v[4];
+    if (n == 16 && (reinterpret_cast<uintptr_t>(cls) & 15) == 0) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(cls));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (4 * k + b < n) word |= (uint32_t)cls[4 * k + b] << (8 * b);
+            v[k] = word;
+        }
+    }
+    uint32_t c = 0, st = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t byte = (v[k] >> (8 * b)) & 0xFFu;
+            c |= (byte != 0 ? 1u : 0u) << (4 * k + b);
+            st |= (byte == 2 ? 1u : 0u) << (4 * k + b);
+        }
+    *cand = c;
+    *strong = st;
+}
+
 __global__ void __launch_bounds__(kPxThreads) canny_union_kernel(const __grid_constant__ CannyLaunch L) {
-    const int64_t q = (int64_t)blockIdx.x * kPxThreads + threadIdx.x;
-    if (q >= L.total_px) return;
-    const CannyFrame &F = L.f[frame_of_px(L, q)];
-    const int p = (int)(q - F.px_begin);
-    if (!F.cls[p]) return;
-    const int w = F.w, x = p % w, y = p / w;
-    // the neighbours that come earlier in raster order: each 8-neighbour pair once
-    if (x > 0 && F.cls[p - 1]) unite(F.parent, p, p - 1);
-    if (y > 0) {
-        const int u = p - w;
-        if (x > 0 && F.cls[u - 1]) unite(F.parent, p, u - 1);
-        if (F.cls[u]) unite(F.parent, p, u);
-        if (x + 1 < w && F.cls[u + 1]) unite(F.parent, p, u + 1);
+    const Chunk c = chunk_of(L, (int64_t)blockIdx.x * kPxThreads + threadIdx.x);
+    if (!c.ok) return;
+    const CannyFrame &F = *c.F;
+    const int w = F.w;
+    const uint8_t *row = F.cls + (size_t)c.y * w + c.x0;
+    uint32_t cand, strong;
+    load_cls16(row, c.n, &cand, &strong);
+    // left neighbour of each pixel is a candidate (bit 0: the previous chunk's last pixel)
+    const uint32_t left = (cand << 1) | ((c.x0 > 0 && row[-1]) ? 1u : 0u);
+    uint32_t m = cand;
+    while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        const int x = c.x0 + i, p = c.y * w + x;
+        // the neighbours that come earlier in raster order: each 8-neighbour pair once
+        if ((left >> i) & 1u) unite(F.parent, p, p - 1);
+        if (c.y > 0) {
+            const int u = p - w;
+            if (x > 0 && F.cls[u - 1]) unite(F.parent, p, u - 1);
+            if (F.cls[u]) unite(F.parent, p, u);
+            if (x + 1 < w && F.cls[u + 1]) unite(F.parent, p, u + 1);
+        }
     }
 }
 
 __global__ void __launch_bounds__(kPxThreads) canny_flatten_kernel(const __grid_constant__ CannyLaunch L) {
-    const int64_t q = (int64_t)blockIdx.x * kPxThreads + threadIdx.x;
-    if (q >= L.total_px) return;
-    const CannyFrame &F = L.f[frame_of_px(L, q)];
-    const int p = (int)(q - F.px_begin);
-    const uint8_t c = F.cls[p];
-    if (!c) return;
-    const int r = find_root(F.parent, p);
-    F.parent[p] = r;
-    if (c == 2) F.strong[r] = 1;
+    const Chunk c = chunk_of(L, (int64_t)blockIdx.x * kPxThreads + threadIdx.x);
+    if (!c.ok) return;
+    const CannyFrame &F = *c.F;
+    uint32_t cand, strong;
+    load_cls16(F.cls + (size_t)c.y * F.w + c.x0, c.n, &cand, &strong);
+    uint32_t m = cand;
+    while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        const int p = c.y * F.w + c.x0 + i;
+        const int r = find_root(F.parent, p);
+        F.parent[p] = r;
+        if ((strong >> i) & 1u) F.strong[r] = 1;
+    }
 }
 
 __global__ void __launch_bounds__(kPxThreads) canny_emit_kernel(const __grid_constant__ CannyLaunch L) {
-    const int64_t q = (int64_t)blockIdx.x * kPxThreads + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    // frames are whole multiples of nothing in particular: a warp may straddle two
-    // frames, so the ballot is per frame (lanes of another frame vote false)
-    const bool in = q < L.total_px;
-    const int fi = in ? frame_of_px(L, q) : 0;
-    const CannyFrame &F = L.f[fi];
-    const int p = in ? (int)(q - F.px_begin) : 0;
-    bool edge = false;
-    int x = 0, y = 0;
-    if (in) {
-        x = p % F.w;
-        y = p / F.w;
-        edge = F.cls[p] && F.strong[__ldcg(F.parent + p)];
-        if (L.border == LD_BORDER_CLEAR && (x == 0 || y == 0 || x == F.w - 1 || y == F.h - 1)) edge = false;
-        if (F.bin) F.bin[(size_t)y * F.pitch + x] = edge ? 255 : 0;
+    const Chunk c = chunk_of(L, (int64_t)blockIdx.x * kPxThreads + threadIdx.x);
+    uint32_t mask = 0;
+    int fi = -1;
+    if (c.ok) {
+        const CannyFrame &F = *c.F;
+        fi = (int)(c.F - L.f);
+        uint32_t cand, strong;
+        load_cls16(F.cls + (size_t)c.y * F.w + c.x0, c.n, &cand, &strong);
+        while (cand) {
+            const int i = __ffs(cand) - 1;
+            cand &= cand - 1;
+            const int p = c.y * F.w + c.x0 + i;
+            if (F.strong[__ldcg(F.parent + p)]) mask |= 1u << i;
+        }
+        if (L.border == LD_BORDER_CLEAR) {
+            if (c.y == 0 || c.y == F.h - 1) mask = 0;
+            if (c.x0 == 0) mask &= ~1u;
+            const int xr = F.w - 1 - c.x0;
+            if (xr < 16) mask &= ~(1u << xr);
+        }
+        if (F.bin) {
+            uint8_t *b = F.bin + (size_t)c.y * F.pitch + c.x0;
+            if (c.n == 16) {   // a whole aligned chunk (pitch and buffer 16-byte aligned)
+                uint32_t v4[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t nib = (mask >> (4 * k)) & 0xFu;
+                    // spread the 4 bits to bytes of 0x00 / 0xFF
+                    v4[k] = ((nib & 1u) ? 0xFFu : 0u) | ((nib & 2u) ? 0xFF00u : 0u) |
+                            ((nib & 4u) ? 0xFF0000u : 0u) | ((nib & 8u) ? 0xFF000000u : 0u);
+                }
+                *reinterpret_cast<uint4 *>(b) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
+            } else {
+                for (int i = 0; i < c.n; ++i) b[i] = (mask >> i) & 1u ? 255 : 0;
+            }
+        }
     }
-    // one atomic per frame present in the warp
-    uint32_t pending = __ballot_sync(0xFFFFFFFFu, edge);
+    // one atomic per frame present in the warp, the lanes' edges in slot order
+    uint32_t pending = __ballot_sync(0xFFFFFFFFu, mask != 0);
     while (pending) {
         const int leader = __ffs(pending) - 1;
         const int lf = __shfl_sync(0xFFFFFFFFu, fi, leader);
-        const uint32_t mine = __ballot_sync(0xFFFFFFFFu, edge && fi == lf);
-        int base = 0;
-        if (lane == leader) base = atomicAdd(L.f[lf].count, __popc(mine));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (edge && fi == lf) {
-            const int64_t pos = (int64_t)base + __popc(mine & ((1u << lane) - 1u));
-            if (pos < F.cap) F.edges[pos] = ((uint32_t)y << 16) | (uint32_t)x;
+        const bool mine = mask != 0 && fi == lf;
+        const int cnt = mine ? __popc(mask) : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
         }
-        pending &= ~mine;
+        const int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        int base = 0;
+        if (lane == leader) base = atomicAdd(L.f[lf].count, tot);
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (mine) {
+            const CannyFrame &F = L.f[lf];
+            int64_t pos = (int64_t)base + incl - cnt;
+            uint32_t m = mask;
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                if (pos < F.cap) F.edges[pos] = ((uint32_t)c.y << 16) | (uint32_t)(c.x0 + i);
+                ++pos;
+            }
+        }
+        pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_canny(const CannyLaunch &L, int n_tiles, cudaStream_t s) {
-    if (L.n <= 0) return cudaSuccess;
-    canny_nms_kernel<<<n_tiles, kCannyThreads, 0, s>>>(L);
+cudaError_t launch_canny(const CannyLaunch &L0, int n_tiles, cudaStream_t s) {
+    if (L0.n <= 0) return cudaSuccess;
+    CannyLaunch L = L0;
+    int64_t chunks = 0;
+    for (int k = 0; k < L.n; ++k) {
+        L.f[k].chunk_begin = chunks;
+        chunks += (int64_t)L.f[k].h * ((L.f[k].w + 15) / 16);
+    }
+    L.total_chunks = chunks;
+    canny_nms_kernel<<<n_tiles, kRowsW, 0, s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (L.total_px + kPxThreads - 1) / kPxThreads;
+    const int64_t blocks = (L.total_chunks + kPxThreads - 1) / kPxThreads;
     if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
     canny_union_kernel<<<(int)blocks, kPxThreads, 0, s>>>(L);
     canny_flatten_kernel<<<(int)blocks, kPxThreads, 0, s>>>(L);
@@ -232,6 +369,6 @@ cudaError_t launch_canny(const CannyLaunch &L, int n_tiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int canny_tiles(int w, int h) { return ((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile); }
+int canny_tiles(int w, int h) { return ((w + kRowsOut - 1) / kRowsOut) * ((h + kStrip - 1) / kStrip); }
 
 }  // namespace ld

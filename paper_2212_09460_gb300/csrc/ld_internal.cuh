@@ -206,6 +206,7 @@ struct CannyFrame {
     uint8_t *strong;       // scratch [h][w]: root holds a strong pixel
     int64_t cap;
     int64_t px_begin;      // first pixel of this frame in the launch's pixel range
+    int64_t chunk_begin;   // first 16-pixel row chunk of this frame (set by launch_canny)
     int32_t w, h, pitch;
     int32_t tile_begin;    // first 32 x 32 tile of this frame
 };
@@ -213,6 +214,7 @@ struct CannyFrame {
 struct CannyLaunch {
     int32_t n, t_low, t_high, border;
     int64_t total_px;
+    int64_t total_chunks;  // set by launch_canny
     CannyFrame f[kMaxLaunchFrames];
 };
 
