@@ -43,9 +43,9 @@ METRIC = "1080p frames/s end-to-end, % of HBM roofline; proposal vs plain at equ
 # valid only while the kernel's sources hash to the recorded value (else null).
 MEASURED_TRAFFIC = {
     "hough": {"sources": ["ld_hough.cu", "ld_select.cuh", "ld_internal.cuh"],
-              "sha1": "e95ca3dc82afd1365b5e8ef5e88e228c7167a943", "bytes_per_frame": (41161472 + 1607168) / 64},
+              "sha1": "9665ce09fba7abc279227cbb3d251cc074f4b233", "bytes_per_frame": (41192960 + 1704448) / 64},
     "sobel": {"sources": ["ld_sobel.cu", "ld_internal.cuh"],
-              "sha1": "1c1e72fcae549c366c2f846bb511a375a06dcb0b", "bytes_per_frame": (132765696 + 22328320) / 64},
+              "sha1": "12598a0bc5c55ed67a71fb0f8b59187c1779cba2", "bytes_per_frame": (143040512 + 20419840) / 64},
 }
 
 
@@ -323,11 +323,14 @@ def oracle_stages(reps_by_px=((400_000, 5), (1_000_000, 3), (2_100_000, 3), (10*
     return out
 
 
-def next_rows(torch, ld, dev, frames, edges_total: float, flush, reps: int = 10) -> dict:
+def next_rows(torch, ld, dev, frames, edges_total: float, flush, hbm_peak: float, red_peak: float,
+              reps: int = 10) -> dict:
     """The other hot-path rows on the same 64 x 1080p batch (frames in HBM, L2
     flushed before each call): Hough lines after the peaks, Canny edges in place
     of Sobel, and Steps 1-3 fused without an edge list; plus one 640x480 frame
-    through the fused path (CUDA-graph replay)."""
+    through the fused path (CUDA-graph replay).  Each row carries a roofline of
+    its own first stage, timed by the library's stage events (hbm_peak in GB/s,
+    red_peak the measured conflict-free shared-reduction rate in Gred/s)."""
     p = ld.params(n_theta=N_THETA, top_k=TOP_K)
     lp = ld.lines_params()
     cp = ld.canny_params()
@@ -347,6 +350,16 @@ def next_rows(torch, ld, dev, frames, edges_total: float, flush, reps: int = 10)
             ms.append(a.elapsed_time(b))
         return float(np.median(ms))
 
+    def stage_ms(c, fn):
+        """Mean device ms of the call's two stages over the timed calls."""
+        ld.ld_ctx_enable_timing(c.handle, True)
+        ld.ld_ctx_stage_ms(c.handle)
+        ms = timed(fn)
+        a, b, n = ld.ld_ctx_stage_ms(c.handle)
+        ld.ld_ctx_enable_timing(c.handle, False)
+        return ms, a / max(n, 1), b / max(n, 1)
+
+    px = float(sum(int(f.shape[0]) * int(f.shape[1]) for f in frames))
     out = {}
     with ld.Context(dev.index) as c:
         prep = c.prepare(frames)
@@ -364,19 +377,39 @@ def next_rows(torch, ld, dev, frames, edges_total: float, flush, reps: int = 10)
                         f"{lp.min_length}", "ms_detect": base, "ms_detect_and_lines": lines_ms,
             "lines_ms": extra_ms, "segments_per_frame": float(nseg.sum().item()) / len(frames),
             "edge_list_reads_gbs": read_bytes / (extra_ms / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": "lines_kernel (one CTA per frame and peak)",
+                         "achieved": read_bytes / (extra_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": read_bytes / (extra_ms / 1e3) / 1e9 / hbm_peak, "traffic": None,
+                         "basis": "algorithmic bytes = 4 B per edge per peak (each CTA streams its frame's "
+                                  "edge list); time = detect+lines minus detect"},
             "note": "lines_ms = detect+lines minus detect; the edge lists are re-read from L2 by the 4 peaks of a frame"}
-        canny_ms = timed(lambda: c.detect_canny_batch(prep, p, cp, stream=s))
-        e = c.canny(frames[0], p, cp)
+        canny_ms, canny_s1, canny_s2 = stage_ms(c, lambda: c.detect_canny_batch(prep, p, cp, stream=s))
+        counts = [int(c.canny(f, p, cp).count.item()) for f in frames]
         torch.cuda.synchronize(dev)
+        canny_bytes = px + 4.0 * sum(counts)   # 1 B per pixel read, 4 B per edge written
         out["canny"] = {"workload": f"{len(frames)} x 1920x1080, Canny (t_low {cp.t_low}, t_high {cp.t_high}) in "
                                     f"place of Sobel, then the same vote and peaks",
                         "ms_per_batch": canny_ms, "frames_per_s": len(frames) / (canny_ms / 1e3),
-                        "edges_frame0": int(e.count.item())}
-        fused_ms = timed(lambda: c.detect_fused_batch(prep, p, stream=s))
+                        "stage_ms": {"canny": canny_s1, "hough_vote_and_peaks": canny_s2},
+                        "edges_per_frame_mean": sum(counts) / len(frames),
+                        "roofline": {"bound": "hbm", "kernel": "canny_nms/union/flatten/emit kernels (the Canny stage)",
+                                     "achieved": canny_bytes / (canny_s1 / 1e3) / 1e9, "peak": hbm_peak,
+                                     "unit": "GB/s", "frac": canny_bytes / (canny_s1 / 1e3) / 1e9 / hbm_peak,
+                                     "traffic": None,
+                                     "basis": "algorithmic bytes = 1 B per pixel read + 4 B per edge written"}}
+        fused_ms, fused_s1, fused_s2 = stage_ms(c, lambda: c.detect_fused_batch(prep, p, stream=s))
+        votes = edges_total * N_THETA
         out["fused"] = {"workload": f"{len(frames)} x 1920x1080, Steps 1-3 fused without an edge list "
                                     "(32x32 blocks vote into block accumulators, global int32 accumulators), "
                                     "then select + merge", "ms_per_batch": fused_ms,
-                        "frames_per_s": len(frames) / (fused_ms / 1e3), "two_stage_ms": base}
+                        "frames_per_s": len(frames) / (fused_ms / 1e3), "two_stage_ms": base,
+                        "stage_ms": {"fused_vote": fused_s1, "select_and_merge": fused_s2},
+                        "roofline": {"bound": "smem_atomic", "kernel": "fused_vote_kernel (with the accumulator clear)",
+                                     "achieved": votes / (fused_s1 / 1e3) / 1e9, "peak": red_peak,
+                                     "unit": "Gvote/s", "frac": votes / (fused_s1 / 1e3) / 1e9 / red_peak,
+                                     "traffic": None,
+                                     "basis": "E x n_theta votes over the measured conflict-free "
+                                              "shared-reduction rate"}}
     from paper_2212_09460_gb300 import synth
     p180 = ld.params(n_theta=180, top_k=2)
     one = [torch.from_numpy(synth.road_frame(0, 640, 480, synth.LATENCY_640x480)).to(dev)]
@@ -656,7 +689,8 @@ def main():
         if mixed_host is not None:
             extra["batching"], extra["latency_640x480"] = batching_and_latency(
                 torch, ld, dev, mixed_host, lambda: flush.fill_(7))
-            extra["next_rows"] = next_rows(torch, ld, dev, frame_list, e_sum, lambda: flush.fill_(5))
+            extra["next_rows"] = next_rows(torch, ld, dev, frame_list, e_sum, lambda: flush.fill_(5),
+                                           hbm_peak, red_rates["conflict_free"])
             extra["proposal"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9))
             # the configuration's literal fallback rule (max band probability < 0.9)
             extra["proposal_fallback_0.9"] = proposal_vs_plain(torch, ld, dev, lambda: flush.fill_(9),

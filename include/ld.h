@@ -375,13 +375,17 @@ LD_API ld_status ld_ctx_plan(ld_ctx *ctx, int32_t w, int32_t h, const ld_params 
 LD_API ld_status ld_ctx_set_wait_limit(ld_ctx *ctx, int64_t polls);
 
 /* Stage timing.  After ld_ctx_enable_timing(ctx, 1), every ld_detect_batch
- * call also records CUDA events on its stream around its launches: before
- * Steps 1-2, between Steps 1-2 and Steps 3-4 (the voting launch also merges
- * the peaks), and after Steps 3-4 (batches of more than 128 frames: the
- * first launch group).  ld_ctx_stage_ms waits for every call timed since its
- * previous use (at most 1024) and returns, summed over them, the device time
- * of Steps 1-2 (ms[0]) and Steps 3-4 (ms[1]) in milliseconds and the number
- * of calls in ms[2].  enable = 0 switches recording off. */
+ * call (and ld_detect_canny_batch, ld_detect_lines_batch and
+ * ld_detect_fused_batch) also records CUDA events on its stream around its
+ * launches: before Steps 1-2, between Steps 1-2 and Steps 3-4 (the voting
+ * launch also merges the peaks), and after Steps 3-4 (batches of more than
+ * 128 frames: the first launch group).  In ld_detect_fused_batch the first
+ * stage is Steps 1-3 (the accumulator clear and the fused vote) and the second
+ * Step 4; the segment search of ld_detect_lines_batch runs after the last
+ * event.  ld_ctx_stage_ms waits for every call timed since its previous use
+ * (at most 1024) and returns, summed over them, the device time of the first
+ * stage (ms[0]) and the second (ms[1]) in milliseconds and the number of calls
+ * in ms[2].  enable = 0 switches recording off. */
 LD_API ld_status ld_ctx_enable_timing(ld_ctx *ctx, int enable);
 LD_API ld_status ld_ctx_stage_ms(ld_ctx *ctx, float ms[3]);
 

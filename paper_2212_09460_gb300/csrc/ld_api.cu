@@ -610,6 +610,23 @@ ld_status ld_sobel_hough_fused(ld_ctx *ctx, const uint8_t *d_img, int32_t w, int
     return LD_OK;
 }
 
+// The stage events of a timed call's first launch group (3 per call), or
+// nullptr when timing is off, g0 is a later group or the record is full.
+static ld_status stage_events(ld_ctx *ctx, int g0, cudaEvent_t **tev) {
+    *tev = nullptr;
+    if (!ctx->timing || g0 != 0 || ctx->timed_calls >= kMaxTimedCalls) return LD_OK;
+    const size_t need = 3 * (size_t)(ctx->timed_calls + 1);
+    while (ctx->ev.size() < need) {
+        cudaEvent_t ne;
+        cudaError_t r = cudaEventCreate(&ne);
+        if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+        ctx->ev.push_back(ne);
+    }
+    *tev = &ctx->ev[3 * ctx->timed_calls];
+    ++ctx->timed_calls;
+    return LD_OK;
+}
+
 ld_status ld_detect_fused_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
                                 ld_peak *d_peaks, int32_t *d_n_peaks, int32_t *d_status, void *stream) {
     if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_fused_batch: NULL ctx");
@@ -655,6 +672,10 @@ ld_status ld_detect_fused_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n
         if (!ctx->cand.ensure((size_t)ccount * 8)) return fail(LD_ERR_NOMEM, "scratch candidates");
         int32_t *acc = (int32_t *)ctx->fused.p;
         uint64_t *cand = (uint64_t *)ctx->cand.p;
+        cudaEvent_t *tev = nullptr;
+        st = stage_events(ctx, g0, &tev);
+        if (st != LD_OK) return st;
+        if (tev) cudaEventRecord(tev[0], s);
         cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)acells * 4, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(acc)");
         FusedLaunch FL;
@@ -711,10 +732,12 @@ ld_status ld_detect_fused_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n
         }
         e = launch_fused_vote(FL, blocks, s);
         if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+        if (tev) cudaEventRecord(tev[1], s);
         e = launch_select(SL, chunks, s);
         if (e != cudaSuccess) return cuda_fail(e, "select launch");
         e = launch_merge(ML, s);
         if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        if (tev) cudaEventRecord(tev[2], s);
     }
     return LD_OK;
 }
@@ -1224,19 +1247,9 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
             st = build_launch(HLp, false, sub_p, sm.queue + 1, bp);
             if (st != LD_OK) return st;
         }
-        // stage events of this call (first launch group), 3 per timed call
         cudaEvent_t *tev = nullptr;
-        if (ctx->timing && g0 == 0 && ctx->timed_calls < kMaxTimedCalls) {
-            const size_t need = 3 * (size_t)(ctx->timed_calls + 1);
-            while (ctx->ev.size() < need) {
-                cudaEvent_t ne;
-                cudaError_t r = cudaEventCreate(&ne);
-                if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
-                ctx->ev.push_back(ne);
-            }
-            tev = &ctx->ev[3 * ctx->timed_calls];
-            ++ctx->timed_calls;
-        }
+        st = stage_events(ctx, g0, &tev);
+        if (st != LD_OK) return st;
         if (tev) cudaEventRecord(tev[0], s);
         if (canny) {   // Canny edges in place of Steps 1-2, into the same lists
             int64_t px = 0;
