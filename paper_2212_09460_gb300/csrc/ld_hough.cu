@@ -747,6 +747,7 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         const int G = n4 >> 2, Gh = (G + kParts - 1) / kParts;
         const int g_lo = half * Gh, g_hi = min(G, g_lo + Gh);
         const uint4 *buf4 = reinterpret_cast<const uint4 *>(ring + st * chunk);
+#pragma unroll 2
         for (int k = warp; k < Gh; k += kColWarps) {
             const int gi = g_lo + k;
             if (gi < g_hi) {
