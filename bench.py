@@ -10,9 +10,10 @@ over the whole batch (Steps 1-4 of the paper's pipeline).
 
 Prints one JSON line.  ``value`` is frames/s with the frames resident in HBM
 (device time from CUDA events on the launching stream, L2 flushed before
-every step); ``e2e`` is frames/s through the same C-ABI call from pinned host
-memory, with the host->device copy of the frames and the device->host copy
-of the peaks inside the timed region.  ``--impl reference`` times the CPU
+every step); ``e2e`` is frames/s through the C-ABI call on host buffers
+(ld_detect_batch_host) from pinned host memory, with the host->device copy
+of the frames and the device->host copy of the peaks inside the timed
+region.  ``--impl reference`` times the CPU
 oracle on a bounded sample of the same workload.  Under torchrun every rank
 processes its own 64-frame batch (weak scaling; frames are independent, so
 there is no collective on the data path).
@@ -558,7 +559,6 @@ def main():
     dev = torch.device("cuda", local_rank)
     frames_d = torch.from_numpy(host_frames).to(dev)                 # [64][1080][1920], pitch 1920
     frames_h = torch.from_numpy(host_frames).pin_memory()
-    frames_e2e = [torch.empty_like(frames_d) for _ in range(2)]   # double buffer for the e2e pipeline
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     p = ld.params(n_theta=N_THETA, top_k=TOP_K)
     ctx = ld.Context(local_rank)
@@ -569,7 +569,6 @@ def main():
            torch.zeros(nf, dtype=torch.int32, device=dev))
     frame_list = [frames_d[i] for i in range(nf)]
     views = ctx.prepare(frame_list)
-    views_e2e = [ctx.prepare([fb[i] for i in range(nf)]) for fb in frames_e2e]
     stream = torch.cuda.current_stream(dev)
     red_rates = smem_red_rates(torch, ld, dev, torch.cuda.get_device_properties(dev).multi_processor_count)
     ld.ld_ctx_enable_timing(ctx.handle, True)   # after the autotuner
@@ -612,35 +611,22 @@ def main():
     ld.ld_ctx_enable_timing(ctx.handle, False)
     stage_ms = np.array([s_sobel, s_hough]) / args.steps          # mean per step
 
-    # ---- end to end through the same call, from pinned host memory: every
-    # step copies its frames host -> device and its peaks back inside the timed
-    # window; the copy of step k+1 (copy stream, second buffer) overlaps the
-    # detection of step k (frames 133 MB > L2, so no flush is needed)
+    # ---- end to end through one C-ABI call on host buffers
+    # (ld_detect_batch_host): every step uploads its frames from pinned host
+    # memory and reads its peaks back inside the timed window; the library
+    # uploads step k+1 on its copy stream while step k is detected (two
+    # staging areas).  Frames (133 MB) exceed L2, so no flush is needed.
     peaks_h = torch.empty((nf, TOP_K, 3), dtype=torch.int32).pin_memory()
     npk_h = torch.empty(nf, dtype=torch.int32).pin_memory()
     st_h = torch.empty(nf, dtype=torch.int32).pin_memory()
+    host_views = ctx.prepare_host(frames_h)
     e2e_steps = max(4, args.steps)
-    copy_stream = torch.cuda.Stream(dev)
 
     def e2e_run(k_steps):
-        copied = [torch.cuda.Event() for _ in range(k_steps)]
-        computed = [torch.cuda.Event() for _ in range(k_steps)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        copy_stream.wait_event(t0)
-        for k in range(k_steps):
-            b = k & 1
-            with torch.cuda.stream(copy_stream):
-                if k >= 2:
-                    copy_stream.wait_event(computed[k - 2])   # buffer b is free again
-                frames_e2e[b].copy_(frames_h, non_blocking=True)
-                copied[k].record(copy_stream)
-            stream.wait_event(copied[k])
-            step(views_e2e[b])
-            peaks_h.copy_(out[0], non_blocking=True)
-            npk_h.copy_(out[1], non_blocking=True)
-            st_h.copy_(out[2], non_blocking=True)
-            computed[k].record(stream)
+        for _ in range(k_steps):
+            ctx.detect_batch_host(host_views, p, out=(peaks_h, npk_h, st_h), stream=stream, sync=False)
         t1.record(stream)
         torch.cuda.synchronize(dev)
         return t0.elapsed_time(t1)
@@ -648,6 +634,7 @@ def main():
     e2e_run(3)
     e2e_ms = e2e_run(e2e_steps) / e2e_steps
     assert int(st_h.abs().sum()) == 0 and bool((npk_h == TOP_K).all())
+    assert torch.equal(peaks_h, out[0].cpu()), "host-buffer call disagrees with the device call"
 
     # max over ranks
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
@@ -715,8 +702,9 @@ def main():
                 "e2e": {"value": e2e_val, "unit": "frames/s",
                         "h2d_bytes_per_step": int(frames_h.numel()),
                         "d2h_bytes_per_step": int(peaks_h.numel() * 4 + npk_h.numel() * 4 + st_h.numel() * 4),
-                        "pipeline": "host->device copy of step k+1 on a second stream overlaps the detection of "
-                                    "step k (two device frame buffers); timed from the first copy to the last "
+                        "api": "ld_detect_batch_host (frames and peaks in pinned host memory)",
+                        "pipeline": "the library uploads step k+1 on its copy stream while step k is detected "
+                                    "(two device staging areas); timed from the first upload to the last "
                                     "peaks read back"},
                 "gpu_launches": 2 * args.steps,
                 "clocks": clk.summary(),

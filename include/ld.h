@@ -177,8 +177,9 @@ LD_API ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_the
  * the worst case (every pixel an edge), so no capacity error can occur.
  * Step 3 runs in one of two voting kernels, per launch group of up to 128
  * frames: with min_votes >= 1, frames whose theta windows fit shared memory
- * (up to about 2560x1440) take the interleaved-column kernel, the others the
- * packed-pair kernel; a group with both kinds takes one launch per kernel
+ * in tiles of 16 or 8 theta pairs (windows up to about 6100 rows: every size
+ * up to 3840x2160 and beyond) take the interleaved-column kernel, the others
+ * the packed-pair kernel; a group with both kinds takes one launch per kernel
  * when each part fills the GPU, else the packed-pair kernel for all.  The
  * results never depend on the kernel, the tile sizes or the edge-range
  * splits.
@@ -186,6 +187,31 @@ LD_API ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_the
 LD_API ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
                           const ld_params *p, ld_peak *d_peaks,
                           int32_t *d_n_peaks, int32_t *d_status, void *stream);
+
+/*
+ * Steps 1-4 as ld_detect_batch for frames and results in HOST memory: the
+ * end-to-end call of a camera pipeline.
+ *   h_frames     host array of n frame descriptors whose img are HOST
+ *                pointers ([h][pitch] uint8, pitch a multiple of 16); page-
+ *                locked memory lets the upload overlap other work.
+ *   h_peaks      host ld_peak [n][top_k], h_n_peaks and h_status host int32
+ *                [n]: the outputs of ld_detect_batch, copied back.
+ * The call enqueues work and returns; the outputs are valid once `stream`'s
+ * work up to this call has completed (e.g. after cudaStreamSynchronize).
+ * The frames are copied (one cudaMemcpyAsync per run of frames adjacent in
+ * host memory) into one of two device staging areas owned by the context,
+ * used by alternate calls, on a copy stream of the context; detection waits
+ * for the upload on `stream`, and an upload waits for the outputs of the
+ * call before last (same area) to be read back.  So the upload of one call
+ * overlaps the detection of the previous one.  The host buffers must stay
+ * valid and unchanged until the call's work has completed.  An area grows
+ * (waiting for its previous call) when a call needs more room.  Not
+ * capturable in a CUDA graph (it uses the context's copy stream).  Argument
+ * errors are reported before anything is enqueued.
+ */
+LD_API ld_status ld_detect_batch_host(ld_ctx *ctx, const ld_frame *h_frames, int32_t n,
+                               const ld_params *p, ld_peak *h_peaks,
+                               int32_t *h_n_peaks, int32_t *h_status, void *stream);
 
 /*
  * Step 4 as ld_hough_peaks, for callers that may not allocate device memory.

@@ -98,6 +98,14 @@ struct ld_ctx {
     uint32_t wait_polls = kSpinLimit;      // consumer-side chunk waits of the voting kernels
     // (w, h, n_theta) -> rows of the interleaved-column accumulator
     mutable std::map<std::tuple<int, int, int>, int> col_rows;
+    // ld_detect_batch_host: two device staging areas (frames, then the outputs)
+    // used by alternate calls, the copy stream and, per area, the events that
+    // mark its frames copied and its outputs read back
+    DevBuf stage[2];
+    cudaStream_t hcopy = nullptr;
+    cudaEvent_t hev_copied[2] = {nullptr, nullptr}, hev_free[2] = {nullptr, nullptr};
+    bool hev_used[2] = {false, false};
+    uint64_t host_calls = 0;
     std::mutex mu;
 };
 
@@ -437,6 +445,13 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->part.release();
         ctx->canny.release();
         ctx->fused.release();
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->hev_free[b]) cudaEventSynchronize(ctx->hev_free[b]);
+            ctx->stage[b].release();
+            if (ctx->hev_copied[b]) cudaEventDestroy(ctx->hev_copied[b]);
+            if (ctx->hev_free[b]) cudaEventDestroy(ctx->hev_free[b]);
+        }
+        if (ctx->hcopy) cudaStreamDestroy(ctx->hcopy);
     }
     delete ctx;
     return LD_OK;
@@ -1006,6 +1021,88 @@ ld_status ld_detect_batch(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, cons
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
     return detect_impl(ctx, h_frames, n, p, d_peaks, d_n_peaks, d_status, (cudaStream_t)stream);
+}
+
+ld_status ld_detect_batch_host(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld_params *pp,
+                               ld_peak *h_peaks, int32_t *h_n_peaks, int32_t *h_status, void *stream) {
+    if (!ctx) return fail(LD_ERR_INVALID, "ld_detect_batch_host: NULL ctx");
+    ld_params p = pp ? *pp : defaults();
+    ld_status st = check_params(&p);
+    if (st != LD_OK) return st;
+    if (!h_frames || n < 1) return fail(LD_ERR_INVALID, "ld_detect_batch_host: need n >= 1 frames");
+    if (!h_peaks || !h_n_peaks || !h_status) return fail(LD_ERR_INVALID, "ld_detect_batch_host: NULL output");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(LD_ERR_CUDA, "cannot select device %d", ctx->device);
+    const int32_t *dt;
+    const std::vector<int32_t> *ht;
+    st = get_trig(ctx, p.n_theta, &dt, &ht);
+    if (st != LD_OK) return st;
+    // the staging area: frame i at off[i] (16-byte aligned), then the outputs
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const ld_frame &f = h_frames[i];
+        st = check_size(f.w, f.h, p, ht);
+        if (st != LD_OK) return fail(st, "frame %d: %s", i, g_err.c_str());
+        if (!f.img || f.pitch < f.w || (f.pitch & 15) || f.reserved != 0)
+            return fail(LD_ERR_INVALID, "frame %d: NULL image or bad pitch", i);
+        off[i] = total;
+        total += ((size_t)f.pitch * f.h + 15) / 16 * 16;
+    }
+    const size_t pk_bytes = (size_t)n * p.top_k * sizeof(ld_peak);
+    const size_t out_off = total, np_off = out_off + (pk_bytes + 15) / 16 * 16, st_off = np_off + (size_t)n * 4;
+    const size_t need = st_off + (size_t)n * 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->hcopy) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->hcopy, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&ctx->hev_copied[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->hev_free[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream / events");
+    }
+    const int b = (int)(ctx->host_calls & 1u);
+    DevBuf &stg = ctx->stage[b];
+    if (need > stg.bytes) {   // grow: the area's previous call must be done with it
+        cudaError_t e = ctx->hev_used[b] ? cudaEventSynchronize(ctx->hev_free[b]) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->hcopy);   // uploads of a call that failed later
+        if (e != cudaSuccess) return cuda_fail(e, "staging area in use");
+        if (!stg.ensure(need)) return fail(LD_ERR_NOMEM, "staging area of %zu bytes", need);
+    }
+    uint8_t *base = (uint8_t *)stg.p;
+    // frames: one copy per run of frames that are adjacent in host memory, on
+    // the copy stream, after the area's previous outputs were read back
+    cudaError_t e = cudaSuccess;
+    if (ctx->hev_used[b]) e = cudaStreamWaitEvent(ctx->hcopy, ctx->hev_free[b], 0);
+    for (int i = 0; i < n && e == cudaSuccess;) {
+        const uint8_t *src = h_frames[i].img;
+        size_t bytes = (size_t)h_frames[i].pitch * h_frames[i].h;
+        int j = i + 1;
+        while (j < n && h_frames[j].img == src + bytes && off[j] == off[i] + bytes) {
+            bytes += (size_t)h_frames[j].pitch * h_frames[j].h;
+            ++j;
+        }
+        e = cudaMemcpyAsync(base + off[i], src, bytes, cudaMemcpyHostToDevice, ctx->hcopy);
+        i = j;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->hev_copied[b], ctx->hcopy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->hev_copied[b], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "frame upload");
+    std::vector<ld_frame> dev(h_frames, h_frames + n);
+    for (int i = 0; i < n; ++i) dev[i].img = base + off[i];
+    ld_peak *d_pk = (ld_peak *)(base + out_off);
+    int32_t *d_np = (int32_t *)(base + np_off), *d_st = (int32_t *)(base + st_off);
+    st = detect_impl(ctx, dev.data(), n, p, d_pk, d_np, d_st, s);
+    if (st != LD_OK) return st;
+    e = cudaMemcpyAsync(h_peaks, d_pk, pk_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_n_peaks, d_np, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_status, d_st, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->hev_free[b], s);
+    if (e != cudaSuccess) return cuda_fail(e, "result download");
+    ctx->hev_used[b] = true;
+    ++ctx->host_calls;
+    return LD_OK;
 }
 
 }  // extern "C"

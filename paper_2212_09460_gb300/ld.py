@@ -97,6 +97,8 @@ _SIGS = {
     "ld_hough_peaks": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P],
     "ld_detect_batch": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P, _P,
                         _P],
+    "ld_detect_batch_host": [_P, ctypes.POINTER(ld_frame), ctypes.c_int32, ctypes.POINTER(ld_params), _P, _P,
+                             _P, _P],
     "ld_ctx_set_wait_limit": [_P, ctypes.c_int64],
     "ld_lines_params_default": [ctypes.POINTER(ld_lines_params)],
     "ld_sobel_hough_fused": [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ld_params),
@@ -231,6 +233,13 @@ def ld_detect_batch(ctx, frames, p, d_peaks, d_n_peaks, d_status, stream) -> Non
     """frames: sequence of (device_ptr, w, h, pitch), or a ctypes ld_frame array."""
     arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
     _check(load().ld_detect_batch(ctx, arr, len(arr), ctypes.byref(p), d_peaks, d_n_peaks, d_status, stream))
+
+
+def ld_detect_batch_host(ctx, frames, p, h_peaks, h_n_peaks, h_status, stream) -> None:
+    """frames: sequence of (host_ptr, w, h, pitch), or a ctypes ld_frame array;
+    outputs are host pointers, valid once the stream's work has completed."""
+    arr = frames if isinstance(frames, ctypes.Array) else _frames_array(frames)
+    _check(load().ld_detect_batch_host(ctx, arr, len(arr), ctypes.byref(p), h_peaks, h_n_peaks, h_status, stream))
 
 
 def ld_sobel_hough_fused(ctx, d_img, w, h, pitch, p, d_acc, stream) -> None:
@@ -682,6 +691,41 @@ class Context:
         ld_detect_lines_batch(self.handle, descs, p, lp, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
                               segs.data_ptr(), nseg.data_ptr(), sup.data_ptr(), _stream_handle(stream))
         return peaks, npk, st, segs, nseg, sup
+
+    @staticmethod
+    def _host_descs(frames, widths=None):
+        torch = _torch()
+        if isinstance(frames, torch.Tensor) and frames.dim() == 3:
+            frames = list(frames.unbind(0))
+        descs = []
+        for i, f in enumerate(frames):
+            if f.dtype != torch.uint8 or f.dim() != 2 or f.is_cuda or f.stride(1) != 1:
+                raise ValueError("host frames must be 2-D uint8 CPU tensors with unit column stride")
+            descs.append((f.data_ptr(), f.shape[1] if widths is None else widths[i], f.shape[0], f.stride(0)))
+        return descs
+
+    def detect_batch_host(self, frames, p: ld_params, widths=None, out=None, stream=None, sync: bool = True):
+        """Steps 1-4 on frames in host memory (a list of uint8 CPU tensors, or
+        one [n][h][pitch] tensor; pinned memory lets the upload overlap):
+        returns host (peaks [n][top_k][3], n_peaks [n], status [n]).  With
+        sync=False the outputs are valid only after the stream is synchronised,
+        and the frames must stay unchanged until then."""
+        torch = _torch()
+        descs = frames if isinstance(frames, ctypes.Array) else _frames_array(self._host_descs(frames, widths))
+        n = len(descs)
+        if out is None:
+            out = (torch.zeros((n, p.top_k, 3), dtype=torch.int32).pin_memory(),
+                   torch.zeros(n, dtype=torch.int32).pin_memory(), torch.zeros(n, dtype=torch.int32).pin_memory())
+        peaks, npk, st = out
+        ld_detect_batch_host(self.handle, descs, p, peaks.data_ptr(), npk.data_ptr(), st.data_ptr(),
+                             _stream_handle(stream))
+        if sync:
+            (stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", self.device))).synchronize()
+        return peaks, npk, st
+
+    def prepare_host(self, frames, widths=None):
+        """Frame descriptors of host frames, built once for repeated detect_batch_host calls."""
+        return _frames_array(self._host_descs(frames, widths))
 
     def detect_batch(self, frames, p: ld_params, widths=None, out=None, stream=None):
         """Steps 1-4 on a list of uint8 CUDA tensors (or a PreparedBatch);
