@@ -36,13 +36,22 @@ namespace {
 
 constexpr int kPxThreads = 256;
 
-__device__ __forceinline__ int find_root(const int32_t *parent, int i) {
-    int p = __ldcg(parent + i);
-    while (p != i) {
-        i = p;
-        p = __ldcg(parent + i);
+// Root of i's tree, halving the path on the way: a node that is not a root
+// is pointed at its grandparent.  A root is the smallest index of its tree
+// (links put the larger root under the smaller), and the halving writes are
+// minima with an ancestor, so a pointer only ever moves up its own tree and
+// never past the root: concurrent links, halvings and the flatten's writes
+// of roots all keep every node in its tree, and a root written by the
+// flatten stays.
+__device__ __forceinline__ int find_root(int32_t *parent, int i) {
+    for (;;) {
+        const int p = __ldcg(parent + i);
+        if (p == i) return i;
+        const int gp = __ldcg(parent + p);
+        if (gp == p) return p;
+        atomicMin(parent + i, gp);
+        i = gp;
     }
-    return i;
 }
 
 __device__ __forceinline__ void unite(int32_t *parent, int a, int b) {
