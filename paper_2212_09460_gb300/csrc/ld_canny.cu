@@ -13,7 +13,8 @@
 //
 // Kernels:
 //   canny_nms_kernel     stages 1-4 in one pass down a strip of rows per CTA
-//                        (one thread per column, a single barrier per row);
+//                        (two columns per thread as 16-bit lanes, a single
+//                        barrier per row);
 //                        writes the class map (0, 1 weak, 2 strong) and, for
 //                        candidates only, parent[i] = i and strong[i] = 0.
 //   canny_union_kernel   a thread per 16 pixels of a row (one 16-byte read of
@@ -79,107 +80,156 @@ __device__ __forceinline__ int frame_of_tile(const CannyLaunch &L, int t) {
     return lo;
 }
 
-// A CTA covers kRowsOut output columns and kStrip output rows of one frame
-// with one thread per column of its kRowsW-wide input window (x = X0 - 4 + c)
-// and walks down the rows.  Vertical neighbourhoods stay in registers (the
-// last five horizontal blur sums, the last three blurred rows); horizontal
-// ones go through shared memory rows.  The stages are skewed by one step so
-// that a step needs a single barrier: at step t (input row yi = Y0 - 4 + t)
-// a thread publishes the input pixel of row yi, the vertical Sobel parts of
-// row yi - 4 and the magnitude of row yi - 5, then after the barrier reads
-// them back to form the blur of row yi - 2 (-> Sobel parts of row yi - 3),
-// the magnitude and sector of row yi - 4, and the suppression of row yi - 6.
-// Shared rows are double-buffered (magnitudes: a ring of four) so that a
-// step's writes never meet the previous step's reads.
-constexpr int kRowsW = 128;
-constexpr int kRowsOut = kRowsW - 8;
+// A CTA of kRowsT threads covers kRowsOut output columns and kStrip output
+// rows of one frame and walks down the rows.  Thread t holds columns
+// x = X0 - 4 + 2t and x + 1 of the CTA's input window as the two 16-bit
+// lanes of a word (low: x, high: x + 1).  The horizontal blur sums (<= 4080),
+// the vertical blur sum with its rounding term (<= 65408), the Sobel
+// smoothing (<= 1020) and the biased differences stay below 2^16 and never
+// borrow, so one 32-bit add serves both columns.  Vertical neighbourhoods
+// stay in registers (the last five horizontal sums, the last three blurred
+// rows); horizontal ones go through shared-memory rows.  The stages are
+// skewed by one step so that a step needs a single barrier: at step t (input
+// row yi = Y0 - 4 + t) a thread publishes the input pair of row yi, the
+// vertical Sobel parts of row yi - 4 and the magnitudes of row yi - 5, then
+// after the barrier reads them back to form the blur of row yi - 2 (-> Sobel
+// parts of row yi - 3), the magnitudes and sectors of row yi - 4, and the
+// suppression of row yi - 6.  Shared rows are double-buffered (magnitudes: a
+// ring of four) so that a step's writes never meet the previous step's reads.
+constexpr int kRowsT = 128;
+constexpr int kRowsOut = 2 * kRowsT - 8;
 constexpr int kStrip = 64;
 
-__device__ __forceinline__ int load_px(const CannyFrame &F, int x, bool xin, int y) {
-    return (xin && y >= 0 && y < F.h) ? (int)F.img[(size_t)y * F.pitch + x] : 0;
+// Pixels (x, y) and (x + 1, y) as a 16-bit pair, zero outside the image (x
+// even: 2-byte aligned, as the image and its pitch are 16-byte aligned).
+__device__ __forceinline__ uint32_t load_pair(const CannyFrame &F, int x, int y) {
+    if (y < 0 || y >= F.h || x < 0 || x >= F.w) return 0u;   // x even: x < 0 also puts x + 1 outside
+    const uint8_t *q = F.img + (size_t)y * F.pitch + x;
+    return x + 1 < F.w ? (uint32_t)*reinterpret_cast<const uint16_t *>(q) : (uint32_t)q[0];
 }
 
-__global__ void __launch_bounds__(kRowsW) canny_nms_kernel(const __grid_constant__ CannyLaunch L) {
-    __shared__ uint8_t Is[2][kRowsW + 4];    // input row, column c at [2 + c]
-    __shared__ uint32_t Vs[2][kRowsW + 2];   // Sobel parts, column c at [1 + c]
-    __shared__ int16_t Ms[4][kRowsW + 2];    // magnitude rows y at [y & 3], column c at [1 + c]
+// |gx| + |gy| from the biased Sobel sums (0 outside the image).
+__device__ __forceinline__ int magnitude(uint32_t gxb, uint32_t gyb, bool inside) {
+    return inside ? abs((int)gxb - 1024) + abs((int)gyb - 1024) : 0;
+}
+
+// Direction sector of a pixel from its biased Sobel sums: 0 along x, 2 along
+// y, 1 and 3 the diagonals (gx gy > 0 and < 0).
+__device__ __forceinline__ int sector(uint32_t gxb, uint32_t gyb) {
+    const int gx = (int)gxb - 1024, gy = (int)gyb - 1024;
+    const int ax = abs(gx), ay = abs(gy);   // <= 1020: the products below fit 32 bits
+    if (ay * 65536 <= 27146 * ax) return 0;
+    if (ay * 65536 >= 158218 * ax) return 2;
+    return (gx > 0) == (gy > 0) ? 1 : 3;   // gx gy > 0 (neither is 0 here)
+}
+
+__global__ void __launch_bounds__(kRowsT) canny_nms_kernel(const __grid_constant__ CannyLaunch L) {
+    __shared__ uint32_t Is[2][kRowsT + 2];    // input pairs, thread t at [1 + t]
+    __shared__ uint32_t Vss[2][kRowsT + 2];   // smoothing pairs G(y-1) + 2 G(y) + G(y+1)
+    __shared__ uint32_t Vds[2][kRowsT + 2];   // difference pairs G(y+1) - G(y-1) + 256
+    __shared__ uint32_t Ms[4][kRowsT + 2];    // magnitude pairs of row y at [y & 3]
     const int fi = frame_of_tile(L, blockIdx.x);
     const CannyFrame &F = L.f[fi];
     const int local = blockIdx.x - F.tile_begin;
     const int w = F.w, h = F.h;
     const int bxs = (w + kRowsOut - 1) / kRowsOut;
     const int X0 = (local % bxs) * kRowsOut, Y0 = (local / bxs) * kStrip;
-    const int c = threadIdx.x, x = X0 - 4 + c;
-    const bool xin = x >= 0 && x < w;
-    const bool out_col = c >= 4 && c < kRowsW - 4 && x < w;
-    if (local == 0 && c == 0) {   // until the merge writes the frame's peaks
+    const int t = threadIdx.x, x = X0 - 4 + 2 * t;
+    const bool in0 = x >= 0 && x < w, in1 = x + 1 >= 0 && x + 1 < w;
+    const uint32_t colmask = (in0 ? 0x0000FFFFu : 0u) | (in1 ? 0xFFFF0000u : 0u);
+    // output columns: window columns 4 .. 2 kRowsT - 5, inside the image
+    const bool out0 = t >= 2 && t < kRowsT - 2 && in0;
+    const bool out1 = t >= 2 && t < kRowsT - 2 && in1;
+    if (local == 0 && t == 0) {   // until the merge writes the frame's peaks
         if (F.status_init) *F.status_init = LD_ERR_TIMEOUT;
         if (F.npeaks_init) *F.npeaks_init = 0;
     }
-    for (int i = c; i < 2 * (kRowsW + 4); i += kRowsW) (&Is[0][0])[i] = 0;
-    for (int i = c; i < 2 * (kRowsW + 2); i += kRowsW) (&Vs[0][0])[i] = 0;
-    for (int i = c; i < 4 * (kRowsW + 2); i += kRowsW) (&Ms[0][0])[i] = 0;
+    for (int i = t; i < 2 * (kRowsT + 2); i += kRowsT) {
+        (&Is[0][0])[i] = 0u;
+        (&Vss[0][0])[i] = 0u;
+        (&Vds[0][0])[i] = 0u;
+    }
+    for (int i = t; i < 4 * (kRowsT + 2); i += kRowsT) (&Ms[0][0])[i] = 0u;
     __syncthreads();
     const int yend = min(Y0 + kStrip, h);
     const int T = yend - Y0 + 10;   // the last step suppresses row yend - 1
-    int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;   // horizontal blur sums, rows yi-4 .. yi
-    int g0 = 0, g1 = 0, g2 = 0;                    // blurred rows yi-4 .. yi-2
-    uint32_t vpend = 0;                            // Sobel parts awaiting publication
-    int mpend = 0, sc1 = 0, sc2 = 0;               // magnitude awaiting publication; sectors of the last two steps
-    int pf0 = load_px(F, x, xin, Y0 - 4), pf1 = load_px(F, x, xin, Y0 - 3);
-    for (int t = 0; t < T; ++t) {
-        const int yi = Y0 - 4 + t, b = t & 1;
-        const int cur = pf0;
+    uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;   // horizontal blur pairs, rows yi-4 .. yi
+    uint32_t g0 = 0, g1 = 0, g2 = 0;                    // blurred pairs, rows yi-4 .. yi-2
+    uint32_t vs_pend = 0, vd_pend = 0, m_pend = 0;      // awaiting publication
+    uint32_t gx1 = 0, gy1 = 0, gx2 = 0, gy2 = 0;        // biased Sobel sums of the last two steps
+    uint32_t pf0 = load_pair(F, x, Y0 - 4), pf1 = load_pair(F, x, Y0 - 3);
+    for (int s = 0; s < T; ++s) {
+        const int yi = Y0 - 4 + s, b = s & 1;
+        const uint32_t cur = pf0;
         pf0 = pf1;
-        pf1 = load_px(F, x, xin, yi + 2);
-        Is[b][2 + c] = (uint8_t)cur;
-        Vs[b][1 + c] = vpend;
-        Ms[(yi - 5) & 3][1 + c] = (int16_t)mpend;
+        pf1 = load_pair(F, x, yi + 2);
+        Is[b][1 + t] = cur;
+        Vss[b][1 + t] = vs_pend;
+        Vds[b][1 + t] = vd_pend;
+        Ms[(yi - 5) & 3][1 + t] = m_pend;
         __syncthreads();
-        // 5x5 binomial blur: horizontal sum of row yi, vertical over the last five
-        const uint8_t *q = Is[b] + c;   // columns c - 2 .. c + 2
-        const int hn = q[0] + 4 * q[1] + 6 * q[2] + 4 * q[3] + q[4];
-        h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = hn;
+        // 5x5 binomial blur: horizontal sums of row yi from columns x-2 .. x+3
+        const uint32_t xw = Is[b][t] | (Is[b][1 + t] << 16);   // I(x-2), I(x-1), I(x), I(x+1)
+        const uint32_t rg = Is[b][2 + t];                        // I(x+2), I(x+3)
+        const uint32_t A = __byte_perm(xw, 0u, 0x4140);   // [I(x-2), I(x-1)]
+        const uint32_t B = __byte_perm(xw, 0u, 0x4241);   // [I(x-1), I(x)]
+        const uint32_t C = __byte_perm(xw, 0u, 0x4342);   // [I(x),   I(x+1)]
+        const uint32_t D = __byte_perm(xw, rg, 0x6463);   // [I(x+1), I(x+2)]
+        const uint32_t E = __byte_perm(rg, 0u, 0x4140);   // [I(x+2), I(x+3)]
+        h0 = h1; h1 = h2; h2 = h3; h3 = h4;
+        h4 = A + E + 4u * (B + D) + 6u * C;
         const int yg = yi - 2;
-        int gn = (h0 + 4 * h1 + 6 * h2 + 4 * h3 + h4 + 128) >> 8;
-        if (!xin || yg < 0 || yg >= h) gn = 0;
-        g0 = g1; g1 = g2; g2 = gn;
-        // Sobel parts of row yi - 3 at this column: smoothing G(y-1) + 2 G(y) + G(y+1)
-        // (low half) and difference G(y+1) - G(y-1) + 256 (high half)
-        vpend = (uint32_t)(g0 + 2 * g1 + g2) | ((uint32_t)(g2 - g0 + 256) << 16);
-        // magnitude and sector of row yi - 4 from the parts published this step
-        const uint32_t va = Vs[b][c], vb = Vs[b][c + 1], vc = Vs[b][c + 2];
-        const int gx = (int)(vc & 0xFFFFu) - (int)(va & 0xFFFFu);
-        const int gy = (int)(va >> 16) + 2 * (int)(vb >> 16) + (int)(vc >> 16) - 4 * 256;
+        uint32_t g = ((h0 + h4 + 0x00800080u + 4u * (h1 + h3) + 6u * h2) >> 8) & 0x00FF00FFu;
+        if (yg < 0 || yg >= h) g = 0u;
+        g &= colmask;
+        g0 = g1; g1 = g2; g2 = g;
+        vs_pend = g0 + 2u * g1 + g2;
+        vd_pend = g2 + 0x01000100u - g0;
+        // magnitudes and sectors of row yi - 4 from the parts published this step
+        const uint32_t so = Vss[b][1 + t], dd = Vds[b][1 + t];
+        const uint32_t sr1 = __byte_perm(so, Vss[b][2 + t], 0x5432);   // [Vs(x+1), Vs(x+2)]
+        const uint32_t sl1 = __byte_perm(Vss[b][t], so, 0x5432);       // [Vs(x-1), Vs(x)]
+        const uint32_t dr1 = __byte_perm(dd, Vds[b][2 + t], 0x5432);
+        const uint32_t dl1 = __byte_perm(Vds[b][t], dd, 0x5432);
+        const uint32_t gxb = sr1 + 0x04000400u - sl1;   // gx + 1024 per lane
+        const uint32_t gyb = dl1 + 2u * dd + dr1;      // gy + 1024 per lane (each part carries 256)
         const int ym = yi - 4;
-        int m = 0, sc = 0;
-        if (xin && ym >= 0 && ym < h) {
-            const int ax = abs(gx), ay = abs(gy);   // <= 1020: the products below fit 32 bits
-            m = ax + ay;
-            if (ay * 65536 <= 27146 * ax) sc = 0;
-            else if (ay * 65536 >= 158218 * ax) sc = 2;
-            else sc = (gx > 0) == (gy > 0) ? 1 : 3;   // gx gy > 0 (neither is 0 here)
-        }
-        mpend = m;
-        // suppression of row yn = yi - 6 (sector from two steps ago), magnitude rows yn-1 .. yn+1
-        const int yn = yi - 6, scn = sc2;
-        sc2 = sc1;
-        sc1 = sc;
-        if (t >= 10 && out_col) {
-            // (n1, n2) per sector: along x (x-1, x+1); (x-1,y-1), (x+1,y+1); along y; (x+1,y-1), (x-1,y+1)
-            const int dx1 = scn == 0 ? -1 : scn == 1 ? -1 : scn == 2 ? 0 : 1;
-            const int dy1 = scn == 0 ? 0 : -1;
-            const int mc = Ms[yn & 3][1 + c];
-            const int m1 = Ms[(yn + dy1) & 3][1 + c + dx1], m2 = Ms[(yn - dy1) & 3][1 + c - dx1];
-            const bool keep = mc > 0 && mc > m1 && mc >= m2;
-            const uint8_t cls = !keep ? 0 : (mc >= L.t_high ? 2 : (mc >= L.t_low ? 1 : 0));
-            // the forest and the strong marks are initialised for candidates only
-            // (nothing else reads them)
-            const int p = yn * w + x;
-            F.cls[p] = cls;
-            if (cls) {
-                F.parent[p] = p;
-                F.strong[p] = 0;
+        const bool yok = ym >= 0 && ym < h;
+        m_pend = (uint32_t)magnitude(gxb & 0xFFFFu, gyb & 0xFFFFu, in0 && yok) |
+                 ((uint32_t)magnitude(gxb >> 16, gyb >> 16, in1 && yok) << 16);
+        // suppression of row yn = yi - 6 (its Sobel sums from two steps ago),
+        // magnitude rows yn-1 .. yn+1; a pixel below t_low is never an edge
+        const int yn = yi - 6;
+        const uint32_t gxn = gx2, gyn = gy2;
+        gx2 = gx1;
+        gy2 = gy1;
+        gx1 = gxb;
+        gy1 = gyb;
+        if (s >= 10) {
+            const uint32_t mcp = Ms[yn & 3][1 + t];
+            const size_t prow = (size_t)yn * w + x;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!(k == 0 ? out0 : out1)) continue;
+                const int mc = (int)((mcp >> (16 * k)) & 0xFFFFu);
+                uint8_t cls = 0;
+                if (mc >= L.t_low) {
+                    const int sc = sector((gxn >> (16 * k)) & 0xFFFFu, (gyn >> (16 * k)) & 0xFFFFu);
+                    const int col = 2 + 2 * t + k;   // 16-bit index in a row of Ms
+                    // (n1, n2) per sector: along x (x-1, x+1); (x-1,y-1), (x+1,y+1); along y; (x+1,y-1), (x-1,y+1)
+                    const int dx1 = sc == 0 ? -1 : sc == 1 ? -1 : sc == 2 ? 0 : 1;
+                    const int dy1 = sc == 0 ? 0 : -1;
+                    const int m1n = reinterpret_cast<const uint16_t *>(Ms[(yn + dy1) & 3])[col + dx1];
+                    const int m2n = reinterpret_cast<const uint16_t *>(Ms[(yn - dy1) & 3])[col - dx1];
+                    if (mc > m1n && mc >= m2n) cls = mc >= L.t_high ? 2 : 1;   // mc >= t_low >= 1 > 0
+                }
+                F.cls[prow + k] = cls;
+                // the forest and the strong marks are initialised for candidates
+                // only (nothing else reads them)
+                if (cls) {
+                    F.parent[prow + k] = (int32_t)(prow + k);
+                    F.strong[prow + k] = 0;
+                }
             }
         }
     }
@@ -367,7 +417,7 @@ cudaError_t launch_canny(const CannyLaunch &L0, int n_tiles, cudaStream_t s) {
         chunks += (int64_t)L.f[k].h * ((L.f[k].w + 15) / 16);
     }
     L.total_chunks = chunks;
-    canny_nms_kernel<<<n_tiles, kRowsW, 0, s>>>(L);
+    canny_nms_kernel<<<n_tiles, kRowsT, 0, s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t blocks = (L.total_chunks + kPxThreads - 1) / kPxThreads;
