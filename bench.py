@@ -528,12 +528,17 @@ def main():
                     help="length of the 8-camera serving run at the nominal 30 frames/s per camera (0: skip)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames per GPU (the workload is 64; smaller values are for profiling captures)")
+    ap.add_argument("--next-rows-only", action="store_true",
+                    help="measure only the Hough-lines, Canny and fused rows (one JSON line; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     nf = args.frames
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.next_rows_only:
+        run_next_rows_only(nf)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -713,6 +718,33 @@ def main():
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_next_rows_only(nf: int) -> None:
+    """The next_rows measurements alone on the 64 x 1080p batch (one GPU), inside
+    an NVTX range "rows" for profilers; prints {"next_rows": ...}."""
+    host_frames = make_frames(rank_seeds(0, nf))
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_09460_gb300 import ld
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    frames_d = torch.from_numpy(host_frames).to(dev)
+    frame_list = [frames_d[i] for i in range(nf)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    p = ld.params(n_theta=N_THETA, top_k=TOP_K)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = float(json.load(open(peaks_path)).get("hbm_gbs", 6800.0)) if os.path.exists(peaks_path) else 6800.0
+    with ld.Context(0) as ctx:
+        e_sum = edge_count_total(ctx, frame_list, p, dev)
+    red = smem_red_rates(torch, ld, dev, torch.cuda.get_device_properties(dev).multi_processor_count)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push("rows")
+    rows = next_rows(torch, ld, dev, frame_list, e_sum, lambda: flush.fill_(5), hbm_peak, red["conflict_free"])
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"next_rows": rows, "hbm_peak_gbs": hbm_peak}), flush=True)
 
 
 def edge_count_total(ctx, views, p, dev) -> float:
