@@ -708,6 +708,9 @@ def main():
                         "h2d_bytes_per_step": int(frames_h.numel()),
                         "d2h_bytes_per_step": int(peaks_h.numel() * 4 + npk_h.numel() * 4 + st_h.numel() * 4),
                         "api": "ld_detect_batch_host (frames and peaks in pinned host memory)",
+                        "ms_per_step": e2e_ms,
+                        "upload_gbs_implied": frames_h.numel() / (e2e_ms / 1e3) / 1e9,
+                        "copy_bound": bool(e2e_ms > 1.05 * total_ms / args.steps),
                         "pipeline": "the library uploads step k+1 on its copy stream while step k is detected "
                                     "(two device staging areas); timed from the first upload to the last "
                                     "peaks read back"},
