@@ -7,13 +7,14 @@
 //   conv4 3x3 s2 32->32, each + bias + ReLU | adaptive average pool to 4x8 |
 //   linear 1024 -> 44 logits (36 theta bands + 8 row bands) | BCE loss.
 //
-// conv2..4 are implicit GEMMs on the bf16 tensor cores with fp32
-// accumulation: the forward pass (M = output pixels, N = Cout, K = 9*Cin) on
-// tcgen05 with a tensor-memory accumulator (ld_conv_tc.cu); the input
-// gradient (M = input pixels, N = Cin, K = 9*Cout, transposed stride-2 taps)
-// and the weight gradient (M = Cout, N = 9*Cin, K = pixels, split over CTAs,
-// fp32 atomics) with warp-level mma.sync m16n8k16 here.  conv1 has a single
-// input channel (K = 9) and runs on the CUDA cores.  Every output of the
+// conv2..4 are implicit GEMMs on the fifth-generation tensor cores (tcgen05,
+// bf16 operands in shared memory, fp32 accumulators in tensor memory;
+// ld_conv_tc.cu): the forward pass (M = output pixels, N = Cout, K = 9*Cin),
+// the input gradient (M = input pixels, N = Cin, K = 9*Cout over the taps
+// that read each pixel) and the weight gradient (M = (tap, Cin) plus a row
+// of ones for the bias, N = Cout, K = pixels, split over CTAs into partial
+// sums added in a fixed order).  conv1 has a single input channel (K = 9)
+// and runs on the CUDA cores.  Every output of the
 // forward pass depends only on its own sample, in a fixed summation order,
 // so a frame's logits are the same alone and in any batch.
 #include <cmath>
@@ -28,29 +29,15 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 __device__ __forceinline__ uint32_t bits16(const bf16 *p) {
     return (uint32_t) * reinterpret_cast<const unsigned short *>(p);
 }
-__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
 __device__ __forceinline__ uint32_t to_bf16x2(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 // dy masked by the ReLU: keep the gradient where the stored output is > 0
 // (ReLU outputs are +0 or positive, so "bits != 0" is "> 0").
-__device__ __forceinline__ uint32_t relu_mask2(uint32_t dyw, uint32_t yw) {
-    const uint32_t m = ((yw & 0xFFFFu) ? 0xFFFFu : 0u) | ((yw >> 16) ? 0xFFFF0000u : 0u);
-    return dyw & m;
-}
 __device__ __forceinline__ uint32_t relu_mask1(uint32_t dyb, uint32_t yb) { return yb ? dyb : 0u; }
 
 // ------------------------------------------------------------------ conv1 (Cin = 1)
@@ -127,190 +114,10 @@ __global__ void __launch_bounds__(256) conv1_wgrad_kernel(const uint8_t *x, cons
 
 // ------------------------------------------------------------------ conv2..4 on tensor cores
 
-// Geometry of one layer.  Kernels index pixels within one image (grid y =
-// image) and split a pixel index into (row, column) by a multiply-high with
-// a precomputed magic number: floor(q / d) = umulhi(q, ceil(2^32 / d)) for
-// q * d < 2^32 (here q < 2^16 and d < 2^16).
+// Geometry of one layer (the forward and backward kernels are in ld_conv_tc.cu).
 struct ConvGeom {
     int n, h, w, oh, ow, stride;
-    uint32_t w_magic, ow_magic;
 };
-
-__device__ __forceinline__ void split_px(int q, int ww, uint32_t magic, int &yy, int &xx) {
-    yy = (int)__umulhi((uint32_t)q, magic);
-    xx = q - yy * ww;
-}
-
-// Input gradient: each warp computes 16 input pixels x CIN channels of
-// dx[i][ci] = sum_{tap, co} dy_pre[o(i, tap)][co] * w[co][tap][ci], where
-// o(i, tap) is the output pixel whose tap `tap` reads input pixel i.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv_dgrad_kernel(const bf16 *y, const bf16 *dy, ConvGeom G, const bf16 *wt,
-                                                        bf16 *dx) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int M = G.h * G.w;   // input pixels of one image
-    const int m0 = (blockIdx.x * 4 + warp) * 16;
-    if (m0 >= M) return;
-    const int im = blockIdx.y;
-    int img[2], iy[2], ix[2];
-    bool rv[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int p = m0 + g + 8 * r;
-        rv[r] = p < M;
-        img[r] = im;
-        split_px(rv[r] ? p : 0, G.w, G.w_magic, iy[r], ix[r]);
-    }
-    bf16 *dxi = dx + (int64_t)im * M * CIN;
-    float acc[CIN / 8][4];
-#pragma unroll
-    for (int nt = 0; nt < CIN / 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-        int64_t off[2];
-        bool ok[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int ny = iy[r] + 1 - ky, nx = ix[r] + 1 - kx;
-            const int oy = ny / G.stride, ox = nx / G.stride;
-            ok[r] = rv[r] && ny >= 0 && nx >= 0 && ny % G.stride == 0 && nx % G.stride == 0 && oy < G.oh &&
-                    ox < G.ow;
-            off[r] = ok[r] ? (((int64_t)img[r] * G.oh + oy) * G.ow + ox) * COUT : 0;
-        }
-#pragma unroll
-        for (int cb = 0; cb < COUT / 16; ++cb) {
-            uint32_t a[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = q & 1, kk = cb * 16 + 2 * t + (q >> 1) * 8;
-                a[q] = ok[r] ? relu_mask2(ld_u32(dy + off[r] + kk), ld_u32(y + off[r] + kk)) : 0u;
-            }
-#pragma unroll
-            for (int nt = 0; nt < CIN / 8; ++nt) {
-                const int ci = nt * 8 + g;
-                const int co0 = cb * 16 + 2 * t;
-                const uint32_t b0 = pack2(bits16(wt + ((int64_t)co0 * 9 + tap) * CIN + ci),
-                                          bits16(wt + ((int64_t)(co0 + 1) * 9 + tap) * CIN + ci));
-                const uint32_t b1 = pack2(bits16(wt + ((int64_t)(co0 + 8) * 9 + tap) * CIN + ci),
-                                          bits16(wt + ((int64_t)(co0 + 9) * 9 + tap) * CIN + ci));
-                mma_bf16(acc[nt], a, b0, b1);
-            }
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < CIN / 8; ++nt) {
-        const int c = nt * 8 + 2 * t;
-        if (rv[0])
-            *reinterpret_cast<uint32_t *>(dxi + (int64_t)(m0 + g) * CIN + c) = to_bf16x2(acc[nt][0], acc[nt][1]);
-        if (rv[1])
-            *reinterpret_cast<uint32_t *>(dxi + (int64_t)(m0 + g + 8) * CIN + c) = to_bf16x2(acc[nt][2], acc[nt][3]);
-    }
-}
-
-// Weight gradient: the partial sums dw[co][tap][ci] = sum_p dy_pre[p][co] *
-// x[pix(p, tap)][ci] over this CTA's chunk of output pixels (M = COUT,
-// N = 9*CIN, K = pixels) go to part[cta][co * 9 * CIN + (tap, ci)], and the
-// bias partials to part_b[cta][co]; reduce_parts sums them in CTA order, so
-// gradients are bitwise reproducible.  Warp w takes n-tiles w, w+4, ...
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) conv_wgrad_kernel(const bf16 *x, const bf16 *y, const bf16 *dy, ConvGeom G,
-                                                        int chunk, float *part, float *part_b) {
-    constexpr int NT = 9 * CIN / 8;            // n8 tiles over (tap, ci)
-    constexpr int NTW = (NT + 3) / 4;          // tiles per warp
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    // pixels [p_begin, p_end) of image blockIdx.y, as global pixel indices
-    const int Mi = G.oh * G.ow;
-    const int64_t ibase = (int64_t)blockIdx.y * Mi;
-    const int64_t p_begin = ibase + (int64_t)blockIdx.x * chunk;
-    const int64_t p_end = (blockIdx.x * chunk + chunk < Mi) ? p_begin + chunk : ibase + Mi;
-    float acc[COUT / 16][NTW][4];
-#pragma unroll
-    for (int mt = 0; mt < COUT / 16; ++mt)
-#pragma unroll
-        for (int j = 0; j < NTW; ++j)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[mt][j][i] = 0.f;
-    float bacc = 0.f;   // bias partial: thread (warp 0) sums channel lane for its pixels
-    for (int64_t k0 = p_begin; k0 < p_end; k0 += 16) {
-        // A fragments: rows co, columns = 16 pixels k0 .. k0+15 (dy masked by ReLU)
-        int64_t pk[4];
-        bool pv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pk[q] = k0 + 2 * t + (q & 1) + (q >> 1) * 8;   // pixels 2t, 2t+1, 2t+8, 2t+9
-            pv[q] = pk[q] < p_end;
-        }
-        uint32_t a[COUT / 16][4];
-#pragma unroll
-        for (int mt = 0; mt < COUT / 16; ++mt) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int co = mt * 16 + g + 8 * rr;
-                uint32_t v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    v[q] = pv[q] ? relu_mask1(bits16(dy + pk[q] * COUT + co), bits16(y + pk[q] * COUT + co)) : 0u;
-                a[mt][rr] = pack2(v[0], v[1]);       // k = 2t, 2t+1
-                a[mt][2 + rr] = pack2(v[2], v[3]);   // k = 2t+8, 2t+9
-            }
-        }
-        // pixel coordinates of the 4 pixels this thread reads for B
-        int img[4], oy[4], ox[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            img[q] = blockIdx.y;
-            split_px(pv[q] ? (int)(pk[q] - ibase) : 0, G.ow, G.ow_magic, oy[q], ox[q]);
-        }
-#pragma unroll
-        for (int j = 0; j < NTW; ++j) {
-            const int nt = warp + 4 * j;
-            if (nt >= NT) break;
-            const int ncol = nt * 8 + g;             // (tap, ci) column of this thread
-            const int tap = ncol / CIN, ci = ncol - tap * CIN;
-            const int ky = tap / 3, kx = tap % 3;
-            uint32_t v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int iy = oy[q] * G.stride + ky - 1, ix = ox[q] * G.stride + kx - 1;
-                const bool ok = pv[q] && iy >= 0 && iy < G.h && ix >= 0 && ix < G.w;
-                v[q] = ok ? bits16(x + (((int64_t)img[q] * G.h + iy) * G.w + ix) * CIN + ci) : 0u;
-            }
-            const uint32_t b0 = pack2(v[0], v[1]), b1 = pack2(v[2], v[3]);
-#pragma unroll
-            for (int mt = 0; mt < COUT / 16; ++mt) mma_bf16(acc[mt][j], a[mt], b0, b1);
-        }
-        if (warp == 0) {   // bias: lane = channel
-            for (int q = 0; q < 16 && k0 + q < p_end; ++q) {
-                const int64_t pp = k0 + q;
-                if (lane < COUT)
-                    bacc += __uint_as_float(relu_mask1(bits16(dy + pp * COUT + lane), bits16(y + pp * COUT + lane))
-                                            << 16);
-            }
-        }
-    }
-#pragma unroll
-    for (int mt = 0; mt < COUT / 16; ++mt) {
-#pragma unroll
-        for (int j = 0; j < NTW; ++j) {
-            const int nt = warp + 4 * j;
-            if (nt >= NT) break;
-            const int ncol = nt * 8 + 2 * t;
-            const int co0 = mt * 16 + g;
-            // column ncol = tap * CIN + ci maps to dw[co][tap][ci] = dw[co * 9 * CIN + ncol]
-            float *pc = part + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * (COUT * 9 * CIN);
-            pc[co0 * 9 * CIN + ncol] = acc[mt][j][0];
-            pc[co0 * 9 * CIN + ncol + 1] = acc[mt][j][1];
-            pc[(co0 + 8) * 9 * CIN + ncol] = acc[mt][j][2];
-            pc[(co0 + 8) * 9 * CIN + ncol + 1] = acc[mt][j][3];
-        }
-    }
-    if (warp == 0 && lane < COUT) part_b[(int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * COUT + lane] = bacc;
-}
 
 // out[i] += sum over r < rows of part[r][i], in order (one thread per i).
 __global__ void __launch_bounds__(256) reduce_parts(const float *part, int rows, int cols, float *out) {
@@ -473,17 +280,14 @@ ld_status bad(const char *msg) {
     set_last_error(msg);
     return LD_ERR_INVALID;
 }
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 bool shape_ok(int cin, int cout) {
     return (cin == 1 && cout == 16) || (cin == 16 && cout == 32) || (cin == 32 && cout == 32);
 }
-uint32_t magic_of(int d) { return (uint32_t)(((uint64_t)1 << 32) / (uint64_t)d + 1); }
-// the magic-number split of a pixel index needs w >= 2 and (h*w)*w < 2^32
+// pixel indices of one image stay below 2^31, and w >= 2 (3x3 windows)
 bool size_ok(int h, int w) { return w >= 2 && (uint64_t)h * (uint64_t)w * (uint64_t)w < ((uint64_t)1 << 32); }
 ConvGeom geom(int n, int h, int w, int stride) {
-    ConvGeom G{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride, 0u, 0u};
-    G.w_magic = magic_of(w);
-    G.ow_magic = magic_of(G.ow);
-    return G;
+    return ConvGeom{n, h, w, (h + 2 - 3) / stride + 1, (w + 2 - 3) / stride + 1, stride};
 }
 }  // namespace
 
@@ -530,33 +334,34 @@ ld_status ld_conv3x3_backward(const void *d_x, int32_t n, int32_t h, int32_t w, 
         cudaFreeAsync(part, s);
         return launch_status("conv1_wgrad");
     }
+    if (h > 65535 || w > 65535 || !aligned16(d_x) || !aligned16(d_y) || !aligned16(d_dy) || !aligned16(d_w) ||
+        (d_dx && !aligned16(d_dx)))
+        return bad("ld_conv3x3_backward: h, w <= 65535 and 16-byte aligned tensors required");
     const ConvGeom G = geom(n, h, w, stride);
+    const ConvTcGeom T{n, h, w, G.oh, G.ow, stride};
     const int chunk = 2048;
-    const dim3 wgrid((G.oh * G.ow + chunk - 1) / chunk, n);
-    const int ctas = (int)(wgrid.x * wgrid.y), nw = cout * 9 * cin;
+    const int ctas = ((G.oh * G.ow + chunk - 1) / chunk) * n, nw = cout * 9 * cin;
     float *part = nullptr;   // per-CTA partial sums (weights, then biases), stream-ordered
     if (cudaMallocAsync((void **)&part, (size_t)ctas * (nw + cout) * sizeof(float), s) != cudaSuccess)
         return launch_status("conv_wgrad workspace");
     float *part_b = part + (size_t)ctas * nw;
-    if (cin == 16)
-        conv_wgrad_kernel<16, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
-                                                        G, chunk, part, part_b);
-    else
-        conv_wgrad_kernel<32, 32><<<wgrid, 128, 0, s>>>((const bf16 *)d_x, (const bf16 *)d_y, (const bf16 *)d_dy,
-                                                        G, chunk, part, part_b);
+    cudaError_t e = launch_conv_wgrad_tc(d_x, d_y, d_dy, T, cin, chunk, part, part_b, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(part, s);
+        set_last_error(cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
     reduce_parts<<<(nw + 255) / 256, 256, 0, s>>>(part, ctas, nw, d_dw);
     reduce_parts<<<1, 256, 0, s>>>(part_b, ctas, cout, d_db);
     cudaFreeAsync(part, s);
-    ld_status st = launch_status("conv_wgrad");
+    ld_status st = launch_status("conv_wgrad_tc");
     if (st != LD_OK || !d_dx) return st;
-    const dim3 dgrid((h * w + 63) / 64, n);
-    if (cin == 16)
-        conv_dgrad_kernel<16, 32><<<dgrid, 128, 0, s>>>((const bf16 *)d_y, (const bf16 *)d_dy, G,
-                                                        (const bf16 *)d_w, (bf16 *)d_dx);
-    else
-        conv_dgrad_kernel<32, 32><<<dgrid, 128, 0, s>>>((const bf16 *)d_y, (const bf16 *)d_dy, G,
-                                                        (const bf16 *)d_w, (bf16 *)d_dx);
-    return launch_status("conv_dgrad");
+    e = launch_conv_dgrad_tc(d_y, d_dy, T, cin, d_w, d_dx, s);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
+    return launch_status("conv_dgrad_tc");
 }
 
 ld_status ld_pool_head_forward(const void *d_y4, int32_t n, int32_t h4, int32_t w4, const float *d_wh,

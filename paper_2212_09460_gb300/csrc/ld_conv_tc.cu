@@ -394,6 +394,386 @@ cudaError_t launch_tc(const bf16 *x, const ConvTcGeom &G, const bf16 *w, const f
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------ backward
+
+// Instruction descriptor (kind::f16) for M = 128 and N columns: D fp32, A and
+// B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+// Offset of the 16-byte chunk (K chunk kc, row r) in a K-major operand of
+// `rows` rows (unswizzled core matrices of 8 rows x 16 bytes: the rows of a
+// core matrix 16 bytes apart, row groups 128 bytes apart (SBO), K chunks
+// rows * 16 bytes apart (LBO)).
+__device__ __forceinline__ uint32_t kmaj(int kc, int r, int rows) {
+    return (uint32_t)(((kc * (rows >> 3) + (r >> 3)) * 8 + (r & 7)) * 16);
+}
+
+// ReLU gradient mask of 8 bf16 gradients by the stored outputs (> 0: bits != 0).
+__device__ __forceinline__ uint4 relu_mask8(uint4 d, uint4 o) {
+    auto m2 = [](uint32_t dw, uint32_t ow) {
+        return dw & (((ow & 0xFFFFu) ? 0xFFFFu : 0u) | ((ow >> 16) ? 0xFFFF0000u : 0u));
+    };
+    return make_uint4(m2(d.x, o.x), m2(d.y, o.y), m2(d.z, o.z), m2(d.w, o.w));
+}
+
+// Transpose of an 8 x 8 block of bf16: W[i] holds 8 channels of pixel i;
+// returns in out[c] the 8 pixels of channel c (pixel 2k in the low half of
+// word k).
+__device__ __forceinline__ void transpose8(const uint4 (&W)[8], uint4 (&out)[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint4 &q = W[i];
+            v[i] = (c >> 1) == 0 ? q.x : (c >> 1) == 1 ? q.y : (c >> 1) == 2 ? q.z : q.w;
+        }
+        out[c] = make_uint4(__byte_perm(v[0], v[1], sel), __byte_perm(v[2], v[3], sel), __byte_perm(v[4], v[5], sel),
+                            __byte_perm(v[6], v[7], sel));
+    }
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Weight gradient, per CTA a chunk of one image's output pixels (K = pixels):
+//   D[(tap, ci)][co] = sum_p x[pix(p, tap)][ci] dz[p][co],  dz = dy masked by
+// the ReLU, i.e. dw transposed, plus a row of ones whose D row is the bias
+// gradient sum_p dz[p][co].  M = 9 CIN + 1 rows in tiles of 128 (2 or 3
+// tensor-memory accumulators of 32 columns), N = 32, K blocks of 64 pixels:
+// the block's x values per tap and its dz are transposed into K-major
+// operands (8 x 8 blocks through registers), then one thread issues the
+// tiles' MMAs and commits; the next block is staged after a bounded wait.
+// The CTA's partial sums go to part[cta][co * 9 CIN + (tap, ci)] and
+// part_b[cta][co], summed over CTAs in a fixed order (reduce_parts).
+constexpr int kWgKB = 64;
+template <int CIN>
+__global__ void __launch_bounds__(kTcThreads, 1) conv_wgrad_tc_kernel(const bf16 *x, const bf16 *y, const bf16 *dy,
+                                                                   ConvTcGeom G, int chunk, float *part,
+                                                                   float *part_b) {
+    constexpr int KW = 9 * CIN, QPP = CIN / 8;
+    constexpr int MT = (KW + 1 + kTcM - 1) / kTcM;
+    constexpr int A_TILE = kTcM * kWgKB * 2;
+    constexpr uint32_t IDESC = idesc_n(32);
+    extern __shared__ __align__(1024) uint8_t smem[];   // MT A tiles, then B
+    uint8_t *const As = smem, *const Bs = smem + MT * A_TILE;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_s;
+    __shared__ int pix_s[kWgKB];   // (oy << 16 | ox) of the block's pixels, -1 past the chunk
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_s)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // rows past the ones row stay zero; the ones row (bf16 1.0) is written once
+    for (int i = tid; i < MT * A_TILE / 16; i += kTcThreads) reinterpret_cast<uint4 *>(As)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (tid < kWgKB / 8)
+        *reinterpret_cast<uint4 *>(As + (KW / kTcM) * A_TILE + kmaj(tid, KW % kTcM, kTcM)) =
+            make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_s;
+    const int Mi = G.oh * G.ow, img = blockIdx.y;
+    const int p_begin = blockIdx.x * chunk, p_end = min(Mi, p_begin + chunk);
+    const bf16 *xi = x + (int64_t)img * G.h * G.w * CIN;
+    const int64_t zbase = (int64_t)img * Mi * 32;
+    bool fault = false;
+    int it = 0;
+    for (int k0 = p_begin; k0 < p_end; k0 += kWgKB, ++it) {   // block-uniform
+        if (tid < kWgKB) {
+            const int p = k0 + tid;
+            pix_s[tid] = p < p_end ? ((p / G.ow) << 16 | (p % G.ow)) : -1;
+        }
+        __syncthreads();
+        // B: dz of the block, 8 pixels x 8 channels per thread
+        if (tid < 32) {
+            const int pg = tid >> 2, cg = tid & 3;
+            uint4 W[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                W[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (pix_s[pg * 8 + i] >= 0) {
+                    const int64_t off = zbase + (int64_t)(k0 + pg * 8 + i) * 32 + cg * 8;
+                    W[i] = relu_mask8(__ldg(reinterpret_cast<const uint4 *>(dy + off)),
+                                      __ldg(reinterpret_cast<const uint4 *>(y + off)));
+                }
+            }
+            uint4 T[8];
+            transpose8(W, T);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(Bs + kmaj(pg, cg * 8 + c, 32)) = T[c];
+        }
+        // A: x of the block per tap, 8 pixels x 8 channels per thread and step
+        for (int b = tid; b < 9 * QPP * 8; b += kTcThreads) {
+            const int pg = b & 7, rest = b >> 3, cg = rest % QPP, tap = rest / QPP;
+            const int ky = tap / 3, kx = tap % 3;
+            uint4 W[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                W[i] = make_uint4(0u, 0u, 0u, 0u);
+                const int pp = pix_s[pg * 8 + i];
+                if (pp >= 0) {
+                    const int iy = G.stride * (pp >> 16) + ky - 1, ix = G.stride * (pp & 0xFFFF) + kx - 1;
+                    if (iy >= 0 && iy < G.h && ix >= 0 && ix < G.w)
+                        W[i] = __ldg(reinterpret_cast<const uint4 *>(xi + ((int64_t)iy * G.w + ix) * CIN + cg * 8));
+                }
+            }
+            uint4 T[8];
+            transpose8(W, T);
+            const int m0 = tap * CIN + cg * 8;   // 8 rows of one core matrix
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<uint4 *>(As + (m0 / kTcM) * A_TILE + kmaj(pg, (m0 % kTcM) + c, kTcM)) = T[c];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // smem writes -> tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = saddr(As), b0 = saddr(Bs);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+#pragma unroll
+                for (int j = 0; j < kWgKB / 16; ++j)
+                    mma_f16(tmem + (uint32_t)(t * 32), mat_desc(a0 + t * A_TILE + (2 * j) * (kTcM * 16), kTcM * 16, 128),
+                            mat_desc(b0 + (2 * j) * (32 * 16), 32 * 16, 128), IDESC, (it > 0 || j > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             saddr(&bar))
+                         : "memory");
+        }
+        const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+        const bool all_done = __syncthreads_and(done ? 1 : 0) != 0;   // block-uniform
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!all_done) {
+            fault = true;
+            break;
+        }
+    }
+    if (!fault && it > 0) {
+        const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll 1
+        for (int t = 0; t < MT; ++t) {
+            uint32_t r[32];
+            tmem_ld32(tmem + (uint32_t)(t * 32) + ((uint32_t)(warp * 32) << 16), r);
+            const int m = t * kTcM + warp * 32 + lane;
+            if (m < KW) {
+                float *pc = part + (int64_t)cta * (32 * KW) + m;
+#pragma unroll
+                for (int co = 0; co < 32; ++co) pc[co * KW] = __uint_as_float(r[co]);
+            } else if (m == KW) {
+#pragma unroll
+                for (int co = 0; co < 32; ++co) part_b[(int64_t)cta * 32 + co] = __uint_as_float(r[co]);
+            }
+        }
+    }
+    if (fault && tid == 0) atomicOr(&g_conv_faults, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+}
+
+// Input gradient:
+//   dx[q][ci] = sum over (tap, co) of dz[o(q, tap)][co] w[co][tap][ci],
+// o(q, tap) the output pixel whose tap reads input pixel q.  With stride 2 a
+// tap reads q only if it matches q's parity: ky = 1 for even rows, ky = 0 or
+// 2 for odd ones (and so for x), so the input pixels fall into 4 parity
+// classes with 1, 2, 2 and 4 taps (stride 1: one class, 9 taps).  A CTA tile
+// is 128 input pixels of one class of one image (persistent CTAs), so K =
+// taps x 32 only: M = 128, N = CIN, 2 MMAs of K = 16 per tap.  A is dz
+// gathered per (pixel, tap) in K-major chunks of 8 channels (no transpose:
+// channels are contiguous); B is the weights transposed once per CTA for all
+// 9 taps, and each MMA points at its tap's chunks.  The accumulator is read
+// with tcgen05.ld and stored as bf16 NHWC.
+struct DgClass {
+    int py, px, ny, nx, ntap, tiles;
+};
+
+// Tap (ky * 3 + kx) of slot `slot` of a class: stride 1, every tap in order;
+// stride 2, ky = 1 (even rows) or 0, 2 (odd rows), and so for x.
+__device__ __forceinline__ int dg_tap(const DgClass &k, int slot, int stride) {
+    if (stride != 2) return slot;
+    const int nkx = k.px ? 2 : 1, a = slot / nkx, b = slot - a * nkx;
+    return (k.py ? 2 * a : 1) * 3 + (k.px ? 2 * b : 1);
+}
+
+__device__ __forceinline__ DgClass dg_class(const ConvTcGeom &G, int c) {
+    DgClass k;
+    const int S = G.stride;
+    k.py = S == 2 ? c >> 1 : 0;
+    k.px = S == 2 ? c & 1 : 0;
+    k.ny = S == 2 ? (G.h - k.py + 1) >> 1 : G.h;
+    k.nx = S == 2 ? (G.w - k.px + 1) >> 1 : G.w;
+    k.tiles = (k.ny * k.nx + kTcM - 1) / kTcM;
+    k.ntap = S == 2 ? (k.py ? 2 : 1) * (k.px ? 2 : 1) : 9;
+    return k;
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(kTcThreads, 1) conv_dgrad_tc_kernel(const bf16 *y, const bf16 *dy, ConvTcGeom G,
+                                                                   const bf16 *wt, bf16 *dx) {
+    constexpr int KCH = 9 * 32 / 8;   // K chunks (tap, 8 output channels) of all taps
+    constexpr int B_BYTES = CIN * KCH * 16;
+    constexpr uint32_t IDESC = idesc_n(CIN);
+    extern __shared__ __align__(1024) uint8_t smem[];   // B, then A (at most 9 taps)
+    uint8_t *const Bs = smem, *const As = smem + (B_BYTES + 1023) / 1024 * 1024;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_s)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // B[ci][(tap, co)] = w[co][tap][ci]
+    for (int b = tid; b < KCH * CIN; b += kTcThreads) {
+        const int ci = b % CIN, kc = b / CIN, tap = kc >> 2, cg = kc & 3;
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t lo = *reinterpret_cast<const unsigned short *>(wt + ((cg * 8 + 2 * k) * 9 + tap) * CIN + ci);
+            const uint32_t hi =
+                *reinterpret_cast<const unsigned short *>(wt + ((cg * 8 + 2 * k + 1) * 9 + tap) * CIN + ci);
+            v[k] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4 *>(Bs + kmaj(kc, ci, CIN)) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_s;
+    const int n_cls = G.stride == 2 ? 4 : 1;
+    int tiles_img = 0;
+    for (int c = 0; c < n_cls; ++c) tiles_img += dg_class(G, c).tiles;
+    const int n_tiles = G.n * tiles_img;
+    bool fault = false;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {   // block-uniform
+        const int img = tile / tiles_img;
+        int r = tile - img * tiles_img, c = 0;
+        DgClass K = dg_class(G, 0);
+        while (r >= K.tiles) {
+            r -= K.tiles;
+            K = dg_class(G, ++c);
+        }
+        const int s0 = r * kTcM, npts = K.ny * K.nx;
+        const int64_t zbase = (int64_t)img * G.oh * G.ow * 32;
+        // A[q][(slot, co)]: thread b takes chunk (slot, row q, 8 channels cg); 4 threads per pixel
+        for (int b = tid; b < K.ntap * 4 * kTcM; b += kTcThreads) {
+            const int cg = b & 3, q = (b >> 2) & (kTcM - 1), slot = b >> 9;
+            const int tap = dg_tap(K, slot, G.stride);
+            const int sidx = s0 + q;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (sidx < npts) {
+                const int i = sidx / K.nx, j = sidx - i * K.nx;
+                const int qy = K.py + G.stride * i, qx = K.px + G.stride * j;
+                const int ny = qy + 1 - tap / 3, nx = qx + 1 - tap % 3;   // divisible by the stride (class)
+                if (ny >= 0 && nx >= 0) {
+                    const int oy = ny / G.stride, ox = nx / G.stride;
+                    if (oy < G.oh && ox < G.ow) {
+                        const int64_t off = zbase + ((int64_t)oy * G.ow + ox) * 32 + cg * 8;
+                        v = relu_mask8(__ldg(reinterpret_cast<const uint4 *>(dy + off)),
+                                       __ldg(reinterpret_cast<const uint4 *>(y + off)));
+                    }
+                }
+            }
+            *reinterpret_cast<uint4 *>(As + kmaj(slot * 4 + cg, q, kTcM)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = saddr(As), b0 = saddr(Bs);
+            for (int slot = 0; slot < K.ntap; ++slot) {
+                const int tap = dg_tap(K, slot, G.stride);
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+                    mma_f16(tmem, mat_desc(a0 + (slot * 4 + 2 * m) * (kTcM * 16), kTcM * 16, 128),
+                            mat_desc(b0 + (tap * 4 + 2 * m) * (CIN * 16), CIN * 16, 128), IDESC,
+                            (slot > 0 || m > 0) ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             saddr(&bar))
+                         : "memory");
+        }
+        const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+        const bool all_done = __syncthreads_and(done ? 1 : 0) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!all_done) {
+            fault = true;
+            break;
+        }
+        uint32_t rr[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), rr);   // CIN < 32: the upper columns are unused
+        const int sidx = s0 + warp * 32 + lane;
+        if (sidx < npts) {
+            const int i = sidx / K.nx, j = sidx - i * K.nx;
+            const int qy = K.py + G.stride * i, qx = K.px + G.stride * j;
+            uint4 *dst = reinterpret_cast<uint4 *>(dx + (((int64_t)img * G.h + qy) * G.w + qx) * CIN);
+#pragma unroll
+            for (int c8 = 0; c8 < CIN / 8; ++c8)
+                dst[c8] = make_uint4(to_bf16x2(__uint_as_float(rr[8 * c8]), __uint_as_float(rr[8 * c8 + 1])),
+                                     to_bf16x2(__uint_as_float(rr[8 * c8 + 2]), __uint_as_float(rr[8 * c8 + 3])),
+                                     to_bf16x2(__uint_as_float(rr[8 * c8 + 4]), __uint_as_float(rr[8 * c8 + 5])),
+                                     to_bf16x2(__uint_as_float(rr[8 * c8 + 6]), __uint_as_float(rr[8 * c8 + 7])));
+        }
+        // the accumulator is read and A is consumed before the next tile's staging and MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (fault && tid == 0) atomicOr(&g_conv_faults, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+template <int CIN>
+int wgrad_smem() {
+    constexpr int MT = (9 * CIN + 1 + kTcM - 1) / kTcM;
+    constexpr int need = MT * kTcM * kWgKB * 2 + 32 * kWgKB * 2;
+    return need > 56 * 1024 ? need : 56 * 1024;
+}
+template <int CIN>
+int dgrad_smem() {
+    return (CIN * 36 * 16 + 1023) / 1024 * 1024 + kTcM * 36 * 16;
+}
+
 }  // namespace
 
 cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, const void *w, const float *b, void *y,
@@ -407,6 +787,102 @@ cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, cons
         if (cin == 32) return launch_tc<32, 1, false>((const bf16 *)x, G, (const bf16 *)w, b, (bf16 *)y, none, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// Grid limit of a kernel: SMs x CTAs per SM by shared memory (and the
+// per-block reservation) and by tensor-memory columns.
+static cudaError_t grid_limit(const void *kern, int smem, int tmem_cols, int *limit) {
+    int dev = 0, sms = 0, sm_smem = 0, reserved = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    if (r == cudaSuccess) r = cudaFuncGetAttributes(&fa, kern);
+    if (r != cudaSuccess) return r;
+    int per_sm = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
+    if (per_sm * tmem_cols > 512) per_sm = 512 / tmem_cols;
+    if (per_sm < 1) per_sm = 1;
+    *limit = sms * per_sm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_conv_wgrad_tc(const void *x, const void *y, const void *dy, const ConvTcGeom &G, int cin,
+                                 int chunk, float *part, float *part_b, cudaStream_t s) {
+    if ((cin != 16 && cin != 32) || chunk < 1) return cudaErrorInvalidValue;
+    const dim3 grid((G.oh * G.ow + chunk - 1) / chunk, G.n);
+    static std::atomic<uint64_t> done16{0}, done32{0};
+    if (cin == 16) {
+        auto kern = conv_wgrad_tc_kernel<16>;
+        const int smem = wgrad_smem<16>();
+        cudaError_t e = once_per_device(done16, [&](int) {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        });
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kTcThreads, smem, s>>>((const bf16 *)x, (const bf16 *)y, (const bf16 *)dy, G, chunk, part, part_b);
+    } else {
+        auto kern = conv_wgrad_tc_kernel<32>;
+        const int smem = wgrad_smem<32>();
+        cudaError_t e = once_per_device(done32, [&](int) {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        });
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kTcThreads, smem, s>>>((const bf16 *)x, (const bf16 *)y, (const bf16 *)dy, G, chunk, part, part_b);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_dgrad_tc(const void *y, const void *dy, const ConvTcGeom &G, int cin, const void *w, void *dx,
+                                 cudaStream_t s) {
+    if (cin != 16 && cin != 32) return cudaErrorInvalidValue;
+    int tiles = 0;   // per image: the parity classes' tiles (stride 2), else ceil(h w / 128)
+    if (G.stride == 2) {
+        for (int c = 0; c < 4; ++c) {
+            const int ny = (G.h - (c >> 1) + 1) >> 1, nx = (G.w - (c & 1) + 1) >> 1;
+            tiles += (ny * nx + kTcM - 1) / kTcM;
+        }
+    } else {
+        tiles = (G.h * G.w + kTcM - 1) / kTcM;
+    }
+    tiles *= G.n;
+    static std::atomic<uint64_t> done16{0}, done32{0};
+    static std::atomic<int> lim16[64], lim32[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidValue;
+    if (cin == 16) {
+        auto kern = conv_dgrad_tc_kernel<16>;
+        const int smem = dgrad_smem<16>();
+        e = once_per_device(done16, [&](int d) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            int lim = 0;
+            if (r == cudaSuccess) r = grid_limit((const void *)kern, smem, kTmemCols, &lim);
+            if (r == cudaSuccess) lim16[d].store(lim, std::memory_order_release);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+        const int lim = lim16[dev].load(std::memory_order_acquire);
+        if (lim <= 0) return cudaErrorInvalidValue;
+        kern<<<tiles < lim ? tiles : lim, kTcThreads, smem, s>>>((const bf16 *)y, (const bf16 *)dy, G,
+                                                                  (const bf16 *)w, (bf16 *)dx);
+    } else {
+        auto kern = conv_dgrad_tc_kernel<32>;
+        const int smem = dgrad_smem<32>();
+        e = once_per_device(done32, [&](int d) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            int lim = 0;
+            if (r == cudaSuccess) r = grid_limit((const void *)kern, smem, kTmemCols, &lim);
+            if (r == cudaSuccess) lim32[d].store(lim, std::memory_order_release);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+        const int lim = lim32[dev].load(std::memory_order_acquire);
+        if (lim <= 0) return cudaErrorInvalidValue;
+        kern<<<tiles < lim ? tiles : lim, kTcThreads, smem, s>>>((const bf16 *)y, (const bf16 *)dy, G,
+                                                                  (const bf16 *)w, (bf16 *)dx);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const void *w1, const float *b1,

@@ -293,6 +293,15 @@ struct ConvTcGeom {
 };
 cudaError_t launch_conv_fwd_tc(const void *x, const ConvTcGeom &G, int cin, const void *w, const float *b, void *y,
                                cudaStream_t s);
+// Backward of conv2..4 on tcgen05 (ld_conv_tc.cu).  Weight gradient: per CTA
+// (chunk of output pixels of one image) the partial sums of dw [32][9][cin]
+// and db [32] into part / part_b (as many rows as CTAs: ceil(oh*ow/chunk) x n,
+// image-major), to be summed in CTA order.  Input gradient: dx [n][h][w][cin]
+// bf16 from dy masked by the ReLU of y (both [n][oh][ow][32]).
+cudaError_t launch_conv_wgrad_tc(const void *x, const void *y, const void *dy, const ConvTcGeom &G, int cin,
+                                 int chunk, float *part, float *part_b, cudaStream_t s);
+cudaError_t launch_conv_dgrad_tc(const void *y, const void *dy, const ConvTcGeom &G, int cin, const void *w, void *dx,
+                                 cudaStream_t s);
 // Inference: conv1 (1->16, from the uint8 edge counts x0 [n][h][w]) fused into
 // conv2 (16->32, stride 2); G describes conv2 (input h x w = conv1's output).
 cudaError_t launch_conv12_fused_tc(const uint8_t *x0, const ConvTcGeom &G, const void *w1, const float *b1,

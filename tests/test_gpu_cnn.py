@@ -155,6 +155,54 @@ def test_tensor_core_conv_matches_oracle(ldlib, cin, stride, h, w):
     assert (err <= bound).all(), float((err / np.maximum(bound, 1e-300)).max())
 
 
+@pytest.mark.parametrize("cin,stride,h,w", [(16, 2, 37, 41), (32, 2, 20, 23), (16, 1, 19, 13), (32, 1, 17, 18),
+                                            (32, 2, 68, 120)])
+def test_tensor_core_conv_backward_matches_reference(ldlib, cin, stride, h, w):
+    # every (channels, stride) form of the tcgen05 weight and input gradients,
+    # at ragged sizes, against float64 sums of the same bf16 values.  The ReLU
+    # mask is the GPU forward's own output (y > 0), applied on both sides, so
+    # the only errors are fp32 sums (within a CTA on the tensor core, then of
+    # the CTAs' partials in a fixed order) and, for dx, the bf16 rounding:
+    # |gpu - ref| <= u |ref| + (1 + u) gamma(K) sum |terms| per element.
+    rng = np.random.default_rng(cin * 1000 + stride * 100 + h)
+    n = 2
+    x = torch.from_numpy(rng.standard_normal((n, h, w, cin)).astype(np.float32)).to(torch.bfloat16)
+    wt = torch.from_numpy(rng.uniform(-0.2, 0.2, (32, 3, 3, cin)).astype(np.float32)).to(torch.bfloat16)
+    b = torch.from_numpy(rng.uniform(-0.1, 0.1, 32).astype(np.float32))
+    oh, ow = (h - 1) // stride + 1, (w - 1) // stride + 1
+    dy = torch.from_numpy(rng.standard_normal((n, oh, ow, 32)).astype(np.float32)).to(torch.bfloat16)
+    xd, wd, bd, dyd = x.cuda().contiguous(), wt.cuda().contiguous(), b.cuda(), dy.cuda().contiguous()
+    y = torch.empty((n, oh, ow, 32), dtype=torch.bfloat16, device="cuda")
+    dx = torch.empty((n, h, w, cin), dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros((32, 3, 3, cin), dtype=torch.float32, device="cuda")
+    db = torch.zeros(32, dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    ldlib.ld_conv3x3_forward(xd.data_ptr(), n, h, w, cin, 32, stride, wd.data_ptr(), bd.data_ptr(), y.data_ptr(), s)
+    ldlib.ld_conv3x3_backward(xd.data_ptr(), n, h, w, cin, 32, stride, wd.data_ptr(), y.data_ptr(), dyd.data_ptr(),
+                              dx.data_ptr(), dw.data_ptr(), db.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert ldlib.ld_conv_faults(0) == 0
+    mask = (y.float().cpu() > 0).double()
+    dz = (dy.double() * mask).permute(0, 3, 1, 2)             # NCHW
+    x64 = x.double().permute(0, 3, 1, 2)
+    w64 = wt.double().permute(0, 3, 1, 2)                     # [co][ci][3][3]
+    gw = torch.nn.grad.conv2d_weight(x64, w64.shape, dz, stride=stride, padding=1)
+    gw_abs = torch.nn.grad.conv2d_weight(x64.abs(), w64.shape, dz.abs(), stride=stride, padding=1)
+    gx = torch.nn.grad.conv2d_input(x64.shape, w64, dz, stride=stride, padding=1)
+    gx_abs = torch.nn.grad.conv2d_input(x64.shape, w64.abs(), dz.abs(), stride=stride, padding=1)
+    ctas = ((oh * ow + 2047) // 2048) * n
+    k_w = n * oh * ow + ctas                                   # terms of a weight-gradient sum
+    got_w = dw.cpu().double().permute(0, 3, 1, 2)
+    bound_w = (1 + cb.U16) * cb.gamma(k_w) * gw_abs
+    assert ((got_w - gw).abs() <= bound_w).all(), float(((got_w - gw).abs() / bound_w.clamp_min(1e-300)).max())
+    got_b, ref_b = db.cpu().double(), dz.sum(dim=(0, 2, 3))
+    bound_b = (1 + cb.U16) * cb.gamma(k_w) * dz.abs().sum(dim=(0, 2, 3))
+    assert ((got_b - ref_b).abs() <= bound_b).all()
+    got_x = dx.float().cpu().double().permute(0, 3, 1, 2)
+    bound_x = cb.U16 * gx.abs() + (1 + cb.U16) * cb.gamma(9 * 32) * gx_abs
+    assert ((got_x - gx).abs() <= bound_x).all(), float(((got_x - gx).abs() / bound_x.clamp_min(1e-300)).max())
+
+
 @pytest.mark.parametrize("hw", [(135, 240), (70, 100)])
 def test_fused_inference_equals_layer_calls(ctx, ldlib, hw):
     # ld_proposal_logits (conv1 fused into the tensor-core conv2) gives the
