@@ -297,10 +297,18 @@ __device__ __forceinline__ void sobel_run(const SobelLaunch &L, const SobelFrame
             for (int k = 0; k < 4; ++k) {
                 uint32_t m = T[k];
                 const uint32_t bk = b0 + ((uint32_t)(2 * k) << 16);
-                while (m) {
+                while (m) {   // two edges per trip
                     const uint32_t sb = bfind32(m);
-                    m &= ~(1u << sb);
-                    *st++ = bk + 16u * sb;
+                    m ^= 1u << sb;
+                    st[0] = bk + 16u * sb;
+                    if (m) {
+                        const uint32_t sc = bfind32(m);
+                        m ^= 1u << sc;
+                        st[1] = bk + 16u * sc;
+                        st += 2;
+                    } else {
+                        st += 1;
+                    }
                 }
             }
             __syncwarp();
