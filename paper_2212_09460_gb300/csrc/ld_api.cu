@@ -290,6 +290,15 @@ HoughPlan plan_cols(const ld_ctx *ctx, int w, int h, int n_theta) {
     return hp;
 }
 
+// An interleaved-kernel plan with `width` pairs per tile (its rows fit).
+HoughPlan plan_cols_width(HoughPlan hp, int n_theta, int width) {
+    const int n_pairs = n_theta / 2;
+    hp.width = width;
+    hp.n_tiles = (n_pairs + width - 1) / width;
+    hp.pairs = (n_pairs + hp.n_tiles - 1) / hp.n_tiles;
+    return hp;
+}
+
 // The voting plan of w x h frames.  allow_cols: the launch may use the
 // interleaved-column kernel (full vote in candidate mode with min_votes >= 1,
 // where cells outside a theta's window, which it does not hold, cannot be
@@ -1135,7 +1144,7 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
         for (int i = g0; i < g1; ++i) {
             ed += ((int64_t)h_frames[i].w * h_frames[i].h + 3) / 4 * 4;
             const int T0 = plan_for(ctx, h_frames[i].w, h_frames[i].h, p.n_theta, false).n_tiles;
-            const int Tc = plan_cols(ctx, h_frames[i].w, h_frames[i].h, p.n_theta).n_tiles;
+            const int Tc = (p.n_theta / 2 + 7) / 8;   // interleaved tiles of 8 pairs at the most
             ca += (int64_t)std::max(Tc, std::min(p.n_theta / 2, T0 + (T0 + 3) / 4)) * M;   // room for balance_tiles
         }
         if (ed > max_edges) max_edges = ed;
@@ -1198,6 +1207,14 @@ ld_status detect_impl(ld_ctx *ctx, const ld_frame *h_frames, int32_t n, const ld
                     const ld_frame &fr = h_frames[g0 + k];
                     plans[k] = plan_for(ctx, fr.w, fr.h, p.n_theta, false);
                     is_cols[k] = 0;
+                }
+        }
+        if (narrow_cols_tiles(tiles_c, ctx->num_sms)) {   // small launch: tiles of 8 pairs
+            tiles_c = 0;
+            for (int k = 0; k < gn; ++k)
+                if (is_cols[k]) {
+                    plans[k] = plan_cols_width(plans[k], p.n_theta, 8);
+                    tiles_c += plans[k].n_tiles;
                 }
         }
         {   // wave-filling tile counts for the packed-pair frames (equal plans only)

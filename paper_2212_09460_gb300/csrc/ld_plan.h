@@ -141,6 +141,12 @@ LD_PLAN_HD inline PieceSplit plan_pieces(const int *tiles, int n, int64_t px_min
     return r;
 }
 
+// A launch whose interleaved-kernel tiles of 16 pairs would occupy at most
+// half the SMs (small batches: latency) votes in tiles of 8 pairs instead:
+// twice the tiles, so the per-tile work (clearing, selection, the merge of a
+// split tile's pieces) runs on twice the SMs.
+inline bool narrow_cols_tiles(int tiles16, int slots) { return tiles16 > 0 && 2 * tiles16 <= slots; }
+
 // A launch group with tiles_c interleaved-kernel tiles and tiles_p
 // packed-pair tiles votes in two launches only if each part fills the slots.
 inline bool two_launches(int tiles_c, int tiles_p, int slots) {

@@ -130,6 +130,14 @@ int main() {
     CHECK(two_launches(168, 180, 152));
     CHECK(!two_launches(72, 864, 152));
     CHECK(!two_launches(864, 0, 152));
+    // small launches vote in tiles of 8 pairs: one 640x480 frame (6 tiles of
+    // 16 pairs at 180 theta), one 1080p frame (12 tiles), not a 64-frame batch
+    CHECK(narrow_cols_tiles(6, 152));
+    CHECK(narrow_cols_tiles(12, 152));
+    CHECK(narrow_cols_tiles(76, 152));
+    CHECK(!narrow_cols_tiles(77, 152));
+    CHECK(!narrow_cols_tiles(768, 152));
+    CHECK(!narrow_cols_tiles(0, 152));
 
     std::printf(failures ? "plan checks: %d FAILED\n" : "plan checks: all passed%.0d\n", failures);
     return failures ? 1 : 0;
