@@ -178,7 +178,9 @@ LD_API ld_status ld_hough_peaks(ld_ctx *ctx, const int32_t *d_acc, int32_t n_the
  * Step 3 runs in one of two voting kernels, per launch group of up to 128
  * frames: with min_votes >= 1, frames whose theta windows fit shared memory
  * in tiles of 16 or 8 theta pairs (windows up to about 6100 rows: every size
- * up to 3840x2160 and beyond) take the interleaved-column kernel, the others
+ * up to 3840x2160 and beyond; 8 pairs for windows over about 3000 rows, and
+ * for launches whose 16-pair tiles would occupy at most half the SMs) take
+ * the interleaved-column kernel, the others
  * the packed-pair kernel; a group with both kinds takes one launch per kernel
  * when each part fills the GPU, else the packed-pair kernel for all.  The
  * results never depend on the kernel, the tile sizes or the edge-range
