@@ -454,6 +454,7 @@ ld_status ld_ctx_destroy(ld_ctx *ctx) {
         ctx->part.release();
         ctx->canny.release();
         ctx->fused.release();
+        if (ctx->hcopy) cudaStreamSynchronize(ctx->hcopy);   // uploads still in flight
         for (int b = 0; b < 2; ++b) {
             if (ctx->hev_free[b]) cudaEventSynchronize(ctx->hev_free[b]);
             ctx->stage[b].release();
