@@ -189,6 +189,7 @@ struct LinesFrame {
 
 struct LinesLaunch {
     int32_t n, top_k, n_theta, fill_gap, min_length, max_segments;
+    int32_t keys_cap, pad_;   // shared-memory keys per CTA (set by launch_lines)
     const int32_t *trig;    // [(n_theta/2 + 1) * 2] Q16 (c_k, s_k), k <= n_theta/2
     LinesFrame f[kMaxLaunchFrames];
 };

@@ -71,10 +71,11 @@ __device__ __forceinline__ int64_t dist2(int x0, int y0, int x1, int y1) {
     return dx * dx + dy * dy;
 }
 
-__global__ void __launch_bounds__(kLinesThreads, 1) lines_kernel(const __grid_constant__ LinesLaunch L) {
+__global__ void __launch_bounds__(kLinesThreads, 2) lines_kernel(const __grid_constant__ LinesLaunch L) {
     extern __shared__ __align__(16) uint32_t lsm[];
-    uint32_t *keys = lsm;                                   // [kLinesKeys] sort keys
-    int32_t *starts = reinterpret_cast<int32_t *>(lsm + kLinesKeys);   // [kLinesKeys] segment starts
+    const int cap = L.keys_cap;                             // >= 2 max(w, h), a power of two
+    uint32_t *keys = lsm;                                   // [cap] sort keys
+    int32_t *starts = reinterpret_cast<int32_t *>(lsm + cap);   // [cap] segment starts
     __shared__ int warp_sums[kLinesWarps + 1];
     __shared__ int n_sh;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kLinesThreads, 1) lines_kernel(const __grid_co
             if (lane == 0) base = atomicAdd(&n_sh, __popc(bal));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
             const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (m && pos < kLinesKeys) keys[pos] = by_x ? (x << 15 | y) : (y << 15 | x);
+            if (m && pos < cap) keys[pos] = by_x ? (x << 15 | y) : (y << 15 | x);
         }
     };
     const int64_t E4 = E >> 2;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kLinesThreads, 1) lines_kernel(const __grid_co
     }
     __syncthreads();
     const int n_all = n_sh;
-    const int n = n_all < kLinesKeys ? n_all : kLinesKeys;   // distinct pixels never exceed it
+    const int n = n_all < cap ? n_all : cap;   // distinct pixels never exceed it
     if (tid == 0 && F.support) F.support[p] = n_all;
 
     // 2. sort ascending (descending sort of the complemented keys; padding
@@ -214,12 +215,22 @@ __global__ void __launch_bounds__(kLinesThreads, 1) lines_kernel(const __grid_co
 
 }  // namespace
 
-cudaError_t launch_lines(const LinesLaunch &L, cudaStream_t s) {
-    if (L.n <= 0) return cudaSuccess;
-    constexpr size_t smem = (size_t)2 * kLinesKeys * 4;
+cudaError_t launch_lines(const LinesLaunch &L0, cudaStream_t s) {
+    if (L0.n <= 0) return cudaSuccess;
+    // keys for the largest frame's 2 max(w, h) supporting pixels: smaller CTAs
+    // let two of them share an SM (one wave for a 64-frame batch's peaks)
+    LinesLaunch L = L0;
+    int side = 1;
+    for (int k = 0; k < L.n; ++k) side = max(side, max(L.f[k].w, L.f[k].h));
+    if (side > kLinesMaxSide) return cudaErrorInvalidValue;
+    int cap = 64;
+    while (cap < 2 * side) cap <<= 1;
+    L.keys_cap = cap;
+    const size_t smem = (size_t)2 * cap * 4;
     static std::atomic<uint64_t> attr_done{0};
     const cudaError_t e = once_per_device(attr_done, [](int) {
-        return cudaFuncSetAttribute(lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return cudaFuncSetAttribute(lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * kLinesKeys * 4));
     });
     if (e != cudaSuccess) return e;
     lines_kernel<<<L.n * L.top_k, kLinesThreads, smem, s>>>(L);
