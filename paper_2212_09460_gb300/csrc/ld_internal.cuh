@@ -220,8 +220,7 @@ struct CannyLaunch {
 };
 
 // ---------------------------------------------------------------- fused Steps 1-3
-constexpr int kFusedBlock = 32;        // block side (pixels)
-constexpr int kFusedRows = 48;         // rho cells a block reaches per theta (<= 45)
+constexpr int kFusedBlock = 32;        // block side (pixels) of the smaller blocks
 constexpr int kFusedMaxTheta = 1024;   // the block's accumulator fits shared memory
 
 struct FusedFrame {
@@ -242,7 +241,10 @@ struct FusedLaunch {
 };
 
 // ---------------------------------------------------------------- launchers
-// Fused Steps 1-3 (no edge list): one CTA per 32 x 32 block.
+// Fused Steps 1-3 (no edge list): one CTA per 64 x 64 block when its
+// accumulator fits shared memory (n_theta <= 512) and the launch has at least
+// two such blocks per SM, else per 32 x 32 block; the launch sets the frames'
+// block layout itself (n_blocks is not used).
 cudaError_t launch_fused_vote(const FusedLaunch &L, int n_blocks, cudaStream_t s);
 size_t fused_smem_bytes(int n_theta);
 int fused_blocks(int w, int h);
