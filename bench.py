@@ -44,9 +44,9 @@ METRIC = "1080p frames/s end-to-end, % of HBM roofline; proposal vs plain at equ
 # valid only while the kernel's sources hash to the recorded value (else null).
 MEASURED_TRAFFIC = {
     "hough": {"sources": ["ld_hough.cu", "ld_select.cuh", "ld_internal.cuh"],
-              "sha1": "845e1ac909435f60d53d19cdef43c6b31d52c657", "bytes_per_frame": (41196032 + 1772288) / 64},
+              "sha1": "a53edfa154bdbf404ec05b105c5a341b7f6a896e", "bytes_per_frame": (41210624 + 2003456) / 64},
     "sobel": {"sources": ["ld_sobel.cu", "ld_internal.cuh"],
-              "sha1": "d66f03457f9eea8348bc6ac07e881eb24fdaf473", "bytes_per_frame": (142081792 + 18793216) / 64},
+              "sha1": "331ed10a263e183df7e2ac37a3ecbac77231d1cf", "bytes_per_frame": (142061312 + 19174656) / 64},
 }
 
 
@@ -216,8 +216,12 @@ def batching_and_latency(torch, ld, dev, mixed_host, flush):
         out1 = (torch.zeros((1, 2, 3), dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev),
                 torch.zeros(1, dtype=torch.int32, device=dev))
         ms1 = graph_time(torch, lambda: c.detect_batch(one, p180, out=out1), 50, None)
+        plan1 = c.plan(640, 480, p180)
     latency = {"workload": "one 640x480 frame (seed 0), 180 theta, top-2, CUDA-graph replay, warm L2",
-               "us_per_frame": ms1 * 1e3}
+               "us_per_frame": ms1 * 1e3,
+               "plan": {"pairs_per_tile": plan1[0], "sobel_groups": plan1[1],
+                        "note": "pairs < 0: the interleaved-column kernel (a launch this small votes in "
+                                "tiles of 8 pairs); each replay is timed alone (events around it)"}}
     return batching, latency
 
 
