@@ -18,12 +18,13 @@
 //                        writes the class map (0, 1 weak, 2 strong) and, for
 //                        candidates only, parent[i] = i and strong[i] = 0.
 //   canny_union_kernel   a thread per 16 pixels of a row (one 16-byte read of
-//                        the classes) joins each candidate to its candidate
-//                        neighbours above and to the left (each
-//                        8-neighbour pair once) in a union-find forest: lock-free
-//                        linking of the larger root under the smaller with
-//                        atomicCAS (parent[i] <= i always, so finding a root
-//                        ends; a failed CAS means another link succeeded).
+//                        the classes) links the candidates run by run: along
+//                        the run, to the left neighbour and to the runs above,
+//                        so that every 8-neighbour pair joins one component of
+//                        a union-find forest: lock-free linking of the larger
+//                        root under the smaller with atomicCAS (parent[i] <= i
+//                        always, so finding a root ends; a failed CAS means
+//                        another link succeeded).
 //   canny_flatten_kernel every candidate points straight at its root; a strong
 //                        pixel marks its root.
 //   canny_emit_kernel    candidates whose root is marked become edges: the
@@ -292,6 +293,13 @@ __device__ __forceinline__ void load_cls16(const uint8_t *cls, int n, uint32_t *
     *strong = st;
 }
 
+// Links by runs: in a chunk, a run of consecutive candidates is connected
+// along the row, so each member is linked straight under the run's first
+// pixel (independent compare-and-swaps, no root searches unless another link
+// got there first); the first pixel then links to the left neighbour across
+// the chunk border, and once to each run of candidates in the row above that
+// touches the run's columns widened by one (any pixel of such a run is in
+// its component).  Every 8-neighbour pair ends up in one component.
 __global__ void __launch_bounds__(kPxThreads) canny_union_kernel(const __grid_constant__ CannyLaunch L) {
     const Chunk c = chunk_of(L, (int64_t)blockIdx.x * kPxThreads + threadIdx.x);
     if (!c.ok) return;
@@ -300,20 +308,37 @@ __global__ void __launch_bounds__(kPxThreads) canny_union_kernel(const __grid_co
     const uint8_t *row = F.cls + (size_t)c.y * w + c.x0;
     uint32_t cand, strong;
     load_cls16(row, c.n, &cand, &strong);
-    // left neighbour of each pixel is a candidate (bit 0: the previous chunk's last pixel)
-    const uint32_t left = (cand << 1) | ((c.x0 > 0 && row[-1]) ? 1u : 0u);
+    if (!cand) return;
+    const int p0 = c.y * w + c.x0;   // pixel of bit 0
+    // the row above, columns x0 - 1 .. x0 + 16 as bits 0 .. 17
+    uint32_t up = 0;
+    if (c.y > 0) {
+        const uint8_t *ur = row - w;
+        uint32_t uc, us;
+        load_cls16(ur, c.n, &uc, &us);
+        up = uc << 1;
+        if (c.x0 > 0 && ur[-1]) up |= 1u;
+        if (c.n == 16 && c.x0 + 16 < w && ur[16]) up |= 1u << 17;
+    }
+    const int pu = p0 - w - 1;   // pixel of bit 0 of `up`
     uint32_t m = cand;
     while (m) {
-        const int i = __ffs(m) - 1;
-        m &= m - 1;
-        const int x = c.x0 + i, p = c.y * w + x;
-        // the neighbours that come earlier in raster order: each 8-neighbour pair once
-        if ((left >> i) & 1u) unite(F.parent, p, p - 1);
-        if (c.y > 0) {
-            const int u = p - w;
-            if (x > 0 && F.cls[u - 1]) unite(F.parent, p, u - 1);
-            if (F.cls[u]) unite(F.parent, p, u);
-            if (x + 1 < w && F.cls[u + 1]) unite(F.parent, p, u + 1);
+        const int a = __ffs(m) - 1;
+        const int len = __ffs(~(m >> a)) - 1;   // the run: bits a .. a + len - 1
+        const int b = a + len - 1;
+        m &= ~(((1u << len) - 1u) << a);
+        const int s0 = p0 + a;
+        for (int i = a + 1; i <= b; ++i) {
+            const int q = p0 + i;
+            if (atomicCAS(F.parent + q, q, s0) != q) unite(F.parent, q, s0);
+        }
+        if (a == 0 && c.x0 > 0 && row[-1]) unite(F.parent, s0, s0 - 1);
+        uint32_t mu = up & ((1u << (b + 3)) - 1u) & ~((1u << a) - 1u);   // columns a - 1 .. b + 1
+        while (mu) {
+            const int j = __ffs(mu) - 1;
+            const int lu = __ffs(~(mu >> j)) - 1;
+            mu &= ~(((1u << lu) - 1u) << j);
+            unite(F.parent, s0, pu + j);
         }
     }
 }
