@@ -238,7 +238,7 @@ def proposal_vs_plain(torch, ld, dev, flush, check_frames: int = 1024, reps: int
     src = tp.FrameSource(torch, dev, N_FRAMES)
     same = fb = act = total = 0
     with ld.Context(dev.index) as c:
-        c.autotune(src.fill(tp.EVAL_SEED0 + np.arange(16)), p, iters=2)
+        c.autotune(src.fill(tp.EVAL_SEED0 + np.arange(N_FRAMES)), p, iters=3)   # a batch of the timed size
         for b0 in range(0, check_frames, N_FRAMES):
             prep = c.prepare(src.fill(tp.EVAL_SEED0 + b0 + np.arange(N_FRAMES)))
             a = [t.cpu().numpy() for t in c.detect_batch(prep, p)]
@@ -368,7 +368,7 @@ def next_rows(torch, ld, dev, frames, edges_total: float, flush, hbm_peak: float
     out = {}
     with ld.Context(dev.index) as c:
         prep = c.prepare(frames)
-        c.autotune(frames[:16], p, iters=2)
+        c.autotune(frames, p, iters=3)   # on the batch that is timed
         base = timed(lambda: c.detect_batch(prep, p, stream=s))
         res = {}
         lines_ms = timed(lambda: res.update(r=c.detect_lines_batch(prep, p, lp, stream=s)))
@@ -572,7 +572,7 @@ def main():
     p = ld.params(n_theta=N_THETA, top_k=TOP_K)
     ctx = ld.Context(local_rank)
     ctx.reserve(nf * W * H, nf, 0, p)
-    ctx.autotune([frames_d[i] for i in range(min(nf, 16))], p, iters=2)   # tile sizes only
+    ctx.autotune([frames_d[i] for i in range(nf)], p, iters=3)   # tile sizes only, on the batch that is timed
     out = (torch.zeros((nf, TOP_K, 3), dtype=torch.int32, device=dev),
            torch.zeros(nf, dtype=torch.int32, device=dev),
            torch.zeros(nf, dtype=torch.int32, device=dev))
