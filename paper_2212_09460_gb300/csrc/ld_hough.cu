@@ -743,20 +743,18 @@ __device__ __forceinline__ int cols_unit(const HoughLaunch &L, const HoughFrame 
         const int64_t start = e0 + (int64_t)c * chunk;
         const int n_c = (int)((e1 - start) < chunk ? (e1 - start) : chunk);
         const int n4 = n_c & ~3;
-        // part `half` of the lanes takes the part-th of the chunk's 4-edge groups
-        const int G = n4 >> 2, Gh = (G + kParts - 1) / kParts;
-        const int g_lo = half * Gh, g_hi = min(G, g_lo + Gh);
+        // the chunk's 4-edge groups: part `half` of warp w takes groups
+        // half + kParts (w + kColWarps i), so the parts of a warp read adjacent
+        // groups (a pointer loop unrolled by four: no per-group bound test)
         const uint4 *buf4 = reinterpret_cast<const uint4 *>(ring + st * chunk);
-#pragma unroll 2
-        for (int k = warp; k < Gh; k += kColWarps) {
-            const int gi = g_lo + k;
-            if (gi < g_hi) {
-                const uint4 q = buf4[gi];   // the half-warp's 4 edges (broadcast)
-                vote(q.x);
-                vote(q.y);
-                vote(q.z);
-                vote(q.w);
-            }
+        const uint4 *const g_end = buf4 + (n4 >> 2);
+#pragma unroll 4
+        for (const uint4 *gp = buf4 + half + kParts * warp; gp < g_end; gp += kParts * kColWarps) {
+            const uint4 q = *gp;   // the part's 4 edges (a broadcast load)
+            vote(q.x);
+            vote(q.y);
+            vote(q.z);
+            vote(q.w);
         }
         if (warp == kColWarps - 1 && half == 0)   // the last n_c % 4 edges (the frame's last chunk)
             for (int i = n4; i < n_c; ++i) vote(F.edges[start + i]);
