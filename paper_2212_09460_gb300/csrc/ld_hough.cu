@@ -155,41 +155,38 @@ __device__ void select_tile(const HoughLaunch &L, uint64_t *out, const uint32_t 
     const int M = L.cand_m;
     const int32_t mv = L.min_votes;
 
-    // pass 0: included count, per-thread maximum, overall maximum
-    int cnt = 0;
-    int tmax = -1;
-    for (int i = tid; i < words; i += nthr) {
-        const uint32_t wv = acc[i];
-        const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-        if (a >= mv) { ++cnt; tmax = max(tmax, a); }
-        if (b >= mv) { ++cnt; tmax = max(tmax, b); }
-    }
-    const int total = block_sum(cnt, S);
-    uint32_t vmax = tmax < 0 ? 0u : (uint32_t)tmax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
-    if (lane == 0) S.red[warp] = vmax;
-    __syncthreads();
-    uint32_t gmax = 0;
-    for (int w = 0; w < nwarps; ++w) gmax = max(gmax, S.red[w]);
-    __syncthreads();
-
-    // Fast path.  L = the M-th largest of the per-thread maxima: M distinct
-    // cells have votes >= L, so every top-M cell does too.  The cells with
-    // votes >= L ("survivors", usually a few hundred) are compacted as keys,
-    // which are unique and ordered like the peaks, and the M largest keys are
-    // exactly the tile's top-M: picked by rank (up to one survivor per
-    // thread) or by a descending sort.  Too many survivors: the general path.
+    // Fast path.  Each thread's largest count over its words (one packed
+    // 16-bit max per word); L = the M-th largest of these maxima among the
+    // threads whose maximum is >= min_votes.  M distinct cells have votes
+    // >= L, so every top-M cell does too.  The cells with votes >= L
+    // ("survivors", a few hundred at most on road frames) are compacted as
+    // keys, which are unique and ordered like the peaks, and the M largest
+    // keys are exactly the tile's top-M: picked by rank (up to one survivor
+    // per thread) or by a descending sort.  No threshold (fewer than M
+    // threads hold a cell >= min_votes) or too many survivors: the general
+    // path below.
     constexpr int kMaxSurv = 2048;
-    if (total > M && M <= nthr) {
+    if (M <= nthr) {
+        uint32_t m2 = 0u;
+        for (int i = tid; i < words; i += nthr) {
+            const uint32_t wv = acc[i];
+            asm("max.u16x2 %0, %1, %2;" : "=r"(m2) : "r"(m2), "r"(wv));
+        }
+        int tmax = max((int)(m2 & 0xFFFFu), (int)(m2 >> 16));
+        if (tmax < mv) tmax = -1;
         uint64_t *keys = reinterpret_cast<uint64_t *>(ring + nthr);
         if (tid == 0) S.surv = 0;
-        const int Lth = block_mth_largest(tmax, M, 16);   // counts are 16-bit
+        const int Lth = block_mth_largest(tmax, M, S);
         if (Lth >= 0) {   // block-uniform
+            // a word holds a survivor iff max(lo, hi) >= L, i.e. the packed
+            // max with (L-1, L-1) differs from (L-1, L-1)
+            const uint32_t t2 = Lth >= 1 ? (uint32_t)(Lth - 1) * 0x10001u : 0u;
             for (int i = tid; i < words; i += nthr) {
                 const uint32_t wv = acc[i];
-                const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
-                if (a >= Lth || b >= Lth) {
+                uint32_t mx;
+                asm("max.u16x2 %0, %1, %2;" : "=r"(mx) : "r"(wv), "r"(t2));
+                if (Lth == 0 || mx != t2) {
+                    const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
                     int p, ra, rb;
                     lay.cells(i, p, ra, rb);
                     if (a >= Lth) {
@@ -220,6 +217,25 @@ __device__ void select_tile(const HoughLaunch &L, uint64_t *out, const uint32_t 
         }
         __syncthreads();
     }
+
+    // General path.  Pass 0: included count and overall maximum.
+    int cnt = 0;
+    int tmax = -1;
+    for (int i = tid; i < words; i += nthr) {
+        const uint32_t wv = acc[i];
+        const int32_t a = (int32_t)(wv & 0xFFFFu), b = (int32_t)(wv >> 16);
+        if (a >= mv) { ++cnt; tmax = max(tmax, a); }
+        if (b >= mv) { ++cnt; tmax = max(tmax, b); }
+    }
+    const int total = block_sum(cnt, S);
+    uint32_t vmax = tmax < 0 ? 0u : (uint32_t)tmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+    if (lane == 0) S.red[warp] = vmax;
+    __syncthreads();
+    uint32_t gmax = 0;
+    for (int w = 0; w < nwarps; ++w) gmax = max(gmax, S.red[w]);
+    __syncthreads();
 
     const bool all_in = total <= M;
     if (tid == 0) {

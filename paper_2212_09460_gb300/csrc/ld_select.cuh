@@ -55,22 +55,9 @@ __device__ __forceinline__ void block_sort_desc(T *buf, int n) {
     }
 }
 
-// The M-th largest of one value per thread, for values below 2^nbits (a
-// thread without a value passes -1): the largest L >= 0 with at least M
-// threads holding a value >= L, fixed bit by bit from the top with block-wide
-// counts (the count of values >= L only falls as L grows); -1 if fewer than M
-// threads hold a value.  Every thread of the block must call it.
-__device__ __forceinline__ int block_mth_largest(int v, int M, int nbits) {
-    if (__syncthreads_count(v >= 0) < M) return -1;
-    int lo = 0;
-    for (int b = nbits - 1; b >= 0; --b) {
-        const int cand = lo | (1 << b);
-        if (__syncthreads_count(v >= cand) >= M) lo = cand;
-    }
-    return lo;
-}
 
-// The same over unsigned 32-bit values; `has` says whether the thread holds
+// The M-th largest of unsigned 32-bit values, one per thread, fixed bit by bit
+// from the top with block-wide counts; `has` says whether the thread holds
 // one.  Returns false (no threshold) if fewer than M threads hold a value.
 __device__ __forceinline__ bool block_mth_largest_u32(uint32_t u, bool has, int M, uint32_t &L) {
     if (__syncthreads_count(has) < M) return false;
@@ -100,6 +87,44 @@ __device__ __forceinline__ void block_topm_by_rank(const uint64_t *keys, int n, 
 __device__ __forceinline__ void ballot_digits(uint32_t (&wh)[16], bool m, uint32_t dig) {
 #pragma unroll
     for (int d = 0; d < 16; ++d) wh[d] += __popc(__ballot_sync(0xFFFFFFFFu, m && dig == (uint32_t)d));
+}
+
+// The M-th largest of one value per thread (a thread without a value passes
+// -1): the largest L >= 0 with at least M threads holding a value >= L; -1 if
+// fewer than M threads hold a value.  L is fixed bit by bit from the top with
+// block-wide counts (the count of values >= L only falls as L grows), starting
+// at the highest set bit of the block's largest value: a higher bit would
+// give a candidate above every value, which no thread reaches.  One barrier
+// pass gathers the count of values and the largest (per-warp figures in
+// S.hist, the block's in S.digit_sum), then one barrier per bit.  Every
+// thread of the block must call it; the caller writes S.hist and S.digit_sum
+// again only after another barrier.
+__device__ __forceinline__ int block_mth_largest(int v, int M, SelectSmem &S) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int wcnt = __popc(__ballot_sync(0xFFFFFFFFu, v >= 0));
+    const int wmax = __reduce_max_sync(0xFFFFFFFFu, v);
+    if (lane == 0) {
+        S.hist[warp][0] = (uint32_t)wcnt;
+        S.hist[warp][1] = (uint32_t)wmax;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int c = __reduce_add_sync(0xFFFFFFFFu, lane < nw ? (int)S.hist[lane][0] : 0);
+        const int m = __reduce_max_sync(0xFFFFFFFFu, lane < nw ? (int)S.hist[lane][1] : -1);
+        if (lane == 0) {
+            S.digit_sum[0] = (uint32_t)c;
+            S.digit_sum[1] = (uint32_t)m;
+        }
+    }
+    __syncthreads();
+    const int n_with = (int)S.digit_sum[0], vmax = (int)S.digit_sum[1];
+    if (n_with < M) return -1;
+    int lo = 0;
+    for (int b = 31 - __clz(vmax); b >= 0; --b) {   // vmax >= 0 here
+        const int cand = lo | (1 << b);
+        if (__syncthreads_count(v >= cand) >= M) lo = cand;
+    }
+    return lo;
 }
 
 // Block sum of a per-thread int.
