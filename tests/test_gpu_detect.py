@@ -235,3 +235,52 @@ def test_detect_noise_frames_nearly_all_edges(ctx, ldlib, ora):
         kw = dict(n_theta=360, top_k=4)
         pk, cnt, st = _detect(ctx, ldlib, frames, [f.shape[1] for f in frames], **kw)
         _check(ora, frames, pk, cnt, st, **kw)
+
+
+def _dots(w, h, pts):
+    img = np.zeros((h, w), np.uint8)
+    for x, y in pts:
+        img[y, x] = 255
+    return img
+
+
+def _tile_totals(acc, n_theta, width, min_votes):
+    """Cells >= min_votes in each tile of `width` theta pairs (pairs split
+    evenly over the tiles; pair j holds theta j and n - j, pair 0 holds 0 and
+    n/2), the counts a tile's top-M selection sees."""
+    n_pairs = n_theta // 2
+    n_tiles = -(-n_pairs // width)
+    base, extra = divmod(n_pairs, n_tiles)
+    per_theta = (acc >= min_votes).sum(axis=1)
+    out = []
+    for t in range(n_tiles):
+        j0 = t * base + min(t, extra)
+        js = range(j0, j0 + base + (1 if t < extra else 0))
+        out.append(int(sum(per_theta[j] + per_theta[n_theta // 2 if j == 0 else n_theta - j] for j in js)))
+    return out
+
+
+@pytest.mark.parametrize("min_votes", [1, 2])
+def test_detect_tiles_near_candidate_count(ctx, ldlib, ora, min_votes):
+    # A few isolated bright pixels (a ring of 8 edge pixels each) leave 45 to
+    # 300 voted cells per tile.  Sweeping top_k and the suppression window moves
+    # M = nms_theta * nms_rho * (top_k - 1) + 1 across those counts, so tiles
+    # hold fewer cells >= min_votes than M, exactly M, and more: the tile
+    # selection's threshold path and its general path both run, and both
+    # must give the oracle's peaks.
+    raw = [_dots(48, 40, [(20, 18)]), _dots(64, 33, [(10, 10), (40, 20), (43, 23)])]
+    n_theta = 32
+    totals = set()
+    for r in raw:
+        acc = ora.hough(ora.edge_list(ora.binarize(ora.sobel_mag(r), 128)), r.shape[1], r.shape[0], n_theta)
+        for width in (8, 16):
+            totals.update(_tile_totals(acc, n_theta, width, min_votes))
+    swept = set()
+    for nms_theta in (1, 3):
+        for nms_rho in (1, 3, 5, 7):
+            for top_k in range(1, 17):
+                kw = dict(n_theta=n_theta, top_k=top_k, nms_theta=nms_theta, nms_rho=nms_rho, min_votes=min_votes)
+                swept.add(nms_theta * nms_rho * (top_k - 1) + 1)
+                pk, n, st = _detect(ctx, ldlib, raw, [r.shape[1] for r in raw], **kw)
+                _check(ora, raw, pk, n, st, **kw)
+    assert totals & swept, (sorted(totals), sorted(swept))
