@@ -56,7 +56,7 @@ select_kernel(const __grid_constant__ SelectLaunch L) {
         __shared__ int n_surv;
         if (tid == 0) n_surv = 0;
         uint32_t Lu = 0;
-        if (block_mth_largest_u32(umax, cnt > 0, M, Lu)) {   // block-uniform
+        if (block_mth_largest_u32(umax, cnt > 0, M, Lu, S)) {   // block-uniform
             for (int i = tid; i < n; i += kSelectThreads) {
                 const int32_t v = a[i];
                 if (v >= mv && ((uint32_t)v ^ 0x80000000u) >= Lu) {

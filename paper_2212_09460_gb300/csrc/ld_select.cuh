@@ -56,13 +56,49 @@ __device__ __forceinline__ void block_sort_desc(T *buf, int n) {
 }
 
 
-// The M-th largest of unsigned 32-bit values, one per thread, fixed bit by bit
-// from the top with block-wide counts; `has` says whether the thread holds
-// one.  Returns false (no threshold) if fewer than M threads hold a value.
-__device__ __forceinline__ bool block_mth_largest_u32(uint32_t u, bool has, int M, uint32_t &L) {
-    if (__syncthreads_count(has) < M) return false;
-    uint32_t lo = 0;
-    for (int b = 31; b >= 0; --b) {
+// The M-th largest of unsigned 32-bit values, one per thread; `has` says
+// whether the thread holds one.  Returns false (no threshold) if fewer than M
+// threads hold a value.  The threshold lies between the smallest and the
+// largest value held (M of them reach it, all of them reach the smallest),
+// so it shares the bits above their highest differing bit; those are taken
+// as found, and the rest fixed bit by bit with block-wide counts.  One
+// barrier pass gathers the count, the smallest and the largest (per-warp
+// figures in S.hist, the block's in S.digit_sum), then one barrier per bit.
+// Every thread of the block must call it; the caller writes S.hist and
+// S.digit_sum again only after another barrier.
+__device__ __forceinline__ bool block_mth_largest_u32(uint32_t u, bool has, int M, uint32_t &L, SelectSmem &S) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t wcnt = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, has));
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, has ? u : 0u);
+    const uint32_t wmin = __reduce_min_sync(0xFFFFFFFFu, has ? u : 0xFFFFFFFFu);
+    if (lane == 0) {
+        S.hist[warp][0] = wcnt;
+        S.hist[warp][1] = wmax;
+        S.hist[warp][2] = wmin;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, lane < nw ? S.hist[lane][0] : 0u);
+        const uint32_t mx = __reduce_max_sync(0xFFFFFFFFu, lane < nw ? S.hist[lane][1] : 0u);
+        const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, lane < nw ? S.hist[lane][2] : 0xFFFFFFFFu);
+        if (lane == 0) {
+            S.digit_sum[0] = c;
+            S.digit_sum[1] = mx;
+            S.digit_sum[2] = mn;
+        }
+    }
+    __syncthreads();
+    const int n_with = (int)S.digit_sum[0];
+    const uint32_t umax = S.digit_sum[1], umin = S.digit_sum[2];
+    if (n_with < M) return false;
+    const uint32_t diff = umin ^ umax;
+    if (diff == 0u) {   // every value held is the same
+        L = umax;
+        return true;
+    }
+    const int hb = 31 - __clz(diff);   // highest differing bit
+    uint32_t lo = hb == 31 ? 0u : umax & (0xFFFFFFFFu << (hb + 1));
+    for (int b = hb; b >= 0; --b) {
         const uint32_t cand = lo | (1u << b);
         if (__syncthreads_count(has && u >= cand) >= M) lo = cand;
     }
